@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Throughput of the tracer-box lattice Boltzmann step on GB300.
+
+Workload (default): one D3Q19 BGK box of 128^3 sites, tau 0.8, FP32
+populations stored as deviations f_i - w_i, velocity boundaries on all six
+faces from a synthetic Kolmogorov-spectrum field (1024 modes, |k| in
+[1, 64], one coarse sample per LB step), one 64-bead FENE chain with
+Philox noise at kT 1e-4 coupled by Stokes friction.  One "step" is one full
+LB step: bead coupling, fused stream-collide + boundary layer, forced
+re-collision.  The boundary samples of all timed steps are generated on the
+GPU before the timed region and stay resident in HBM (they stand in for the
+DNS record the paper reads from disk); each step's working set
+(2 x 159 MB of populations) exceeds the 129 MB L2, so no flush is needed.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+the host cores instead (each step a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(E=128, tau=0.8, M=1024, k_min=1.0, k_max=64.0, K=1, nbeads=64, kT=1e-4, n_md=50, seed=0)
+METRIC = "LB MLUPS"
+UNIT = "MLUPS"
+Q = 19
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10000)
+    p.add_argument("--warmup", type=int, default=50)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--storage", default="f32", choices=["f32", "f64", "f16", "bf16"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--threads", type=int, default=0, help="stream-collide block size (0 = library default)")
+    p.add_argument("--ctas", type=int, default=0, help="persistent grid size (0 = one block per tile)")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def alg_bytes_per_launch(E, s_elem, s_real, time_interp=0):
+    """Algorithmic bytes of one stream-collide launch over one box with
+    velocity faces: interior sites read and write 19 populations, boundary
+    sites write 19 and read 3 components of 2 (linear) or 4 (Hermite)
+    coarse samples."""
+    interior = (E - 2) ** 3
+    boundary = E ** 3 - interior
+    nsamp = 2 if time_interp == 0 else 4
+    return interior * 2 * Q * s_elem + boundary * (Q * s_elem + 3 * nsamp * s_real)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_0809_4958_gb300/csrc/lbt_kernels.cuh", "paper_0809_4958_gb300/csrc/lbt_device.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(storage):
+    """DRAM bytes per stream-collide launch from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        ent = d.get(storage)
+        if ent and ent.get("kernel_hash") == kernel_source_hash():
+            return float(ent["bytes_per_launch_full_size"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(storage_name):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload:
+    a few LB steps of the 128^3 box with the same chain and boundary recipe,
+    on all host cores it uses (OpenMP)."""
+    import oracle
+    from paper_0809_4958_gb300 import inputs
+    w = WORKLOAD
+    E = w["E"]
+    modes = inputs.mode_table(w["seed"] + 1000, 64, w["k_min"], w["k_max"], E)
+    box = oracle.BoxParams(E=E, tau=w["tau"], K=1)
+    ch = oracle.ChainParams(nbeads=w["nbeads"], kT=w["kT"], n_md=w["n_md"], seed=1)
+    pos0 = inputs.chain_start(w["seed"] + 5, w["nbeads"], E)
+    probe = 1
+    S = oracle.face_samples(modes, E, 1, 0, 8)
+    sim = oracle.Sim(box, np.zeros((3, E, E, E)), S, ch, pos0)
+    t0 = time.perf_counter()
+    assert sim.run(probe) == 0
+    t1 = time.perf_counter() - t0
+    nsteps = int(max(1, min(100, 12.0 / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    assert sim.run(nsteps) == 0
+    dt = time.perf_counter() - t0
+    return {"value": E ** 3 * nsteps / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d FP64 oracle steps of the %d^3 box (same chain and boundary recipe, 64-mode boundary "
+                      "field, initial field at rest), after 1 untimed step" % (nsteps, E)}
+
+
+def run_reference(args):
+    """--impl reference: the oracle as it stands, each timed step a bounded
+    sample of the workload (one LB step of a box of edge E_s with the same
+    recipe, E_s the largest of 128, 96, 64, 48, 32 that keeps the run within a
+    few minutes)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_0809_4958_gb300 import inputs
+    oracle.build()
+    w = WORKLOAD
+    budget = 150.0
+    chosen = None
+    for Es in (128, 96, 64, 48, 32):
+        modes = inputs.mode_table(w["seed"] + 1000, 64, w["k_min"], min(w["k_max"], Es / 2), Es)
+        S = oracle.face_samples(modes, Es, 1, 0, args.steps + args.warmup + 3)
+        sim = oracle.Sim(oracle.BoxParams(E=Es, tau=w["tau"], K=1), np.zeros((3, Es, Es, Es)), S,
+                         oracle.ChainParams(nbeads=min(w["nbeads"], 2 * Es // 2), kT=w["kT"], n_md=w["n_md"], seed=1),
+                         inputs.chain_start(w["seed"] + 5, min(w["nbeads"], 2 * Es // 2), Es))
+        t0 = time.perf_counter()
+        assert sim.run(1) == 0
+        t1 = time.perf_counter() - t0
+        if t1 * (args.steps + args.warmup) <= budget or Es == 32:
+            chosen = (Es, sim)
+            break
+    Es, sim = chosen
+    assert sim.run(max(0, args.warmup - 1)) == 0
+    t0 = time.perf_counter()
+    assert sim.run(args.steps) == 0
+    dt = time.perf_counter() - t0
+    value = Es ** 3 * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "tracer box %d^3 D3Q19 BGK tau %.2f, 64-bead FENE chain kT %g, Kolmogorov "
+                                   "velocity boundaries (K=1); FP64 CPU oracle" % (w["E"], w["tau"], w["kT"])},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "each step: one oracle LB step of a %d^3 box with the same recipe" % Es},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_0809_4958_gb300 import inputs, lbtracer as lbt
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    storage = {"f32": lbt.LB_STORE_F32, "f64": lbt.LB_STORE_F64, "f16": lbt.LB_STORE_F16DEV,
+               "bf16": lbt.LB_STORE_BF16DEV}[args.storage]
+    s_elem = {"f32": 4, "f64": 8, "f16": 2, "bf16": 2}[args.storage]
+    s_real = 8 if args.storage == "f64" else 4
+    real = torch.float64 if args.storage == "f64" else torch.float32
+    w = WORKLOAD
+    E = w["E"]
+    seed = w["seed"] + rank  # one independent tracer box per GPU
+
+    # ---- inputs (untimed): boundary record, initial field, chain ----
+    modes = inputs.mode_table(seed, w["M"], w["k_min"], w["k_max"], E)
+    nsamp = args.warmup + args.steps + 2
+    faces = lbt.synth_faces(modes, E, w["K"], 0, nsamp, real)
+    u0 = lbt.synth_volume(modes, E, 0.0, real)
+    pos0 = inputs.chain_start(seed + 5, w["nbeads"], E)
+    stream = torch.cuda.Stream()
+    tr = lbt.Tracers([lbt.box_desc(E, w["tau"], nbeads=w["nbeads"], K=w["K"])], storage, stream=stream)
+    if args.threads:
+        tr.lb_set_launch(args.threads, args.ctas)
+    torch.cuda.synchronize()
+    tr.lb_init(0, u0)
+    tr.chain_couple(0, lbt.chain_desc(w["nbeads"], kT=w["kT"], n_md=w["n_md"], seed=seed), pos0)
+    pushed = [-1]
+
+    def push_until(j, src):
+        while pushed[0] < j:
+            pushed[0] += 1
+            tr.lb_set_boundary(0, pushed[0], src(pushed[0]))
+
+    dev_src = lambda j: faces[j]  # noqa: E731
+    for n in range(args.warmup):
+        push_until(n + 1, dev_src)
+        tr.lb_step(1)
+    tr.lb_sync()
+
+    # ---- timed region (device-resident inputs) ----
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    tr.lb_profile(1, args.steps)
+    clocks.start()
+    time.sleep(0.3)  # let the sampler take its first reading
+    ev0.record(stream)
+    n0 = args.warmup
+    for n in range(n0, n0 + args.steps):
+        push_until(n + 1, dev_src)
+        tr.lb_step(1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    tr.lb_profile(0)
+    sc_ms, sc_n = tr.lb_profile_read()
+    tr.lb_sync()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    ms_per_step = ms / args.steps
+    value = world * E ** 3 * args.steps / (ms * 1e-3) / 1e6
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        e2e_steps = min(args.steps, 2000)
+        host_faces = torch.empty((e2e_steps + 2, 6, 3, E, E), dtype=real, pin_memory=True)
+        host_faces.copy_(faces[:e2e_steps + 2].cpu())
+        host_chain = torch.empty((e2e_steps, 2, w["nbeads"], 3), dtype=torch.float64, pin_memory=True)
+        # fresh context so the pushed samples line up with the host record
+        tr2 = lbt.Tracers([lbt.box_desc(E, w["tau"], nbeads=w["nbeads"], K=w["K"])], storage, stream=stream)
+        torch.cuda.synchronize()
+        tr2.lb_init(0, u0)
+        tr2.chain_couple(0, lbt.chain_desc(w["nbeads"], kT=w["kT"], n_md=w["n_md"], seed=seed), pos0)
+        tr2.lb_set_boundary(0, 0, host_faces[0])
+        tr2.lb_sync()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        for n in range(e2e_steps):
+            tr2.lb_set_boundary(0, n + 1, host_faces[n + 1])
+            tr2.lb_step(1)
+            tr2.lb_read_fields(0, lbt.LB_FIELD_CHAIN | lbt.LB_FIELD_ASYNC, host_chain[n])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms2 = max(ev0.elapsed_time(ev1), wall * 1e3)
+        if world > 1:
+            t = torch.tensor([ms2], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms2 = float(t.item())
+        e2e = {"value": world * E ** 3 * e2e_steps / (ms2 * 1e-3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": 6 * 3 * E * E * s_real, "d2h_bytes_per_step": 2 * w["nbeads"] * 3 * 8,
+               "steps": e2e_steps}
+        tr2.close()
+
+    if rank != 0:
+        tr.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = measured_peaks()
+    alg = alg_bytes_per_launch(E, s_elem, s_real)
+    avg_sc = sc_ms / max(sc_n, 1)
+    achieved = alg / (avg_sc * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "config": {"workload": "tracer box %d^3 D3Q19 BGK tau %.2f, %s populations (f_i - w_i), 64-bead FENE "
+                               "chain kT %g, Kolmogorov velocity boundaries on 6 faces (1024 modes, one sample per "
+                               "step)" % (E, w["tau"], args.storage, w["kT"]),
+                   "boxes_per_gpu": 1, "sites_per_box": E ** 3, "l2": "working set 2 x %.0f MB > L2, no flush"
+                   % (Q * E ** 3 * s_elem / 1e6), "launch": {"threads": args.threads or 256, "ctas": args.ctas}},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": ncu_traffic(args.storage),
+                     "kernel": "k_stream_collide", "avg_launch_ms": avg_sc, "alg_bytes_per_launch": alg,
+                     "peak_kind": peak_kind, "launches_timed": sc_n},
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": args.steps * 3,
+    }
+    if not args.no_cpu:
+        import oracle
+        oracle.build()
+        line["cpu_baseline"] = cpu_baseline(args.storage)
+    tr.close()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+/*
+ * lbtracer.h -- C ABI of the GB300 tracer-box lattice Boltzmann library.
+ *
+ * The library advances many small lattice Boltzmann boxes, each of which
+ * follows one Lagrangian tracer of a coarse turbulent flow, as in Lee,
+ * Duenweg and Schumacher, "Multiscale modelling strategy using the lattice
+ * Boltzmann method for polymer dynamics in a turbulent flow" (arXiv:0809.4958):
+ *
+ *   - D3Q19 lattice (Sec. 3), BGK collision with relaxation time tau
+ *     (the paper does not print the operator; BGK is the reading),
+ *     viscosity nu = (tau - 1/2) / 3 in lattice units;
+ *   - initial condition: local equilibrium with the prescribed velocity on
+ *     every site at t = 0 (Sec. 2);
+ *   - boundary condition: for t > 0 the outer site layer is set to the local
+ *     equilibrium of the prescribed boundary velocity (Sec. 2), interpolated
+ *     in time between coarse samples (Sec. 3, after Eq. 1);
+ *   - a bead-spring chain coupled to the fluid through a Stokes friction
+ *     coefficient (Sec. 1, Ahlrichs-Duenweg hybrid method) with its centre of
+ *     mass pinned at the tracer, i.e. the box centre (Sec. 2).
+ *
+ * Conventions
+ *   Lattice units throughout (spacing 1, time step 1, reference density 1).
+ *   A box has E sites per axis (E a multiple of 8, 8 <= E <= 1024); site
+ *   (x, y, z) is stored at linear index (z*E + y)*E + x (x fastest).
+ *   Population order: rest; +x, -x, +y, -y, +z, -z; then (1,1,0), (-1,-1,0),
+ *   (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1), (0,1,1),
+ *   (0,-1,-1), (0,1,-1), (0,-1,1).
+ *   Face order: x-, x+, y-, y+, z-, z+.  In-face coordinates (p, q) are
+ *   (y, z) on x faces, (x, z) on y faces, (x, y) on z faces; a face array is
+ *   [3 components][q][p].  A site on several velocity faces belongs to the
+ *   first of them in face order.
+ *   "real" below is double for LB_STORE_F64 and float for every other storage.
+ *
+ * Memory ownership
+ *   The library never allocates device memory.  lb_plan reports the size of
+ *   one device arena; the caller allocates it (for example as a torch tensor),
+ *   keeps it alive until lb_destroy, and passes it to lb_create.  Every other
+ *   pointer argument is borrowed for the duration of the call (host or device
+ *   memory, told apart with cudaPointerGetAttributes) unless stated otherwise.
+ *   All work is enqueued on the caller's CUDA stream given to lb_create; calls
+ *   return after enqueueing except those documented as synchronising.
+ *
+ * Errors
+ *   Every function returns LB_OK (0) or an LB_ERR_* code; lb_last_error gives
+ *   a message.  Kernels never trap: a box whose chain breaks a rule (bond at
+ *   the FENE limit, bead stencil leaving the interior) or whose state turns
+ *   non-finite gets a device status word and is frozen (its state stops
+ *   changing); the code is returned by the next synchronising call.
+ */
+#ifndef LBTRACER_H
+#define LBTRACER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define LB_OK 0
+#define LB_ERR_ARG 1        /* bad argument: shape, tau <= 1/2, E not a multiple of 8, null pointer */
+#define LB_ERR_CUDA 2       /* a CUDA runtime call failed */
+#define LB_ERR_FENE 3       /* a bond reached the FENE maximum extension R0 */
+#define LB_ERR_BEAD_OOB 4   /* a bead's interpolation stencil left the box interior */
+#define LB_ERR_NONFINITE 5  /* mass or momentum sum of a box is not finite, or density <= 0 */
+#define LB_ERR_TIMEOUT 6    /* a bounded wait for the stream expired */
+#define LB_ERR_STATE 7      /* call out of order (e.g. stepping past the last boundary sample) */
+#define LB_ERR_SIZE 8       /* arena too small for the plan */
+
+/* ---- population storage (one per context) ---- */
+#define LB_STORE_F64 0      /* f_i - w_i in FP64, FP64 arithmetic */
+#define LB_STORE_F32 1      /* f_i - w_i in FP32, FP32 arithmetic */
+#define LB_STORE_F16DEV 2   /* f_i - w_i in IEEE binary16 (round to nearest even), FP32 arithmetic */
+#define LB_STORE_BF16DEV 3  /* f_i - w_i in bfloat16 (round to nearest even), FP32 arithmetic */
+
+/* ---- face modes (both faces of an axis must agree) ---- */
+#define LB_FACE_VELOCITY 0  /* outer layer set to the equilibrium of the boundary velocity */
+#define LB_FACE_PERIODIC 1
+
+/* ---- time interpolation of the coarse boundary samples ---- */
+#define LB_TIME_LINEAR 0    /* linear between samples j and j+1 (the paper's form) */
+#define LB_TIME_HERMITE 1   /* cubic Hermite, Catmull-Rom tangents, one-sided on the first interval */
+#define LB_TIME_MLP 2       /* Hermite plus a learned residual (reserved, not built) */
+
+/* ---- fields for lb_read_fields ---- */
+#define LB_FIELD_RHO 0      /* real [E^3] density */
+#define LB_FIELD_U 1        /* real [3][E^3] velocity */
+#define LB_FIELD_DEV 2      /* real [19][E^3] stored populations minus weights, f_i - w_i */
+#define LB_FIELD_CHAIN 3    /* double [2][nbeads][3]: positions then velocities */
+#define LB_FIELD_ASYNC 0x100 /* OR-ed into `what`: enqueue the read-out only, no wait, no status check */
+
+#define LB_ALL_BOXES (-1)
+
+typedef struct lb_box_desc {
+    int32_t E;             /* sites per axis, multiple of 8 */
+    int32_t face_mode[6];  /* LB_FACE_* per face, x-, x+, y-, y+, z-, z+ */
+    int32_t time_interp;   /* LB_TIME_* */
+    int32_t K;             /* LB steps per coarse sample interval, >= 1 */
+    int32_t nbeads;        /* capacity for the chain of this box (0 = no chain), <= 256 */
+    double tau;            /* BGK relaxation time, > 1/2 */
+    double rho_b;          /* density of the boundary equilibrium (1.0) */
+    double body_accel[3];  /* uniform body acceleration a; force density rho a (Guo forcing) */
+} lb_box_desc;
+
+typedef struct lb_chain_desc {
+    int32_t nbeads;        /* beads in the chain, 1 .. capacity given in lb_box_desc */
+    int32_t n_md;          /* MD substeps per LB step, >= 1 */
+    int32_t pin_com;       /* 0 off, 1 pin the centre of mass at the box centre, 2 also zero its velocity */
+    int32_t reserved;
+    double k_fene;         /* FENE spring constant k */
+    double R0;             /* FENE maximum bond length */
+    double zeta;           /* bead friction coefficient (Stokes friction of the coupling) */
+    double mass;           /* bead mass */
+    double kT;             /* temperature of the bead noise (0 = none) */
+    double f_ext[3];       /* constant external force on every bead */
+    uint64_t seed;         /* Philox key of the bead noise */
+} lb_chain_desc;
+
+typedef struct lb_ctx lb_ctx;
+
+/*
+ * lb_plan -- size of the device arena for a context.
+ *   boxes[nboxes]: box descriptions (host).  storage: LB_STORE_*.
+ *   *arena_bytes receives the number of bytes the caller must allocate
+ *   (device memory, 256-byte aligned).
+ *   Returns LB_ERR_ARG for an invalid description.
+ */
+int32_t lb_plan(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, size_t* arena_bytes);
+
+/*
+ * lb_create -- build a context over a caller-owned arena.
+ *   arena: device pointer to at least the lb_plan size; borrowed until lb_destroy.
+ *   stream: the cudaStream_t every later call enqueues on (NULL = legacy default stream).
+ *   The library creates one private side stream and a few events for
+ *   concurrency between the bead kernel and the stream-collide kernel.
+ *   Populations are left uninitialised until lb_init.
+ */
+int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, void* arena,
+                  size_t arena_bytes, void* stream, lb_ctx** out);
+
+/* lb_destroy -- wait for the stream, release the host context, events, side
+ * stream and any captured graph.  Does not free the arena. */
+int32_t lb_destroy(lb_ctx* ctx);
+
+/*
+ * lb_init -- initial condition (Sec. 2): every site of the box gets the local
+ * equilibrium with density 1 and velocity u0.
+ *   u0: real [3][E^3], host or device.  A host array is staged through the
+ *   box's second population buffer.  A one-box context may be re-initialised
+ *   at any time (step counter and boundary ring restart at 0); the boxes of a
+ *   multi-box context are initialised before the first lb_step
+ *   (LB_ERR_STATE otherwise).
+ */
+int32_t lb_init(lb_ctx* ctx, int32_t box, const void* u0);
+
+/*
+ * lb_set_boundary -- push coarse boundary sample j (taken at t = j K) into
+ * the 4-slot ring of the box (Sec. 3: boundary velocities interpolated in
+ * time between the samples).
+ *   face_u: real [6][3][E][E] for one box, or, with box == LB_ALL_BOXES, the
+ *   arrays of all boxes back to back in box order; host or device.
+ *   Samples must be pushed in order 0, 1, 2, ...; sample j may be pushed
+ *   once the step that needs sample j-4 has been enqueued.
+ *   The copy is enqueued on the context stream (pinned host memory keeps it
+ *   asynchronous).
+ */
+int32_t lb_set_boundary(lb_ctx* ctx, int32_t box, int64_t sample_index, const void* face_u);
+
+/*
+ * chain_couple -- place the bead-spring chain of a box (Sec. 1 and 2).
+ *   pos0, vel0: double [nbeads][3], host or device (vel0 may be NULL = 0).
+ *   Bead positions are in lattice units; on a velocity axis the bead's
+ *   trilinear stencil must stay within sites 1 .. E-2.
+ */
+int32_t chain_couple(lb_ctx* ctx, int32_t box, const lb_chain_desc* desc, const double* pos0,
+                     const double* vel0);
+
+/*
+ * lb_step -- enqueue nsteps lattice Boltzmann steps for every box.  Each
+ * step n -> n+1: bead coupling (reads the state, moves the chain, records
+ * the force density at <= 8 sites per bead), fused stream-collide of all
+ * sites with the boundary layer set to the equilibrium of the boundary
+ * velocity at t = n+1, re-collision of the forced sites.
+ *   Returns LB_ERR_STATE if a needed boundary sample has not been pushed.
+ */
+int32_t lb_step(lb_ctx* ctx, int32_t nsteps);
+
+/*
+ * lb_graph_capture / lb_graph_launch -- capture nsteps steps into a CUDA
+ * graph owned by the context and replay it.  The graph reads the step
+ * number from device memory, so each replay advances the state by nsteps.
+ */
+int32_t lb_graph_capture(lb_ctx* ctx, int32_t nsteps);
+int32_t lb_graph_launch(lb_ctx* ctx);
+
+/*
+ * lb_read_fields -- observables of one box at the current step.
+ *   LB_FIELD_RHO / LB_FIELD_U: on boundary sites the moments of the stored
+ *   equilibrium; elsewhere the moments of the pulled populations
+ *   f_i(x) = A_i(x - c_i), u = (j + rho a / 2) / rho.
+ *   dst: host or device memory of the size given with the LB_FIELD_* code.
+ *   Synchronising (bounded wait, see lb_sync); returns a pending box error.
+ */
+int32_t lb_read_fields(lb_ctx* ctx, int32_t box, int32_t what, void* dst);
+
+/*
+ * lb_conservation -- FP64 sums over all sites of a box:
+ *   out[0] = sum_x sum_i f_i, out[1..3] = sum_x sum_i c_i f_i,
+ *   out[4..6] = bead momentum m sum_b V_b.   out: host, 7 doubles.
+ *   Synchronising; flags LB_ERR_NONFINITE for a non-finite sum.
+ */
+int32_t lb_conservation(lb_ctx* ctx, int32_t box, double* out);
+
+/* lb_sync -- wait for the context stream at most timeout_ms (LB_ERR_TIMEOUT
+ * after that, the context stays usable) and return the first box error. */
+int32_t lb_sync(lb_ctx* ctx, int32_t timeout_ms);
+
+/* lb_status -- device status word of a box (synchronising), LB_OK if clean. */
+int32_t lb_status(lb_ctx* ctx, int32_t box, int32_t* status);
+
+/* lb_current_step -- number of steps enqueued so far. */
+int64_t lb_current_step(const lb_ctx* ctx);
+
+/* lb_set_launch -- launch shape of the stream-collide kernel: threads per
+ * block (multiple of 32, 64 .. 1024) and a persistent grid of `ctas` blocks
+ * (0 = one block per tile).  Used by the autotuner. */
+int32_t lb_set_launch(lb_ctx* ctx, int32_t threads, int32_t ctas);
+
+/*
+ * lb_profile -- time every stream-collide launch with a pair of CUDA events
+ * recorded on the context stream around it.  enable = 1 starts a new
+ * measurement with room for max_launches launches (later launches are not
+ * timed); enable = 0 stops recording.  lb_profile_read waits for the events
+ * and returns the summed kernel time in milliseconds and the number of timed
+ * launches.  Events are host-side objects; no device memory is used.
+ */
+int32_t lb_profile(lb_ctx* ctx, int32_t enable, int32_t max_launches);
+int32_t lb_profile_read(lb_ctx* ctx, double* total_ms, int64_t* launches);
+
+/* lb_last_error -- message of the last failing call on this context (or of
+ * the last failing lb_plan / lb_create when ctx is NULL). */
+const char* lb_last_error(const lb_ctx* ctx);
+
+/*
+ * Synthetic coarse flow (stands in for the paper's DNS sub-volume record,
+ * Sec. 3: samples around a tracer every 0.05 tau_eta):
+ *   u(x, t) = sum_m amp_m cos(kvec_m . (x - xc) + omega_m t + phi_m),
+ *   xc = ((E-1)/2, (E-1)/2, (E-1)/2).
+ * The mode table (kvec [M][3], amp [M][3], omega [M], phi [M], double,
+ * M <= 3072) is in device memory.  Evaluated in FP64; out_dtype LB_STORE_F64
+ * writes double, LB_STORE_F32 writes float.  workspace: device scratch of at
+ * least lb_synth_workspace_bytes(M, E) bytes for the per-axis phase table.
+ * Enqueued on `stream` (cudaStream_t); no synchronisation.
+ *
+ * lb_synth_faces: samples j0 .. j0+nsamp-1 at t = j K on the six faces,
+ *   out [nsamp][6][3][E][E] (device).
+ * lb_synth_volume: the field on every site at time t, out [3][E^3] (device).
+ */
+size_t lb_synth_workspace_bytes(int32_t M, int32_t E);
+int32_t lb_synth_faces(const double* kvec, const double* amp, const double* omega, const double* phi,
+                       int32_t M, int32_t E, int32_t K, int64_t j0, int64_t nsamp, int32_t out_dtype,
+                       void* out, void* workspace, void* stream);
+int32_t lb_synth_volume(const double* kvec, const double* amp, const double* omega, const double* phi,
+                        int32_t M, int32_t E, double t, int32_t out_dtype, void* out, void* workspace,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBTRACER_H */

@@ -1,0 +1,779 @@
+// C ABI of the tracer-box library (declared in include/lbtracer.h).
+//
+// Host-side bookkeeping only: arena layout, box and chain tables, the ring of
+// coarse boundary samples, step ordering and launches.  All arithmetic of the
+// method runs in the kernels of lbt_kernels.cuh and lbt_synth.cu.
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "lbt_internal.h"
+
+using namespace lbt;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
+
+size_t elem_bytes(int storage) { return storage == kF64 ? 8 : (storage == kF32 ? 4 : 2); }
+size_t real_bytes(int storage) { return storage == kF64 ? 8 : 4; }
+
+int validate_boxes(const lb_box_desc* boxes, int nboxes, int storage, std::string& why)
+{
+    if (!boxes || nboxes <= 0) {
+        why = "no boxes";
+        return LB_ERR_ARG;
+    }
+    if (storage < LB_STORE_F64 || storage > LB_STORE_BF16DEV) {
+        why = "unknown storage";
+        return LB_ERR_ARG;
+    }
+    for (int b = 0; b < nboxes; b++) {
+        const lb_box_desc& d = boxes[b];
+        char buf[160];
+        if (d.E < 8 || d.E > 1024 || d.E % 8) {
+            snprintf(buf, sizeof buf, "box %d: E=%d must be a multiple of 8 in [8, 1024]", b, d.E);
+            why = buf;
+            return LB_ERR_ARG;
+        }
+        if (!(d.tau > 0.5)) {
+            snprintf(buf, sizeof buf, "box %d: tau=%g must exceed 1/2", b, d.tau);
+            why = buf;
+            return LB_ERR_ARG;
+        }
+        for (int a = 0; a < 3; a++) {
+            const int m0 = d.face_mode[2 * a], m1 = d.face_mode[2 * a + 1];
+            if (m0 != m1 || (m0 != LB_FACE_VELOCITY && m0 != LB_FACE_PERIODIC)) {
+                snprintf(buf, sizeof buf, "box %d: faces of axis %d must both be VELOCITY or both PERIODIC", b, a);
+                why = buf;
+                return LB_ERR_ARG;
+            }
+        }
+        if (d.time_interp != LB_TIME_LINEAR && d.time_interp != LB_TIME_HERMITE) {
+            snprintf(buf, sizeof buf, "box %d: time_interp %d not available", b, d.time_interp);
+            why = buf;
+            return LB_ERR_ARG;
+        }
+        if (d.K < 1 || d.nbeads < 0 || d.nbeads > kMaxBeads || !(d.rho_b > 0.0)) {
+            snprintf(buf, sizeof buf, "box %d: need K >= 1, 0 <= nbeads <= %d, rho_b > 0", b, kMaxBeads);
+            why = buf;
+            return LB_ERR_ARG;
+        }
+    }
+    return LB_OK;
+}
+
+Layout plan_layout(const lb_box_desc* boxes, int nboxes, int storage)
+{
+    Layout L{};
+    size_t off = 0;
+    L.boxes = off;
+    off = align_up(off + sizeof(BoxDev) * nboxes);
+    L.tile_prefix = off;
+    off = align_up(off + sizeof(int64_t) * (nboxes + 1));
+    L.chains = off;
+    off = align_up(off + sizeof(ChainDev) * nboxes);
+    size_t pop = 0, ring = 0;
+    int64_t beads = 0, chunks = 1;
+    for (int b = 0; b < nboxes; b++) {
+        const int64_t E = boxes[b].E, n3 = E * E * E;
+        pop = align_up(pop + 19 * n3 * elem_bytes(storage));
+        ring += align_up(6 * 3 * E * E * real_bytes(storage)) / real_bytes(storage);
+        beads += boxes[b].nbeads;
+        const int64_t c = (n3 + 4095) / 4096;
+        if (c > chunks) chunks = c;
+    }
+    L.pop_bytes = pop;
+    L.ring_slot_elems = ring;
+    L.total_beads = beads;
+    L.cons_chunks = chunks;
+    L.pop_a = off;
+    off = align_up(off + pop);
+    L.pop_b = off;
+    off = align_up(off + pop);
+    L.ring = off;
+    off = align_up(off + kRingSlots * ring * real_bytes(storage));
+    L.pos = off;
+    off = align_up(off + sizeof(double) * 3 * (beads + 1));
+    L.vel = off;
+    off = align_up(off + sizeof(double) * 3 * (beads + 1));
+    L.forces = off;
+    off = align_up(off + sizeof(ForceEntry) * 8 * (beads + 1));
+    L.cons_partial = off;
+    off = align_up(off + sizeof(double) * 4 * nboxes * chunks);
+    L.cons_out = off;
+    off = align_up(off + sizeof(double) * 8 * nboxes);
+    L.status = off;
+    off = align_up(off + sizeof(int32_t) * nboxes);
+    L.step = off;
+    off = align_up(off + sizeof(int64_t));
+    L.total = off;
+    return L;
+}
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct lb_ctx {
+    int storage = 0;
+    int nboxes = 0;
+    std::vector<lb_box_desc> desc;
+    std::vector<BoxDev> boxes;
+    std::vector<ChainDev> chains;      // one per box with nbeads > 0
+    Layout L{};
+    char* arena = nullptr;
+    cudaStream_t stream = nullptr, side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool a_is_pop_a = true;            // which buffer holds the current state
+    int64_t step = 0;                  // steps enqueued so far
+    std::vector<int64_t> pushed;       // last boundary sample pushed per box (-1 none)
+    int threads = 256, ctas = 0;
+    std::vector<int64_t> tile_prefix;  // for the current block size
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    bool graph_parity = true;
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_ev;  // pairs around stream-collide launches
+    size_t prof_used = 0;
+    std::string err;
+
+    template <class T>
+    T* at(size_t off) const { return reinterpret_cast<T*>(arena + off); }
+    void* curA() const { return arena + (a_is_pop_a ? L.pop_a : L.pop_b); }
+    void* curB() const { return arena + (a_is_pop_a ? L.pop_b : L.pop_a); }
+    bool has_velocity_faces(int b) const { return boxes[b].per_mask != 7; }
+    int fail(int code, const std::string& msg)
+    {
+        err = msg;
+        g_last_error = msg;
+        return code;
+    }
+    int cuda_fail(cudaError_t e, const char* where)
+    {
+        return fail(LB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    }
+};
+
+#define CK(call)                                             \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return ctx->cuda_fail(e_, #call); \
+    } while (0)
+
+namespace {
+
+#define DISPATCH(storage, expr)                          \
+    ((storage) == kF64   ? Launch<kF64>::expr            \
+     : (storage) == kF32 ? Launch<kF32>::expr            \
+     : (storage) == kF16 ? Launch<kF16>::expr            \
+                         : Launch<kBF16>::expr)
+
+int rebuild_tiles(lb_ctx* ctx)
+{
+    const int vw = ctx->storage == kF64 ? 2 : (ctx->storage == kF32 ? 4 : 8);
+    ctx->tile_prefix.assign(ctx->nboxes + 1, 0);
+    for (int b = 0; b < ctx->nboxes; b++) {
+        const int64_t groups = ctx->boxes[b].n3 / vw;
+        ctx->tile_prefix[b + 1] = ctx->tile_prefix[b] + (groups + ctx->threads - 1) / ctx->threads;
+    }
+    CK(cudaMemcpyAsync(ctx->at<int64_t>(ctx->L.tile_prefix), ctx->tile_prefix.data(),
+                       sizeof(int64_t) * (ctx->nboxes + 1), cudaMemcpyHostToDevice, ctx->stream));
+    // the host vector must outlive the copy: synchronise (set-up path only)
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LB_OK;
+}
+
+// Samples box b needs for the step that starts at step n.
+void needed_samples(const lb_ctx* ctx, int b, int64_t n, int64_t& lo, int64_t& hi)
+{
+    const lb_box_desc& d = ctx->desc[b];
+    const int64_t j = n / d.K;
+    if (d.time_interp == LB_TIME_LINEAR) {
+        lo = j;
+        hi = j + 1;
+    } else {
+        lo = j > 0 ? j - 1 : 0;
+        hi = j + 2;
+    }
+}
+
+int check_samples(lb_ctx* ctx, int64_t n0, int64_t nsteps)
+{
+    for (int b = 0; b < ctx->nboxes; b++) {
+        if (!ctx->has_velocity_faces(b)) continue;
+        int64_t lo, hi;
+        needed_samples(ctx, b, n0 + nsteps - 1, lo, hi);
+        if (ctx->pushed[b] < hi) {
+            char buf[200];
+            snprintf(buf, sizeof buf, "box %d: step %lld needs boundary sample %lld, last pushed %lld", b,
+                     (long long)(n0 + nsteps - 1), (long long)hi, (long long)ctx->pushed[b]);
+            return ctx->fail(LB_ERR_STATE, buf);
+        }
+        int64_t lo0, hi0;
+        needed_samples(ctx, b, n0, lo0, hi0);
+        if (ctx->pushed[b] - kRingSlots >= lo0) {
+            char buf[200];
+            snprintf(buf, sizeof buf, "box %d: sample %lld was overwritten before step %lld", b, (long long)lo0,
+                     (long long)n0);
+            return ctx->fail(LB_ERR_STATE, buf);
+        }
+    }
+    return LB_OK;
+}
+
+// Enqueue one step n -> n+1 for every box; swaps the buffers.
+int enqueue_step(lb_ctx* ctx)
+{
+    const int nch = (int)ctx->chains.size();
+    void* A = ctx->curA();
+    void* B = ctx->curB();
+    if (nch > 0) {
+        CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+        CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+        BeadParams bp;
+        bp.A = A;
+        bp.boxes = ctx->at<BoxDev>(ctx->L.boxes);
+        bp.chains = ctx->at<ChainDev>(ctx->L.chains);
+        bp.pos = ctx->at<double>(ctx->L.pos);
+        bp.vel = ctx->at<double>(ctx->L.vel);
+        bp.forces = ctx->at<ForceEntry>(ctx->L.forces);
+        bp.step = ctx->at<int64_t>(ctx->L.step);
+        bp.status = ctx->at<int32_t>(ctx->L.status);
+        CK(DISPATCH(ctx->storage, bead_couple(bp, nch, ctx->side)));
+        CK(cudaEventRecord(ctx->ev_join, ctx->side));
+    }
+    SCParams sp;
+    sp.A = A;
+    sp.B = B;
+    sp.ring = ctx->arena + ctx->L.ring;
+    sp.ring_slot_elems = (int64_t)ctx->L.ring_slot_elems;
+    sp.boxes = ctx->at<BoxDev>(ctx->L.boxes);
+    sp.tile_prefix = ctx->at<int64_t>(ctx->L.tile_prefix);
+    sp.nboxes = ctx->nboxes;
+    sp.total_tiles = ctx->tile_prefix[ctx->nboxes];
+    sp.step = ctx->at<int64_t>(ctx->L.step);
+    sp.status = ctx->at<int32_t>(ctx->L.status);
+    const bool timed = ctx->profiling && ctx->prof_used + 2 <= ctx->prof_ev.size();
+    if (timed) CK(cudaEventRecord(ctx->prof_ev[ctx->prof_used], ctx->stream));
+    CK(DISPATCH(ctx->storage, stream_collide(sp, ctx->threads, ctx->ctas, ctx->stream)));
+    if (timed) {
+        CK(cudaEventRecord(ctx->prof_ev[ctx->prof_used + 1], ctx->stream));
+        ctx->prof_used += 2;
+    }
+    if (nch > 0) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+    ForcedParams fp;
+    fp.A = A;
+    fp.B = B;
+    fp.boxes = ctx->at<BoxDev>(ctx->L.boxes);
+    fp.chains = ctx->at<ChainDev>(ctx->L.chains);
+    fp.forces = ctx->at<ForceEntry>(ctx->L.forces);
+    fp.status = ctx->at<int32_t>(ctx->L.status);
+    fp.step = ctx->at<int64_t>(ctx->L.step);
+    fp.nchains = nch;
+    CK(DISPATCH(ctx->storage, forced(fp, ctx->stream)));
+    ctx->a_is_pop_a = !ctx->a_is_pop_a;
+    return LB_OK;
+}
+
+int wait_stream(lb_ctx* ctx, int timeout_ms)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    while (true) {
+        cudaError_t e = cudaStreamQuery(ctx->stream);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return ctx->cuda_fail(e, "cudaStreamQuery");
+        const auto ms =
+            std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+        if (timeout_ms >= 0 && ms > timeout_ms) return ctx->fail(LB_ERR_TIMEOUT, "stream wait timed out");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    return LB_OK;
+}
+
+int first_status(lb_ctx* ctx, int box)
+{
+    std::vector<int32_t> st(ctx->nboxes);
+    CK(cudaMemcpyAsync(st.data(), ctx->at<int32_t>(ctx->L.status), sizeof(int32_t) * ctx->nboxes,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int b = 0; b < ctx->nboxes; b++) {
+        if ((box < 0 || box == b) && st[b] != 0) {
+            char buf[96];
+            snprintf(buf, sizeof buf, "box %d has status %d", b, st[b]);
+            return ctx->fail(st[b], buf);
+        }
+    }
+    return LB_OK;
+}
+
+constexpr int kDefaultTimeoutMs = 120000;
+
+}  // namespace
+
+extern "C" {
+
+int32_t lb_plan(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, size_t* arena_bytes)
+{
+    std::string why;
+    int st = validate_boxes(boxes, nboxes, storage, why);
+    if (st) {
+        g_last_error = why;
+        return st;
+    }
+    if (!arena_bytes) {
+        g_last_error = "null arena_bytes";
+        return LB_ERR_ARG;
+    }
+    *arena_bytes = plan_layout(boxes, nboxes, storage).total;
+    return LB_OK;
+}
+
+int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, void* arena, size_t arena_bytes,
+                  void* stream, lb_ctx** out)
+{
+    std::string why;
+    int st = validate_boxes(boxes, nboxes, storage, why);
+    if (st) {
+        g_last_error = why;
+        return st;
+    }
+    if (!out || !arena) {
+        g_last_error = "null arena or out";
+        return LB_ERR_ARG;
+    }
+    Layout L = plan_layout(boxes, nboxes, storage);
+    if (arena_bytes < L.total) {
+        g_last_error = "arena smaller than lb_plan size";
+        return LB_ERR_SIZE;
+    }
+    if (reinterpret_cast<uintptr_t>(arena) % kAlign) {
+        g_last_error = "arena must be 256-byte aligned";
+        return LB_ERR_ARG;
+    }
+    lb_ctx* ctx = new lb_ctx();
+    ctx->storage = storage;
+    ctx->nboxes = nboxes;
+    ctx->desc.assign(boxes, boxes + nboxes);
+    ctx->L = L;
+    ctx->arena = reinterpret_cast<char*>(arena);
+    ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+    ctx->pushed.assign(nboxes, -1);
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        g_last_error = std::string("stream/event creation: ") + cudaGetErrorString(e);
+        lb_destroy(ctx);
+        return LB_ERR_CUDA;
+    }
+    // box and chain tables
+    size_t pop = 0, ring = 0;
+    int64_t beads = 0;
+    for (int b = 0; b < nboxes; b++) {
+        const lb_box_desc& d = boxes[b];
+        BoxDev bd{};
+        const int64_t E = d.E, n3 = E * E * E;
+        bd.f_off = (int64_t)(pop / elem_bytes(storage));
+        bd.n3 = n3;
+        bd.ring_off = (int64_t)ring;
+        bd.E = d.E;
+        bd.per_mask = (d.face_mode[0] == LB_FACE_PERIODIC ? 1 : 0) | (d.face_mode[2] == LB_FACE_PERIODIC ? 2 : 0) |
+                      (d.face_mode[4] == LB_FACE_PERIODIC ? 4 : 0);
+        bd.time_interp = d.time_interp;
+        bd.K = d.K;
+        bd.chain = -1;
+        bd.tau = d.tau;
+        bd.rho_b = d.rho_b;
+        for (int a = 0; a < 3; a++) bd.accel[a] = d.body_accel[a];
+        bd.has_accel = (d.body_accel[0] != 0.0 || d.body_accel[1] != 0.0 || d.body_accel[2] != 0.0) ? 1 : 0;
+        if (d.nbeads > 0) {
+            ChainDev ch{};
+            ch.box = b;
+            ch.nbeads = 0;
+            ch.n_md = 1;
+            ch.bead_off = beads;
+            ch.force_off = 8 * beads;
+            ch.mass = 1.0;
+            bd.chain = (int)ctx->chains.size();
+            ctx->chains.push_back(ch);
+            beads += d.nbeads;
+        }
+        ctx->boxes.push_back(bd);
+        pop = align_up(pop + 19 * n3 * elem_bytes(storage));
+        ring += align_up(6 * 3 * E * E * real_bytes(storage)) / real_bytes(storage);
+    }
+    // zero the whole arena once (ring, status, step counter, force lists ...)
+    e = cudaMemsetAsync(arena, 0, L.total, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->at<BoxDev>(L.boxes), ctx->boxes.data(), sizeof(BoxDev) * nboxes,
+                            cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && !ctx->chains.empty())
+        e = cudaMemcpyAsync(ctx->at<ChainDev>(L.chains), ctx->chains.data(), sizeof(ChainDev) * ctx->chains.size(),
+                            cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        g_last_error = std::string("arena set-up: ") + cudaGetErrorString(e);
+        lb_destroy(ctx);
+        return LB_ERR_CUDA;
+    }
+    if (rebuild_tiles(ctx) != LB_OK) {
+        g_last_error = ctx->err;
+        lb_destroy(ctx);
+        return LB_ERR_CUDA;
+    }
+    *out = ctx;
+    return LB_OK;
+}
+
+int32_t lb_destroy(lb_ctx* ctx)
+{
+    if (!ctx) return LB_OK;
+    if (ctx->side) {
+        wait_stream(ctx, kDefaultTimeoutMs);
+        cudaStreamSynchronize(ctx->side);
+    }
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    for (cudaEvent_t ev : ctx->prof_ev) cudaEventDestroy(ev);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    delete ctx;
+    return LB_OK;
+}
+
+int32_t lb_init(lb_ctx* ctx, int32_t box, const void* u0)
+{
+    if (!ctx || !u0) return LB_ERR_ARG;
+    if (box == LB_ALL_BOXES) {
+        if (ctx->nboxes != 1) return ctx->fail(LB_ERR_ARG, "lb_init with all boxes needs one u0 per box; call per box");
+        box = 0;
+    }
+    if (box < 0 || box >= ctx->nboxes) return ctx->fail(LB_ERR_ARG, "box index out of range");
+    if (ctx->nboxes > 1 && ctx->step > 0)
+        return ctx->fail(LB_ERR_STATE, "boxes of a multi-box context are initialised before the first step");
+    const BoxDev& bd = ctx->boxes[box];
+    const size_t eb = elem_bytes(ctx->storage), rb = real_bytes(ctx->storage);
+    void* A = reinterpret_cast<char*>(ctx->curA()) + bd.f_off * eb;
+    const void* src = u0;
+    if (!is_device_ptr(u0)) {
+        void* stage = reinterpret_cast<char*>(ctx->curB()) + bd.f_off * eb;
+        CK(cudaMemcpyAsync(stage, u0, 3 * bd.n3 * rb, cudaMemcpyHostToDevice, ctx->stream));
+        src = stage;
+    }
+    CK(DISPATCH(ctx->storage, init(A, ctx->boxes.data(), box, bd.n3, src, ctx->stream)));
+    CK(cudaMemsetAsync(ctx->at<int32_t>(ctx->L.status) + box, 0, sizeof(int32_t), ctx->stream));
+    if (ctx->nboxes == 1) {
+        ctx->step = 0;
+        CK(cudaMemsetAsync(ctx->at<int64_t>(ctx->L.step), 0, sizeof(int64_t), ctx->stream));
+        ctx->pushed.assign(ctx->nboxes, -1);
+    }
+    return LB_OK;
+}
+
+int32_t lb_set_boundary(lb_ctx* ctx, int32_t box, int64_t j, const void* face_u)
+{
+    if (!ctx || !face_u) return LB_ERR_ARG;
+    const size_t rb = real_bytes(ctx->storage);
+    const int b0 = box == LB_ALL_BOXES ? 0 : box;
+    const int b1 = box == LB_ALL_BOXES ? ctx->nboxes : box + 1;
+    if (b0 < 0 || b1 > ctx->nboxes || b0 >= b1) return ctx->fail(LB_ERR_ARG, "box index out of range");
+    for (int b = b0; b < b1; b++) {
+        if (j != ctx->pushed[b] + 1) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "box %d: boundary samples must be pushed in order (expected %lld, got %lld)", b,
+                     (long long)(ctx->pushed[b] + 1), (long long)j);
+            return ctx->fail(LB_ERR_STATE, buf);
+        }
+        int64_t lo, hi;
+        needed_samples(ctx, b, ctx->step, lo, hi);
+        if (j - kRingSlots >= lo && j >= kRingSlots) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "box %d: sample %lld would overwrite sample %lld still needed at step %lld", b,
+                     (long long)j, (long long)(j - kRingSlots), (long long)ctx->step);
+            return ctx->fail(LB_ERR_STATE, buf);
+        }
+    }
+    char* slot = ctx->arena + ctx->L.ring + (size_t)(j % kRingSlots) * ctx->L.ring_slot_elems * rb;
+    const char* src = reinterpret_cast<const char*>(face_u);
+    for (int b = b0; b < b1; b++) {
+        const int64_t E = ctx->boxes[b].E;
+        const size_t bytes = 6 * 3 * E * E * rb;
+        CK(cudaMemcpyAsync(slot + ctx->boxes[b].ring_off * rb, src, bytes, cudaMemcpyDefault, ctx->stream));
+        src += bytes;
+        ctx->pushed[b] = j;
+    }
+    return LB_OK;
+}
+
+int32_t chain_couple(lb_ctx* ctx, int32_t box, const lb_chain_desc* d, const double* pos0, const double* vel0)
+{
+    if (!ctx || !d || !pos0) return LB_ERR_ARG;
+    if (box < 0 || box >= ctx->nboxes) return ctx->fail(LB_ERR_ARG, "box index out of range");
+    const int ci = ctx->boxes[box].chain;
+    if (ci < 0) return ctx->fail(LB_ERR_ARG, "box was planned without chain capacity (nbeads = 0)");
+    if (d->nbeads < 1 || d->nbeads > ctx->desc[box].nbeads || d->n_md < 1 || !(d->mass > 0) || d->kT < 0 ||
+        !(d->R0 > 0) || d->zeta < 0 || d->pin_com < 0 || d->pin_com > 2)
+        return ctx->fail(LB_ERR_ARG, "invalid chain description");
+    ChainDev& ch = ctx->chains[ci];
+    ch.nbeads = d->nbeads;
+    ch.n_md = d->n_md;
+    ch.pin_com = d->pin_com;
+    ch.k_fene = d->k_fene;
+    ch.R0 = d->R0;
+    ch.zeta = d->zeta;
+    ch.mass = d->mass;
+    ch.kT = d->kT;
+    for (int a = 0; a < 3; a++) ch.f_ext[a] = d->f_ext[a];
+    ch.seed = d->seed;
+    const size_t bytes = sizeof(double) * 3 * d->nbeads;
+    CK(cudaMemcpyAsync(ctx->at<double>(ctx->L.pos) + 3 * ch.bead_off, pos0, bytes, cudaMemcpyDefault, ctx->stream));
+    if (vel0)
+        CK(cudaMemcpyAsync(ctx->at<double>(ctx->L.vel) + 3 * ch.bead_off, vel0, bytes, cudaMemcpyDefault, ctx->stream));
+    else
+        CK(cudaMemsetAsync(ctx->at<double>(ctx->L.vel) + 3 * ch.bead_off, 0, bytes, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->at<ChainDev>(ctx->L.chains) + ci, &ch, sizeof(ChainDev), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));  // the host copies above must not outlive this call
+    return LB_OK;
+}
+
+int32_t lb_step(lb_ctx* ctx, int32_t nsteps)
+{
+    if (!ctx || nsteps < 0) return LB_ERR_ARG;
+    if (nsteps == 0) return LB_OK;
+    int st = check_samples(ctx, ctx->step, nsteps);
+    if (st) return st;
+    for (int k = 0; k < nsteps; k++) {
+        st = enqueue_step(ctx);
+        if (st) return st;
+        ctx->step++;
+    }
+    return LB_OK;
+}
+
+int32_t lb_graph_capture(lb_ctx* ctx, int32_t nsteps)
+{
+    if (!ctx || nsteps <= 0 || nsteps % 2) return ctx ? ctx->fail(LB_ERR_ARG, "graph needs an even step count") : LB_ERR_ARG;
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    const bool parity = ctx->a_is_pop_a;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    int st = LB_OK;
+    for (int k = 0; k < nsteps && st == LB_OK; k++) st = enqueue_step(ctx);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    ctx->a_is_pop_a = parity;
+    if (st) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaGraphInstantiate");
+    ctx->graph_steps = nsteps;
+    ctx->graph_parity = parity;
+    return LB_OK;
+}
+
+int32_t lb_graph_launch(lb_ctx* ctx)
+{
+    if (!ctx || !ctx->graph) return ctx ? ctx->fail(LB_ERR_STATE, "no captured graph") : LB_ERR_ARG;
+    if (ctx->a_is_pop_a != ctx->graph_parity) return ctx->fail(LB_ERR_STATE, "buffer parity differs from capture");
+    int st = check_samples(ctx, ctx->step, ctx->graph_steps);
+    if (st) return st;
+    CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+    ctx->step += ctx->graph_steps;
+    return LB_OK;
+}
+
+int32_t lb_read_fields(lb_ctx* ctx, int32_t box, int32_t what, void* dst)
+{
+    if (!ctx || !dst) return LB_ERR_ARG;
+    const bool async = (what & LB_FIELD_ASYNC) != 0;
+    what &= ~LB_FIELD_ASYNC;
+    if (async && what == LB_FIELD_DEV && ctx->storage >= kF16 && !is_device_ptr(dst))
+        return ctx->fail(LB_ERR_ARG, "asynchronous 16-bit population read-out needs a device destination");
+    if (box < 0 || box >= ctx->nboxes) return ctx->fail(LB_ERR_ARG, "box index out of range");
+    const BoxDev& bd = ctx->boxes[box];
+    const size_t eb = elem_bytes(ctx->storage), rb = real_bytes(ctx->storage);
+    const bool dev = is_device_ptr(dst);
+    const void* A = reinterpret_cast<const char*>(ctx->curA()) + bd.f_off * eb;
+    if (what == LB_FIELD_CHAIN) {
+        if (bd.chain < 0) return ctx->fail(LB_ERR_ARG, "box has no chain");
+        const ChainDev& ch = ctx->chains[bd.chain];
+        const size_t bytes = sizeof(double) * 3 * ch.nbeads;
+        CK(cudaMemcpyAsync(dst, ctx->at<double>(ctx->L.pos) + 3 * ch.bead_off, bytes, cudaMemcpyDefault, ctx->stream));
+        CK(cudaMemcpyAsync(reinterpret_cast<char*>(dst) + bytes, ctx->at<double>(ctx->L.vel) + 3 * ch.bead_off, bytes,
+                           cudaMemcpyDefault, ctx->stream));
+    } else if (what == LB_FIELD_RHO || what == LB_FIELD_U) {
+        const size_t bytes = (what == LB_FIELD_RHO ? 1 : 3) * bd.n3 * rb;
+        void* out = dev ? dst : reinterpret_cast<char*>(ctx->curB()) + bd.f_off * eb;  // staging in the free buffer
+        CK(DISPATCH(ctx->storage, fields(A, ctx->boxes.data(), box, bd.n3, what == LB_FIELD_RHO ? 0 : 1, out, ctx->stream)));
+        if (!dev) CK(cudaMemcpyAsync(dst, out, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    } else if (what == LB_FIELD_DEV) {
+        if (dev) {
+            CK(DISPATCH(ctx->storage, read_dev(A, 19 * bd.n3, dst, ctx->stream)));
+        } else if (ctx->storage == kF64 || ctx->storage == kF32) {
+            CK(cudaMemcpyAsync(dst, A, 19 * bd.n3 * eb, cudaMemcpyDeviceToHost, ctx->stream));
+        } else {
+            // 16-bit storage: widen to float through the free buffer, 8 populations at a time
+            char* stage = reinterpret_cast<char*>(ctx->curB()) + bd.f_off * eb;
+            for (int i0 = 0; i0 < 19; i0 += 8) {
+                const int ni = i0 + 8 <= 19 ? 8 : 19 - i0;
+                const void* Ai = reinterpret_cast<const char*>(A) + (size_t)i0 * bd.n3 * eb;
+                CK(DISPATCH(ctx->storage, read_dev(Ai, (int64_t)ni * bd.n3, stage, ctx->stream)));
+                CK(cudaMemcpyAsync(reinterpret_cast<char*>(dst) + (size_t)i0 * bd.n3 * rb, stage, ni * bd.n3 * rb,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+                CK(cudaStreamSynchronize(ctx->stream));
+            }
+        }
+    } else {
+        return ctx->fail(LB_ERR_ARG, "unknown field");
+    }
+    if (async) return LB_OK;
+    int st = wait_stream(ctx, kDefaultTimeoutMs);
+    if (st) return st;
+    return first_status(ctx, box);
+}
+
+int32_t lb_conservation(lb_ctx* ctx, int32_t box, double* out)
+{
+    if (!ctx || !out) return LB_ERR_ARG;
+    if (box < 0 || box >= ctx->nboxes) return ctx->fail(LB_ERR_ARG, "box index out of range");
+    CK(DISPATCH(ctx->storage,
+                conservation(ctx->curA(), ctx->at<BoxDev>(ctx->L.boxes), ctx->at<ChainDev>(ctx->L.chains),
+                             ctx->nboxes, ctx->L.cons_chunks, ctx->at<double>(ctx->L.vel),
+                             ctx->at<double>(ctx->L.cons_partial), ctx->at<double>(ctx->L.cons_out),
+                             ctx->at<int32_t>(ctx->L.status), ctx->stream)));
+    double tmp[8];
+    CK(cudaMemcpyAsync(tmp, ctx->at<double>(ctx->L.cons_out) + 8 * box, sizeof tmp, cudaMemcpyDeviceToHost, ctx->stream));
+    int st = wait_stream(ctx, kDefaultTimeoutMs);
+    if (st) return st;
+    memcpy(out, tmp, 7 * sizeof(double));
+    return first_status(ctx, box);
+}
+
+int32_t lb_sync(lb_ctx* ctx, int32_t timeout_ms)
+{
+    if (!ctx) return LB_ERR_ARG;
+    int st = wait_stream(ctx, timeout_ms);
+    if (st) return st;
+    return first_status(ctx, -1);
+}
+
+int32_t lb_status(lb_ctx* ctx, int32_t box, int32_t* status)
+{
+    if (!ctx || !status || box < 0 || box >= ctx->nboxes) return LB_ERR_ARG;
+    int st = wait_stream(ctx, kDefaultTimeoutMs);
+    if (st) return st;
+    CK(cudaMemcpyAsync(status, ctx->at<int32_t>(ctx->L.status) + box, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LB_OK;
+}
+
+int64_t lb_current_step(const lb_ctx* ctx) { return ctx ? ctx->step : -1; }
+
+int32_t lb_set_launch(lb_ctx* ctx, int32_t threads, int32_t ctas)
+{
+    if (!ctx) return LB_ERR_ARG;
+    if (threads < 64 || threads > 256 || threads % 32 || ctas < 0)
+        return ctx->fail(LB_ERR_ARG, "threads must be a multiple of 32 in [64, 256], ctas >= 0");
+    ctx->threads = threads;
+    ctx->ctas = ctas;
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    return rebuild_tiles(ctx);
+}
+
+int32_t lb_profile(lb_ctx* ctx, int32_t enable, int32_t max_launches)
+{
+    if (!ctx || max_launches < 0) return LB_ERR_ARG;
+    if (!enable) {
+        ctx->profiling = false;
+        return LB_OK;
+    }
+    for (cudaEvent_t ev : ctx->prof_ev) cudaEventDestroy(ev);
+    ctx->prof_ev.assign(2 * (size_t)max_launches, nullptr);
+    for (auto& ev : ctx->prof_ev) CK(cudaEventCreate(&ev));
+    ctx->prof_used = 0;
+    ctx->profiling = true;
+    return LB_OK;
+}
+
+int32_t lb_profile_read(lb_ctx* ctx, double* total_ms, int64_t* launches)
+{
+    if (!ctx || !total_ms || !launches) return LB_ERR_ARG;
+    int st = wait_stream(ctx, kDefaultTimeoutMs);
+    if (st) return st;
+    double sum = 0.0;
+    for (size_t k = 0; k + 1 < ctx->prof_used; k += 2) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->prof_ev[k], ctx->prof_ev[k + 1]));
+        sum += ms;
+    }
+    *total_ms = sum;
+    *launches = (int64_t)(ctx->prof_used / 2);
+    return LB_OK;
+}
+
+const char* lb_last_error(const lb_ctx* ctx) { return ctx ? ctx->err.c_str() : g_last_error.c_str(); }
+
+size_t lb_synth_workspace_bytes(int32_t M, int32_t E) { return sizeof(double2) * 3 * (size_t)M * (size_t)E; }
+
+int32_t lb_synth_faces(const double* kvec, const double* amp, const double* omega, const double* phi, int32_t M,
+                       int32_t E, int32_t K, int64_t j0, int64_t nsamp, int32_t out_dtype, void* out, void* workspace,
+                       void* stream)
+{
+    if (!kvec || !amp || !omega || !phi || !out || !workspace || M < 1 || E < 2 || K < 1 || nsamp < 0 ||
+        (out_dtype != LB_STORE_F64 && out_dtype != LB_STORE_F32)) {
+        g_last_error = "lb_synth_faces: bad argument";
+        return LB_ERR_ARG;
+    }
+    cudaError_t e = launch_synth_faces(kvec, amp, omega, phi, M, E, K, j0, nsamp, out_dtype == LB_STORE_F64, out,
+                                       workspace, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        g_last_error = std::string("lb_synth_faces: ") + cudaGetErrorString(e);
+        return e == cudaErrorInvalidValue ? LB_ERR_ARG : LB_ERR_CUDA;
+    }
+    return LB_OK;
+}
+
+int32_t lb_synth_volume(const double* kvec, const double* amp, const double* omega, const double* phi, int32_t M,
+                        int32_t E, double t, int32_t out_dtype, void* out, void* workspace, void* stream)
+{
+    if (!kvec || !amp || !omega || !phi || !out || !workspace || M < 1 || E < 2 ||
+        (out_dtype != LB_STORE_F64 && out_dtype != LB_STORE_F32)) {
+        g_last_error = "lb_synth_volume: bad argument";
+        return LB_ERR_ARG;
+    }
+    cudaError_t e = launch_synth_volume(kvec, amp, omega, phi, M, E, t, out_dtype == LB_STORE_F64, out, workspace,
+                                        reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        g_last_error = std::string("lb_synth_volume: ") + cudaGetErrorString(e);
+        return e == cudaErrorInvalidValue ? LB_ERR_ARG : LB_ERR_CUDA;
+    }
+    return LB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,225 @@
+// Device helpers: D3Q19 constants, population storage formats, Philox4x64-10.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+
+#include "lbt_internal.h"
+
+namespace lbt {
+
+// D3Q19 velocity set: rest, +-x, +-y, +-z, then the 12 edge vectors in
+// opposite pairs.  Indices are compile-time after unrolling, so these fold
+// into immediates.
+__host__ __device__ constexpr int cvec(int i, int a)
+{
+    constexpr int c[kQ][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
+                              {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                              {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                              {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    return c[i][a];
+}
+
+template <class T>
+__host__ __device__ constexpr T wgt(int i)
+{
+    return i == 0 ? T(1) / T(3) : (i < 7 ? T(1) / T(18) : T(1) / T(36));
+}
+
+// ---- storage formats -------------------------------------------------------
+// Every format stores the deviation d_i = f_i - w_i.  E: stored element type,
+// A: arithmetic type, R: type of boundary samples and of field read-outs.
+template <int ST>
+struct Stor;
+
+template <>
+struct Stor<kF64> {
+    using E = double;
+    using A = double;
+    using R = double;
+    static __device__ __forceinline__ A in(E v) { return v; }
+    static __device__ __forceinline__ E out(A v) { return v; }
+};
+
+template <>
+struct Stor<kF32> {
+    using E = float;
+    using A = float;
+    using R = float;
+    static __device__ __forceinline__ A in(E v) { return v; }
+    static __device__ __forceinline__ E out(A v) { return v; }
+};
+
+template <>
+struct Stor<kF16> {
+    using E = uint16_t;
+    using A = float;
+    using R = float;
+    static __device__ __forceinline__ A in(E v) { return __half2float(__ushort_as_half(v)); }
+    static __device__ __forceinline__ E out(A v) { return __half_as_ushort(__float2half_rn(v)); }
+};
+
+template <>
+struct Stor<kBF16> {
+    using E = uint16_t;
+    using A = float;
+    using R = float;
+    static __device__ __forceinline__ A in(E v) { return __bfloat162float(__ushort_as_bfloat16(v)); }
+    static __device__ __forceinline__ E out(A v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+};
+
+// A vector of VW consecutive stored elements moved with one load/store.
+template <int BYTES>
+struct RawOf;
+template <>
+struct RawOf<16> {
+    using T = uint4;
+};
+template <>
+struct RawOf<8> {
+    using T = uint2;
+};
+template <>
+struct RawOf<4> {
+    using T = unsigned int;
+};
+template <>
+struct RawOf<2> {
+    using T = unsigned short;
+};
+
+template <class E, int VW>
+struct Pack {
+    using Raw = typename RawOf<sizeof(E) * VW>::T;
+    union {
+        Raw raw;
+        E e[VW];
+    };
+};
+
+template <class Raw>
+__device__ __forceinline__ Raw ld_nc(const Raw* p)
+{
+    return __ldg(p);
+}
+template <>
+__device__ __forceinline__ unsigned short ld_nc<unsigned short>(const unsigned short* p)
+{
+    return __ldg(p);
+}
+
+template <class Raw>
+__device__ __forceinline__ Raw zero_raw()
+{
+    Raw r;
+    memset(&r, 0, sizeof(Raw));
+    return r;
+}
+
+// ---- Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) ----------------------
+__device__ __forceinline__ void philox4x64_10(uint64_t x[4], uint64_t k0, uint64_t k1)
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        uint64_t hi0 = __umul64hi(M0, x[0]), lo0 = M0 * x[0];
+        uint64_t hi1 = __umul64hi(M1, x[2]), lo1 = M1 * x[2];
+        uint64_t y0 = hi1 ^ x[1] ^ k0, y2 = hi0 ^ x[3] ^ k1;
+        x[0] = y0;
+        x[1] = lo1;
+        x[2] = y2;
+        x[3] = lo0;
+    }
+}
+
+// Unit-variance uniform number on [-sqrt3, sqrt3) from the top 53 bits.
+__device__ __forceinline__ double unit_uniform(uint64_t v)
+{
+    double u01 = (double)(v >> 11) * (1.0 / 9007199254740992.0);
+    return sqrt(3.0) * (2.0 * u01 - 1.0);
+}
+
+__device__ __forceinline__ int wrapi(int v, int E) { return v < 0 ? v + E : (v >= E ? v - E : v); }
+
+// Time-interpolation weights of the four ring samples j-1, j, j+1, j+2 for
+// the boundary velocity at t = n + 1, t in (jK, (j+1)K].
+template <class R>
+struct TimeWeights {
+    int slot[4];
+    R c[4];
+};
+
+template <class R>
+__device__ __forceinline__ TimeWeights<R> time_weights(int64_t n, int K, int mode)
+{
+    TimeWeights<R> tw;
+    int64_t j = n / K;
+    int s = (int)(n + 1 - j * K);
+    R th = (R)s / (R)K;
+    for (int a = 0; a < 4; a++) {
+        int64_t jj = j - 1 + a;
+        tw.slot[a] = (int)(((jj % kRingSlots) + kRingSlots) % kRingSlots);
+        tw.c[a] = R(0);
+    }
+    if (mode == 0) {
+        tw.c[1] = R(1) - th;
+        tw.c[2] = th;
+    } else {
+        R h00 = 2 * th * th * th - 3 * th * th + 1;
+        R h10 = th * th * th - 2 * th * th + th;
+        R h01 = -2 * th * th * th + 3 * th * th;
+        R h11 = th * th * th - th * th;
+        if (j >= 1) {
+            tw.c[0] = -R(0.5) * h10;
+            tw.c[1] = h00 - R(0.5) * h11;
+            tw.c[2] = h01 + R(0.5) * h10;
+            tw.c[3] = R(0.5) * h11;
+        } else {
+            tw.c[1] = h00 - h10 - R(0.5) * h11;
+            tw.c[2] = h01 + h10;
+            tw.c[3] = R(0.5) * h11;
+        }
+    }
+    return tw;
+}
+
+// Owning face of a boundary site (first velocity face containing it in the
+// order x-, x+, y-, y+, z-, z+) and its in-face coordinates.
+__device__ __forceinline__ int owning_face(int x, int y, int z, int E, int per, int& p, int& q)
+{
+    if (!(per & 1) && x == 0) { p = y; q = z; return 0; }
+    if (!(per & 1) && x == E - 1) { p = y; q = z; return 1; }
+    if (!(per & 2) && y == 0) { p = x; q = z; return 2; }
+    if (!(per & 2) && y == E - 1) { p = x; q = z; return 3; }
+    if (!(per & 4) && z == 0) { p = x; q = y; return 4; }
+    p = x; q = y;
+    return 5;
+}
+
+// Boundary velocity of a site from the ring of coarse samples.
+template <class R>
+__device__ __forceinline__ void boundary_velocity(const R* ring, int64_t slot_elems, int64_t ring_off, int E,
+                                                  int f, int p, int q, const TimeWeights<R>& tw, R u[3])
+{
+    const int64_t fe = (int64_t)E * E;
+    const int64_t site = (int64_t)q * E + p;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        R acc = R(0);
+        for (int a = 0; a < 4; a++) {
+            if (tw.c[a] != R(0)) {  // a zero weight never touches its (possibly unpushed) slot
+                const R* base = ring + (int64_t)tw.slot[a] * slot_elems + ring_off;
+                acc += tw.c[a] * base[((int64_t)f * 3 + c) * fe + site];
+            }
+        }
+        u[c] = acc;
+    }
+}
+
+}  // namespace lbt

@@ -1,0 +1,6 @@
+// Kernels of the step for one population storage format.
+#include "lbt_kernels.cuh"
+
+namespace lbt {
+template struct Launch<kF32>;
+}  // namespace lbt

@@ -1,0 +1,124 @@
+// Internal structures of the tracer-box library, shared by host and device code.
+// Plain structs only; everything here is copied into the caller's device arena.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "lbtracer.h"
+
+namespace lbt {
+
+constexpr int kQ = 19;
+constexpr int kRingSlots = 4;       // coarse samples j-1, j, j+1, j+2 live in slots j mod 4
+constexpr int kMaxBeads = 256;      // beads per chain (one CTA per chain, one thread per bead)
+
+// One box as the kernels see it.
+struct BoxDev {
+    int64_t f_off;      // element offset of the box's populations in each population buffer
+    int64_t n3;         // E^3
+    int64_t ring_off;   // element offset of the box's six faces inside one ring slot
+    int32_t E;
+    int32_t per_mask;   // bit a set: axis a periodic
+    int32_t time_interp;
+    int32_t K;
+    int32_t chain;      // index into the chain table, -1 if none
+    int32_t has_accel;
+    double tau;
+    double rho_b;
+    double accel[3];
+};
+
+// One chain (bead-spring polymer) as the bead kernel sees it.
+struct ChainDev {
+    int32_t box;
+    int32_t nbeads;     // current chain length (0 until chain_couple)
+    int32_t n_md;
+    int32_t pin_com;
+    int64_t bead_off;   // offset in beads into the position / velocity arrays
+    int64_t force_off;  // offset in entries into the force list (8 per bead)
+    double k_fene, R0, zeta, mass, kT;
+    double f_ext[3];
+    uint64_t seed;
+};
+
+// Force density at one lattice site, produced by the bead kernel, consumed by
+// the forced re-collision.  site = -1 marks a duplicate of an earlier entry.
+struct ForceEntry {
+    int32_t site;
+    int32_t pad;
+    double g[3];
+};
+
+// Arena layout (byte offsets), computed by plan().
+struct Layout {
+    size_t boxes, tile_prefix, chains, pop_a, pop_b, ring, pos, vel, forces, cons_partial, cons_out,
+        status, step, total;
+    size_t pop_bytes;        // bytes of one population buffer
+    size_t ring_slot_elems;  // real elements per ring slot
+    int64_t cons_chunks;     // max conservation chunks per box
+    int64_t total_beads;
+};
+
+enum Storage { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
+
+// Parameters of the stream-collide kernel (fused with the boundary layer).
+struct SCParams {
+    const void* A;
+    void* B;
+    const void* ring;             // real elements
+    int64_t ring_slot_elems;
+    const BoxDev* boxes;
+    const int64_t* tile_prefix;   // [nboxes + 1] first tile of each box for the current block size
+    int32_t nboxes;
+    int64_t total_tiles;
+    const int64_t* step;          // device step counter n (state holds step n)
+    int32_t* status;
+};
+
+struct BeadParams {
+    const void* A;
+    const BoxDev* boxes;
+    const ChainDev* chains;
+    double* pos;
+    double* vel;
+    ForceEntry* forces;
+    const int64_t* step;
+    int32_t* status;
+};
+
+struct ForcedParams {
+    const void* A;
+    void* B;
+    const BoxDev* boxes;
+    const ChainDev* chains;
+    const ForceEntry* forces;
+    const int32_t* status;
+    int64_t* step;                // incremented once per step by block 0
+    int32_t nchains;
+};
+
+// Host-side launchers, one instantiation per storage type.
+template <int ST>
+struct Launch {
+    static cudaError_t stream_collide(const SCParams& p, int threads, int ctas, cudaStream_t s);
+    static cudaError_t bead_couple(const BeadParams& p, int nchains, cudaStream_t s);
+    static cudaError_t forced(const ForcedParams& p, cudaStream_t s);
+    static cudaError_t init(void* A, const BoxDev* boxes, int box, int64_t n3, const void* u0, cudaStream_t s);
+    static cudaError_t fields(const void* A, const BoxDev* boxes, int box, int64_t n3, int what, void* dst,
+                              cudaStream_t s);
+    static cudaError_t read_dev(const void* A, int64_t count, void* dst, cudaStream_t s);
+    static cudaError_t conservation(const void* A, const BoxDev* boxes, const ChainDev* chains, int nboxes,
+                                    int64_t chunks, const double* vel, double* partial, double* out,
+                                    int32_t* status, cudaStream_t s);
+};
+
+// Generator launchers; workspace holds the per-axis phase table (3 M E double2).
+cudaError_t launch_synth_faces(const double* kvec, const double* amp, const double* omega, const double* phi,
+                               int M, int E, int K, int64_t j0, int64_t nsamp, int out_f64, void* out,
+                               void* workspace, cudaStream_t s);
+cudaError_t launch_synth_volume(const double* kvec, const double* amp, const double* omega, const double* phi,
+                                int M, int E, double t, int out_f64, void* out, void* workspace, cudaStream_t s);
+
+}  // namespace lbt

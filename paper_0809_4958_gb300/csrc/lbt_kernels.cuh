@@ -1,0 +1,711 @@
+// Kernel templates of the tracer-box lattice Boltzmann step.  Included once
+// per storage format by lbt_inst_*.cu.
+//
+// One step n -> n+1 (state A = post-collision populations of step n, with the
+// boundary layer at the equilibrium of t = n):
+//   k_bead_couple     (side stream)  chain MD over the step, force list
+//   k_stream_collide                  every site of every box: pull, BGK
+//                                     collide (interior) or boundary
+//                                     equilibrium at t = n+1, write B
+//   k_forced                          re-collide the forced sites with the
+//                                     bead force, advance the step counter
+#pragma once
+#include "lbt_device.cuh"
+
+namespace lbt {
+
+// ---------------------------------------------------------------------------
+// Fused stream-collide + boundary layer.
+//
+// Work unit: a group of VW consecutive x-sites, moved with one vector load per
+// population.  Groups of a box are numbered linearly in memory order, a tile
+// is blockDim.x consecutive groups of one box, and blocks walk the global tile
+// list (all boxes) with a stride of gridDim.x (persistent when the grid is
+// smaller than the tile count).
+//
+// Pull scheme: population i of site x comes from x - c_i.  The y/z shift moves
+// whole rows, so the load stays aligned; the x shift (c_ix = +-1) needs one
+// element of the neighbouring group, taken from the neighbouring lane by a
+// warp shuffle, or loaded directly at a warp edge and at a periodic x wrap.
+// ---------------------------------------------------------------------------
+template <int ST, int VW, bool ACCEL>
+__device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, int64_t G, int64_t n, int lane)
+{
+    using S = Stor<ST>;
+    using E = typename S::E;
+    using A = typename S::A;
+    using R = typename S::R;
+    using P = Pack<E, VW>;
+    using Raw = typename P::Raw;
+
+    const int Ei = bd.E;
+    const int64_t n3 = bd.n3;
+    const int gpr = Ei / VW;
+    const int64_t groups = n3 / VW;
+    const bool active = G < groups;
+    const int64_t Gc = active ? G : 0;
+    const int xg = (int)(Gc % gpr);
+    const int64_t row = Gc / gpr;
+    const int y = (int)(row % Ei);
+    const int z = (int)(row / Ei);
+    const int per = bd.per_mask;
+    const bool px = per & 1, py = per & 2, pz = per & 4;
+    const bool row_bnd = (!py && (y == 0 || y == Ei - 1)) || (!pz && (z == 0 || z == Ei - 1));
+    const bool interior = active && !row_bnd;
+
+    const E* Ab = reinterpret_cast<const E*>(p.A) + bd.f_off;
+    E* Bb = reinterpret_cast<E*>(p.B) + bd.f_off;
+
+    // ---- loads ----
+    P v[kQ];
+    A nb[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; i++) {
+        int ys = y - cvec(i, 1), zs = z - cvec(i, 2);
+        if (py) ys = wrapi(ys, Ei);
+        if (pz) zs = wrapi(zs, Ei);
+        const int64_t src = ((int64_t)zs * Ei + ys) * gpr + xg;
+        v[i].raw = interior ? ld_nc(reinterpret_cast<const Raw*>(Ab + (int64_t)i * n3) + src) : zero_raw<Raw>();
+    }
+#pragma unroll
+    for (int i = 0; i < kQ; i++) {
+        const int cx = cvec(i, 0);
+        if (cx == 0) continue;
+        int ys = y - cvec(i, 1), zs = z - cvec(i, 2);
+        if (py) ys = wrapi(ys, Ei);
+        if (pz) zs = wrapi(zs, Ei);
+        const E* rowp = Ab + (int64_t)i * n3 + ((int64_t)zs * Ei + ys) * Ei;
+        if (cx == 1) {
+            // site x0 needs element x0 - 1: last element of the previous group
+            A t = __shfl_up_sync(0xffffffffu, S::in(v[i].e[VW - 1]), 1);
+            const bool need = interior && (xg == 0 ? px : lane == 0);
+            if (need) t = S::in(rowp[xg == 0 ? Ei - 1 : xg * VW - 1]);
+            nb[i] = t;
+        } else {
+            // site x0 + VW - 1 needs element x0 + VW: first element of the next group
+            A t = __shfl_down_sync(0xffffffffu, S::in(v[i].e[0]), 1);
+            const bool need = interior && (xg == gpr - 1 ? px : lane == 31);
+            if (need) t = S::in(rowp[xg == gpr - 1 ? 0 : (xg + 1) * VW]);
+            nb[i] = t;
+        }
+    }
+
+    // ---- moments of the pulled populations ----
+    auto fval = [&](int i, int k) -> A {
+        const int cx = cvec(i, 0);
+        if (cx == 0) return S::in(v[i].e[k]);
+        if (cx == 1) return k == 0 ? nb[i] : S::in(v[i].e[k - 1]);
+        return k == VW - 1 ? nb[i] : S::in(v[i].e[k + 1]);
+    };
+
+    A drho[VW], ux[VW], uy[VW], uz[VW];
+#pragma unroll
+    for (int k = 0; k < VW; k++) {
+        A r = A(0), jx = A(0), jy = A(0), jz = A(0);
+#pragma unroll
+        for (int i = 0; i < kQ; i++) {
+            const A f = fval(i, k);
+            r += f;
+            if (cvec(i, 0)) jx += cvec(i, 0) * f;
+            if (cvec(i, 1)) jy += cvec(i, 1) * f;
+            if (cvec(i, 2)) jz += cvec(i, 2) * f;
+        }
+        const A rho = A(1) + r;
+        const A inv = A(1) / rho;
+        if (ACCEL) {
+            jx += A(0.5) * rho * (A)bd.accel[0];
+            jy += A(0.5) * rho * (A)bd.accel[1];
+            jz += A(0.5) * rho * (A)bd.accel[2];
+        }
+        drho[k] = r;
+        ux[k] = jx * inv;
+        uy[k] = jy * inv;
+        uz[k] = jz * inv;
+    }
+
+    // ---- boundary sites: equilibrium of the interpolated boundary velocity ----
+    unsigned bmask = 0;
+    if (active) {
+        if (row_bnd) bmask = (1u << VW) - 1u;
+        else if (!px) bmask = (xg == 0 ? 1u : 0u) | (xg == gpr - 1 ? (1u << (VW - 1)) : 0u);
+    }
+    if (bmask) {
+        const TimeWeights<R> tw = time_weights<R>(n, bd.K, bd.time_interp);
+        const R* ring = reinterpret_cast<const R*>(p.ring);
+#pragma unroll
+        for (int k = 0; k < VW; k++) {
+            if (bmask & (1u << k)) {
+                int pp, qq;
+                const int x = xg * VW + k;
+                const int f = owning_face(x, y, z, Ei, per, pp, qq);
+                R ub[3];
+                boundary_velocity<R>(ring, p.ring_slot_elems, bd.ring_off, Ei, f, pp, qq, tw, ub);
+                drho[k] = (A)bd.rho_b - A(1);
+                ux[k] = (A)ub[0];
+                uy[k] = (A)ub[1];
+                uz[k] = (A)ub[2];
+            }
+        }
+    }
+
+    // ---- collide and store, one population at a time ----
+    const A om = A(1) / (A)bd.tau;
+    const A srcfac = A(1) - A(0.5) * om;
+    A usq[VW], ua[VW];
+#pragma unroll
+    for (int k = 0; k < VW; k++) {
+        usq[k] = A(1.5) * (ux[k] * ux[k] + uy[k] * uy[k] + uz[k] * uz[k]);
+        if (ACCEL) ua[k] = ux[k] * (A)bd.accel[0] + uy[k] * (A)bd.accel[1] + uz[k] * (A)bd.accel[2];
+    }
+#pragma unroll
+    for (int i = 0; i < kQ; i++) {
+        const A w = wgt<A>(i);
+        const int cx = cvec(i, 0), cy = cvec(i, 1), cz = cvec(i, 2);
+        P o;
+#pragma unroll
+        for (int k = 0; k < VW; k++) {
+            const A rho = A(1) + drho[k];
+            A cu = A(0);
+            if (cx) cu += cx * ux[k];
+            if (cy) cu += cy * uy[k];
+            if (cz) cu += cz * uz[k];
+            const A deq = w * (drho[k] + rho * (A(3) * cu + A(4.5) * cu * cu - usq[k]));
+            const A f = fval(i, k);
+            A val = f + om * (deq - f);
+            if (ACCEL) {
+                const A ca = (A)(cx * bd.accel[0] + cy * bd.accel[1] + cz * bd.accel[2]);
+                val += srcfac * w * rho * (A(3) * (ca - ua[k]) + A(9) * cu * ca);
+            }
+            if (bmask & (1u << k)) val = deq;
+            o.e[k] = S::out(val);
+        }
+        if (active) reinterpret_cast<Raw*>(Bb + (int64_t)i * n3)[G] = o.raw;
+    }
+}
+
+template <int ST, int VW>
+__device__ __forceinline__ void copy_tile(const SCParams& p, const BoxDev& bd, int64_t G)
+{
+    using E = typename Stor<ST>::E;
+    using Raw = typename Pack<E, VW>::Raw;
+    if (G >= bd.n3 / VW) return;
+    const Raw* a = reinterpret_cast<const Raw*>(reinterpret_cast<const E*>(p.A) + bd.f_off);
+    Raw* b = reinterpret_cast<Raw*>(reinterpret_cast<E*>(p.B) + bd.f_off);
+    const int64_t gq = bd.n3 / VW;
+    for (int i = 0; i < kQ; i++) b[i * gq + G] = a[i * gq + G];
+}
+
+template <int ST, int VW>
+__global__ void __launch_bounds__(256) k_stream_collide(SCParams p)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t n = *p.step;
+    for (int64_t tile = blockIdx.x; tile < p.total_tiles; tile += gridDim.x) {
+        int lo = 0, hi = p.nboxes - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.tile_prefix[mid] <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        const BoxDev& bd = p.boxes[lo];
+        const int64_t G = (tile - p.tile_prefix[lo]) * blockDim.x + threadIdx.x;
+        if (p.status[lo] != 0) {
+            copy_tile<ST, VW>(p, bd, G);  // frozen box: state does not change
+            continue;
+        }
+        if (bd.has_accel) sc_tile<ST, VW, true>(p, bd, G, n, lane);
+        else sc_tile<ST, VW, false>(p, bd, G, n, lane);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-site helpers for the scalar kernels (bead gather, forced re-collision,
+// fields).
+// ---------------------------------------------------------------------------
+template <int ST>
+__device__ __forceinline__ void pull_site(const typename Stor<ST>::E* Ab, int64_t n3, int E, int per, int x, int y,
+                                          int z, typename Stor<ST>::A f[kQ])
+{
+#pragma unroll
+    for (int i = 0; i < kQ; i++) {
+        int xs = x - cvec(i, 0), ys = y - cvec(i, 1), zs = z - cvec(i, 2);
+        if (per & 1) xs = wrapi(xs, E);
+        if (per & 2) ys = wrapi(ys, E);
+        if (per & 4) zs = wrapi(zs, E);
+        f[i] = Stor<ST>::in(Ab[(int64_t)i * n3 + ((int64_t)zs * E + ys) * E + xs]);
+    }
+}
+
+template <class A>
+__device__ __forceinline__ void moments(const A f[kQ], A& drho, A j[3])
+{
+    drho = A(0);
+    j[0] = j[1] = j[2] = A(0);
+#pragma unroll
+    for (int i = 0; i < kQ; i++) {
+        drho += f[i];
+        if (cvec(i, 0)) j[0] += cvec(i, 0) * f[i];
+        if (cvec(i, 1)) j[1] += cvec(i, 1) * f[i];
+        if (cvec(i, 2)) j[2] += cvec(i, 2) * f[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bead coupling: one block per chain, one thread per bead in the MD phase.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(int32_t* st, int code) { atomicCAS(st, 0, code); }
+
+template <int ST>
+__global__ void __launch_bounds__(256) k_bead_couple(BeadParams p)
+{
+    using S = Stor<ST>;
+    using A = typename S::A;
+    const ChainDev& ch = p.chains[blockIdx.x];
+    const int N = ch.nbeads;
+    const int b = ch.box;
+    if (N <= 0 || p.status[b] != 0) return;
+    const BoxDev& bd = p.boxes[b];
+    const int Ei = bd.E, per = bd.per_mask;
+    const int64_t n3 = bd.n3;
+    const int64_t n = *p.step;
+    const int tid = threadIdx.x;
+
+    __shared__ double sR[kMaxBeads][3];     // current positions (MD)
+    __shared__ double sU[kMaxBeads][3];     // fluid velocity at each bead
+    __shared__ double sP[kMaxBeads][3];     // momentum given to the fluid
+    __shared__ double sW[kMaxBeads][8];     // start-of-step trilinear weights
+    __shared__ int sBase[kMaxBeads][3];     // start-of-step stencil corner
+    __shared__ double sRed[2][32][3];
+    __shared__ int sErr;
+
+    double* pos = p.pos + 3 * ch.bead_off;
+    double* vel = p.vel + 3 * ch.bead_off;
+    if (tid == 0) sErr = 0;
+    __syncthreads();
+
+    // 1. stencil of the start-of-step position
+    double R[3] = {0, 0, 0}, V[3] = {0, 0, 0};
+    if (tid < N) {
+        for (int a = 0; a < 3; a++) {
+            R[a] = pos[3 * tid + a];
+            V[a] = vel[3 * tid + a];
+        }
+        double d[3];
+        for (int a = 0; a < 3; a++) {
+            const double fl = floor(R[a]);
+            d[a] = R[a] - fl;
+            long long i0 = (long long)fl;
+            if (!((per >> a) & 1)) {
+                if (i0 < 1 || i0 + 1 > Ei - 2) sErr = LB_ERR_BEAD_OOB;
+                sBase[tid][a] = (int)i0;
+            } else {
+                sBase[tid][a] = (int)(((i0 % Ei) + Ei) % Ei);
+            }
+            sR[tid][a] = R[a];
+            sP[tid][a] = 0.0;
+        }
+        for (int c = 0; c < 8; c++) {
+            const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+            sW[tid][c] = (cx ? d[0] : 1.0 - d[0]) * (cy ? d[1] : 1.0 - d[1]) * (cz ? d[2] : 1.0 - d[2]);
+        }
+    }
+    __syncthreads();
+    if (sErr) {
+        if (tid == 0) set_status(&p.status[b], sErr);
+        return;
+    }
+
+    // 2. fluid velocity at the beads: eight threads per bead, one corner each
+    const typename S::E* Ab = reinterpret_cast<const typename S::E*>(p.A) + bd.f_off;
+    for (int base = 0; base < 8 * N; base += blockDim.x) {
+        const int e = base + tid;
+        const bool act = e < 8 * N;
+        double uc[3] = {0, 0, 0};
+        if (act) {
+            const int bb = e >> 3, c = e & 7;
+            int s[3] = {sBase[bb][0] + (c & 1), sBase[bb][1] + ((c >> 1) & 1), sBase[bb][2] + ((c >> 2) & 1)};
+            for (int a = 0; a < 3; a++)
+                if ((per >> a) & 1) s[a] = wrapi(s[a], Ei);
+            A f[kQ], dr, j[3];
+            pull_site<ST>(Ab, n3, Ei, per, s[0], s[1], s[2], f);
+            moments<A>(f, dr, j);
+            const A rho = A(1) + dr;
+            const double wgt8 = sW[bb][c];
+            for (int a = 0; a < 3; a++) {
+                const A ua = (j[a] + A(0.5) * rho * (A)bd.accel[a]) / rho;
+                uc[a] = wgt8 * (double)ua;
+            }
+        }
+        for (int a = 0; a < 3; a++) {
+            uc[a] += __shfl_xor_sync(0xffffffffu, uc[a], 1);
+            uc[a] += __shfl_xor_sync(0xffffffffu, uc[a], 2);
+            uc[a] += __shfl_xor_sync(0xffffffffu, uc[a], 4);
+        }
+        if (act && (e & 7) == 0)
+            for (int a = 0; a < 3; a++) sU[e >> 3][a] = uc[a];
+    }
+    __syncthreads();
+
+    // 3. MD substeps (symplectic Euler), fluid velocity frozen over the step
+    const double dt = 1.0 / ch.n_md;
+    const double namp = ch.kT > 0.0 ? sqrt(2.0 * ch.kT * ch.zeta / dt) : 0.0;
+    const double R02 = ch.R0 * ch.R0;
+    double P[3] = {0, 0, 0};
+    for (int sub = 0; sub < ch.n_md; sub++) {
+        if (tid < N) {
+            double F[3] = {0, 0, 0};
+            if (tid > 0) {  // bond (tid-1, tid): force -k r / (1 - r^2/R0^2) on the upper bead
+                double r[3], r2 = 0;
+                for (int a = 0; a < 3; a++) {
+                    r[a] = sR[tid][a] - sR[tid - 1][a];
+                    r2 += r[a] * r[a];
+                }
+                if (r2 >= R02) sErr = LB_ERR_FENE;
+                const double fac = ch.k_fene / (1.0 - r2 / R02);
+                for (int a = 0; a < 3; a++) F[a] -= fac * r[a];
+            }
+            if (tid + 1 < N) {  // bond (tid, tid+1): opposite force on the lower bead
+                double r[3], r2 = 0;
+                for (int a = 0; a < 3; a++) {
+                    r[a] = sR[tid + 1][a] - sR[tid][a];
+                    r2 += r[a] * r[a];
+                }
+                if (r2 >= R02) sErr = LB_ERR_FENE;
+                const double fac = ch.k_fene / (1.0 - r2 / R02);
+                for (int a = 0; a < 3; a++) F[a] += fac * r[a];
+            }
+            double xi[3] = {0, 0, 0};
+            if (namp > 0.0) {
+                uint64_t x[4] = {(uint64_t)n, (uint64_t)sub, (uint64_t)tid, (uint64_t)b};
+                philox4x64_10(x, ch.seed, 0);
+                for (int a = 0; a < 3; a++) xi[a] = unit_uniform(x[a]);
+            }
+            for (int a = 0; a < 3; a++) {
+                const double ffric = -ch.zeta * (V[a] - sU[tid][a]);
+                const double fnoise = namp * xi[a];
+                const double ftot = F[a] + ffric + fnoise + ch.f_ext[a];
+                V[a] += dt / ch.mass * ftot;
+                R[a] += dt * V[a];
+                P[a] -= (ffric + fnoise) * dt;
+            }
+        }
+        __syncthreads();
+        if (tid < N)
+            for (int a = 0; a < 3; a++) sR[tid][a] = R[a];
+        __syncthreads();
+        if (sErr) break;
+    }
+    if (sErr) {
+        if (tid == 0) set_status(&p.status[b], sErr);
+        return;
+    }
+
+    // 4. centre of mass pinned at the box centre
+    if (ch.pin_com >= 1) {
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int pass = 0; pass < 2; pass++) {
+            double s[3];
+            for (int a = 0; a < 3; a++) {
+                s[a] = tid < N ? (pass == 0 ? R[a] : V[a]) : 0.0;
+                for (int o = 16; o > 0; o >>= 1) s[a] += __shfl_xor_sync(0xffffffffu, s[a], o);
+            }
+            if (lane == 0)
+                for (int a = 0; a < 3; a++) sRed[pass][warp][a] = s[a];
+        }
+        __syncthreads();
+        double com[3] = {0, 0, 0}, vcm[3] = {0, 0, 0};
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++)
+            for (int a = 0; a < 3; a++) {
+                com[a] += sRed[0][w][a];
+                vcm[a] += sRed[1][w][a];
+            }
+        const double centre = 0.5 * (Ei - 1);
+        if (tid < N)
+            for (int a = 0; a < 3; a++) {
+                R[a] += centre - com[a] / N;
+                if (ch.pin_com >= 2) V[a] -= vcm[a] / N;
+            }
+    }
+    if (tid < N) {
+        for (int a = 0; a < 3; a++) {
+            pos[3 * tid + a] = R[a];
+            vel[3 * tid + a] = V[a];
+            sP[tid][a] = P[a];
+        }
+    }
+    __syncthreads();
+
+    // 5. force density at the stencil sites: every entry sums, in bead order,
+    //    the contributions of all beads whose stencil holds its site; entries
+    //    whose site an earlier bead already holds are marked duplicates.
+    ForceEntry* fl = p.forces + ch.force_off;
+    for (int e = tid; e < 8 * N; e += blockDim.x) {
+        const int bb = e >> 3, c = e & 7;
+        int s[3] = {sBase[bb][0] + (c & 1), sBase[bb][1] + ((c >> 1) & 1), sBase[bb][2] + ((c >> 2) & 1)};
+        for (int a = 0; a < 3; a++)
+            if ((per >> a) & 1) s[a] = wrapi(s[a], Ei);
+        double g[3] = {0, 0, 0};
+        bool dup = false;
+        for (int b2 = 0; b2 < N; b2++) {
+            int o[3];
+            bool in = true;
+            for (int a = 0; a < 3; a++) {
+                int d = s[a] - sBase[b2][a];
+                if ((per >> a) & 1) d = wrapi(d, Ei);
+                o[a] = d;
+                in = in && (d == 0 || d == 1);
+            }
+            if (!in) continue;
+            if (b2 < bb) dup = true;
+            const double w8 = sW[b2][o[0] + 2 * o[1] + 4 * o[2]];
+            for (int a = 0; a < 3; a++) g[a] += w8 * sP[b2][a];
+        }
+        ForceEntry fe;
+        fe.site = dup ? -1 : (int32_t)(((int64_t)s[2] * Ei + s[1]) * Ei + s[0]);
+        fe.pad = 0;
+        for (int a = 0; a < 3; a++) fe.g[a] = g[a];
+        fl[e] = fe;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forced re-collision: the sites that carry a bead force density g are
+// collided again with rho a + g (Guo forcing) and overwrite B.  Block 0
+// advances the device step counter once all of its own work is done.
+// ---------------------------------------------------------------------------
+template <int ST>
+__global__ void __launch_bounds__(256) k_forced(ForcedParams p)
+{
+    using S = Stor<ST>;
+    using A = typename S::A;
+    if ((int)blockIdx.x < p.nchains) {
+        const ChainDev& ch = p.chains[blockIdx.x];
+        const int b = ch.box;
+        if (ch.nbeads > 0 && p.status[b] == 0) {
+            const BoxDev& bd = p.boxes[b];
+            const int Ei = bd.E, per = bd.per_mask;
+            const int64_t n3 = bd.n3;
+            const typename S::E* Ab = reinterpret_cast<const typename S::E*>(p.A) + bd.f_off;
+            typename S::E* Bb = reinterpret_cast<typename S::E*>(p.B) + bd.f_off;
+            const ForceEntry* fl = p.forces + ch.force_off;
+            for (int e = threadIdx.x; e < 8 * ch.nbeads; e += blockDim.x) {
+                const ForceEntry fe = fl[e];
+                if (fe.site < 0) continue;
+                const int x = fe.site % Ei, y = (fe.site / Ei) % Ei, z = fe.site / (Ei * Ei);
+                A f[kQ], dr, j[3];
+                pull_site<ST>(Ab, n3, Ei, per, x, y, z, f);
+                moments<A>(f, dr, j);
+                const A rho = A(1) + dr;
+                A F[3], u[3];
+                for (int a = 0; a < 3; a++) {
+                    F[a] = rho * (A)bd.accel[a] + (A)fe.g[a];
+                    u[a] = (j[a] + A(0.5) * F[a]) / rho;
+                }
+                const A om = A(1) / (A)bd.tau;
+                const A usq = A(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                const A uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+#pragma unroll
+                for (int i = 0; i < kQ; i++) {
+                    const A w = wgt<A>(i);
+                    const A cu = cvec(i, 0) * u[0] + cvec(i, 1) * u[1] + cvec(i, 2) * u[2];
+                    const A cF = cvec(i, 0) * F[0] + cvec(i, 1) * F[1] + cvec(i, 2) * F[2];
+                    const A deq = w * (dr + rho * (A(3) * cu + A(4.5) * cu * cu - usq));
+                    A val = f[i] + om * (deq - f[i]);
+                    val += (A(1) - A(0.5) * om) * w * (A(3) * (cF - uF) + A(9) * cu * cF);
+                    Bb[(int64_t)i * n3 + fe.site] = S::out(val);
+                }
+            }
+        }
+    }
+    if (blockIdx.x == 0) {
+        __syncthreads();
+        if (threadIdx.x == 0) *p.step += 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initial condition: equilibrium with rho = 1 and velocity u0 on every site.
+// ---------------------------------------------------------------------------
+template <int ST>
+__global__ void k_init(typename Stor<ST>::E* Ab, int64_t n3, const typename Stor<ST>::R* u0)
+{
+    using S = Stor<ST>;
+    using A = typename S::A;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n3; s += (int64_t)gridDim.x * blockDim.x) {
+        const A u[3] = {(A)u0[s], (A)u0[n3 + s], (A)u0[2 * n3 + s]};
+        const A usq = A(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#pragma unroll
+        for (int i = 0; i < kQ; i++) {
+            const A cu = cvec(i, 0) * u[0] + cvec(i, 1) * u[1] + cvec(i, 2) * u[2];
+            Ab[(int64_t)i * n3 + s] = S::out(wgt<A>(i) * (A(3) * cu + A(4.5) * cu * cu - usq));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Observables: density and velocity (what = 0: rho, 1: u) and raw deviations.
+// ---------------------------------------------------------------------------
+template <int ST>
+__global__ void k_fields(const typename Stor<ST>::E* Ab, BoxDev bd, int what, typename Stor<ST>::R* dst)
+{
+    using S = Stor<ST>;
+    using A = typename S::A;
+    const int Ei = bd.E, per = bd.per_mask;
+    const int64_t n3 = bd.n3;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n3; s += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(s % Ei), y = (int)((s / Ei) % Ei), z = (int)(s / ((int64_t)Ei * Ei));
+        const bool bnd = (!(per & 1) && (x == 0 || x == Ei - 1)) || (!(per & 2) && (y == 0 || y == Ei - 1)) ||
+                         (!(per & 4) && (z == 0 || z == Ei - 1));
+        A f[kQ], dr, j[3];
+        if (bnd) {
+            for (int i = 0; i < kQ; i++) f[i] = S::in(Ab[(int64_t)i * n3 + s]);
+        } else {
+            pull_site<ST>(Ab, n3, Ei, per, x, y, z, f);
+        }
+        moments<A>(f, dr, j);
+        const A rho = A(1) + dr;
+        if (what == 0) {
+            dst[s] = (typename S::R)rho;
+        } else {
+            for (int a = 0; a < 3; a++) {
+                const A ja = bnd ? j[a] : j[a] + A(0.5) * rho * (A)bd.accel[a];
+                dst[(int64_t)a * n3 + s] = (typename S::R)(ja / rho);
+            }
+        }
+    }
+}
+
+template <int ST>
+__global__ void k_read_dev(const typename Stor<ST>::E* Ab, int64_t count, typename Stor<ST>::R* dst)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < count; s += (int64_t)gridDim.x * blockDim.x)
+        dst[s] = (typename Stor<ST>::R)Stor<ST>::in(Ab[s]);
+}
+
+// ---------------------------------------------------------------------------
+// Conservation sums in FP64: block (chunk, box) sums its sites into a partial,
+// then one thread per box adds the partials in chunk order.
+// ---------------------------------------------------------------------------
+constexpr int kConsThreads = 256;
+constexpr int kConsSitesPerThread = 16;
+constexpr int64_t kConsChunk = (int64_t)kConsThreads * kConsSitesPerThread;
+
+template <int ST>
+__global__ void __launch_bounds__(kConsThreads) k_cons_partial(const void* Araw, const BoxDev* boxes, int64_t chunks,
+                                                               double* partial)
+{
+    using S = Stor<ST>;
+    const int b = blockIdx.y;
+    const BoxDev& bd = boxes[b];
+    const int64_t n3 = bd.n3;
+    const int64_t c0 = (int64_t)blockIdx.x * kConsChunk;
+    if (c0 >= n3) return;
+    const typename S::E* Ab = reinterpret_cast<const typename S::E*>(Araw) + bd.f_off;
+    double acc[4] = {0, 0, 0, 0};
+    for (int k = 0; k < kConsSitesPerThread; k++) {
+        const int64_t s = c0 + (int64_t)k * kConsThreads + threadIdx.x;
+        if (s >= n3) break;
+#pragma unroll
+        for (int i = 0; i < kQ; i++) {
+            const double d = (double)S::in(Ab[(int64_t)i * n3 + s]);
+            acc[0] += d;
+            if (cvec(i, 0)) acc[1] += cvec(i, 0) * d;
+            if (cvec(i, 1)) acc[2] += cvec(i, 1) * d;
+            if (cvec(i, 2)) acc[3] += cvec(i, 2) * d;
+        }
+    }
+    __shared__ double red[kConsThreads / 32][4];
+    for (int a = 0; a < 4; a++)
+        for (int o = 16; o > 0; o >>= 1) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
+    if ((threadIdx.x & 31) == 0)
+        for (int a = 0; a < 4; a++) red[threadIdx.x >> 5][a] = acc[a];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[4] = {0, 0, 0, 0};
+        for (int w = 0; w < kConsThreads / 32; w++)
+            for (int a = 0; a < 4; a++) t[a] += red[w][a];
+        for (int a = 0; a < 4; a++) partial[((int64_t)b * chunks + blockIdx.x) * 4 + a] = t[a];
+    }
+}
+
+__global__ void k_cons_final(const BoxDev* boxes, const ChainDev* chains, int nboxes, int64_t chunks,
+                             const double* partial, const double* vel, double* out, int32_t* status);
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------
+template <int ST>
+constexpr int kVW = ST == kF64 ? 2 : (ST == kF32 ? 4 : 8);
+
+inline int grid_for(int64_t n, int threads, int cap = 152 * 16)
+{
+    int64_t g = (n + threads - 1) / threads;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+template <int ST>
+cudaError_t Launch<ST>::stream_collide(const SCParams& p, int threads, int ctas, cudaStream_t s)
+{
+    int64_t grid = (ctas > 0 && ctas < p.total_tiles) ? ctas : p.total_tiles;
+    if (grid < 1) return cudaSuccess;
+    k_stream_collide<ST, kVW<ST>><<<(unsigned)grid, threads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, cudaStream_t s)
+{
+    if (nchains <= 0) return cudaSuccess;
+    k_bead_couple<ST><<<nchains, kMaxBeads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t Launch<ST>::forced(const ForcedParams& p, cudaStream_t s)
+{
+    k_forced<ST><<<p.nchains > 0 ? p.nchains : 1, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t Launch<ST>::init(void* A, const BoxDev* boxes, int box, int64_t n3, const void* u0, cudaStream_t s)
+{
+    (void)boxes;
+    (void)box;
+    k_init<ST><<<grid_for(n3, 256), 256, 0, s>>>(reinterpret_cast<typename Stor<ST>::E*>(A), n3,
+                                                 reinterpret_cast<const typename Stor<ST>::R*>(u0));
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t Launch<ST>::fields(const void* A, const BoxDev* boxes, int box, int64_t n3, int what, void* dst,
+                               cudaStream_t s)
+{
+    k_fields<ST><<<grid_for(n3, 256), 256, 0, s>>>(reinterpret_cast<const typename Stor<ST>::E*>(A), boxes[box],
+                                                   what, reinterpret_cast<typename Stor<ST>::R*>(dst));
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t Launch<ST>::read_dev(const void* A, int64_t count, void* dst, cudaStream_t s)
+{
+    k_read_dev<ST><<<grid_for(count, 256), 256, 0, s>>>(reinterpret_cast<const typename Stor<ST>::E*>(A), count,
+                                                        reinterpret_cast<typename Stor<ST>::R*>(dst));
+    return cudaGetLastError();
+}
+
+template <int ST>
+cudaError_t Launch<ST>::conservation(const void* A, const BoxDev* boxes, const ChainDev* chains, int nboxes,
+                                     int64_t chunks, const double* vel, double* partial, double* out,
+                                     int32_t* status, cudaStream_t s)
+{
+    dim3 grid((unsigned)chunks, (unsigned)nboxes);
+    k_cons_partial<ST><<<grid, kConsThreads, 0, s>>>(A, boxes, chunks, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_cons_final<<<(nboxes + 127) / 128, 128, 0, s>>>(boxes, chains, nboxes, chunks, partial, vel, out, status);
+    return cudaGetLastError();
+}
+
+}  // namespace lbt

@@ -1,0 +1,306 @@
+"""Python binding of the C ABI in include/lbtracer.h (argument marshalling only).
+
+Every function of the C ABI is exposed under the same name; the ``Tracers``
+class bundles a context with its caller-owned device arena (a torch uint8
+tensor) and the stream it runs on.  All arithmetic of the method runs in the
+CUDA kernels of liblbtracer.so; there is no CPU path: loading fails loudly when
+the library or a CUDA device is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_FENE, LB_ERR_BEAD_OOB = 0, 1, 2, 3, 4
+LB_ERR_NONFINITE, LB_ERR_TIMEOUT, LB_ERR_STATE, LB_ERR_SIZE = 5, 6, 7, 8
+LB_STORE_F64, LB_STORE_F32, LB_STORE_F16DEV, LB_STORE_BF16DEV = 0, 1, 2, 3
+LB_FACE_VELOCITY, LB_FACE_PERIODIC = 0, 1
+LB_TIME_LINEAR, LB_TIME_HERMITE, LB_TIME_MLP = 0, 1, 2
+LB_FIELD_RHO, LB_FIELD_U, LB_FIELD_DEV, LB_FIELD_CHAIN, LB_FIELD_ASYNC = 0, 1, 2, 3, 0x100
+LB_ALL_BOXES = -1
+
+ERROR_NAMES = {0: "LB_OK", 1: "LB_ERR_ARG", 2: "LB_ERR_CUDA", 3: "LB_ERR_FENE", 4: "LB_ERR_BEAD_OOB",
+               5: "LB_ERR_NONFINITE", 6: "LB_ERR_TIMEOUT", 7: "LB_ERR_STATE", 8: "LB_ERR_SIZE"}
+
+EXPORTS = ["lb_plan", "lb_create", "lb_destroy", "lb_init", "lb_set_boundary", "chain_couple", "lb_step",
+           "lb_graph_capture", "lb_graph_launch", "lb_read_fields", "lb_conservation", "lb_sync", "lb_status",
+           "lb_current_step", "lb_set_launch", "lb_profile", "lb_profile_read", "lb_last_error", "lb_synth_workspace_bytes", "lb_synth_faces",
+           "lb_synth_volume"]
+
+
+class lb_box_desc(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_int32), ("face_mode", ctypes.c_int32 * 6), ("time_interp", ctypes.c_int32),
+                ("K", ctypes.c_int32), ("nbeads", ctypes.c_int32), ("tau", ctypes.c_double),
+                ("rho_b", ctypes.c_double), ("body_accel", ctypes.c_double * 3)]
+
+
+class lb_chain_desc(ctypes.Structure):
+    _fields_ = [("nbeads", ctypes.c_int32), ("n_md", ctypes.c_int32), ("pin_com", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("k_fene", ctypes.c_double), ("R0", ctypes.c_double),
+                ("zeta", ctypes.c_double), ("mass", ctypes.c_double), ("kT", ctypes.c_double),
+                ("f_ext", ctypes.c_double * 3), ("seed", ctypes.c_uint64)]
+
+
+class LBError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (ERROR_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+_lib = None
+_vp, _i32, _i64, _f64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+
+
+def load(path: str | None = None, build_if_missing: bool = True):
+    """Load liblbtracer.so (building it in place with nvcc if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise OSError("liblbtracer.so is not built (run paper_0809_4958_gb300/build.py)")
+            _build.build()
+    lib = ctypes.CDLL(path)
+    sig = {
+        "lb_plan": (_i32, [ctypes.POINTER(lb_box_desc), _i32, _i32, ctypes.POINTER(_sz)]),
+        "lb_create": (_i32, [ctypes.POINTER(lb_box_desc), _i32, _i32, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+        "lb_destroy": (_i32, [_vp]),
+        "lb_init": (_i32, [_vp, _i32, _vp]),
+        "lb_set_boundary": (_i32, [_vp, _i32, _i64, _vp]),
+        "chain_couple": (_i32, [_vp, _i32, ctypes.POINTER(lb_chain_desc), _vp, _vp]),
+        "lb_step": (_i32, [_vp, _i32]),
+        "lb_graph_capture": (_i32, [_vp, _i32]),
+        "lb_graph_launch": (_i32, [_vp]),
+        "lb_read_fields": (_i32, [_vp, _i32, _i32, _vp]),
+        "lb_conservation": (_i32, [_vp, _i32, _vp]),
+        "lb_sync": (_i32, [_vp, _i32]),
+        "lb_status": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
+        "lb_current_step": (_i64, [_vp]),
+        "lb_set_launch": (_i32, [_vp, _i32, _i32]),
+        "lb_profile": (_i32, [_vp, _i32, _i32]),
+        "lb_profile_read": (_i32, [_vp, ctypes.POINTER(_f64), ctypes.POINTER(_i64)]),
+        "lb_last_error": (ctypes.c_char_p, [_vp]),
+        "lb_synth_workspace_bytes": (_sz, [_i32, _i32]),
+        "lb_synth_faces": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _i32, _i64, _i64, _i32, _vp, _vp, _vp]),
+        "lb_synth_volume": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _f64, _i32, _vp, _vp, _vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code: int, ctx=None):
+    if code != LB_OK:
+        msg = load().lb_last_error(ctx)
+        raise LBError(code, msg.decode() if msg else "")
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor or numpy array (or an int)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    assert x.is_contiguous()
+    return x.data_ptr()
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("lbtracer needs a CUDA device; there is no CPU fallback")
+    return torch
+
+
+def box_desc(E, tau, periodic=(False, False, False), time_interp=LB_TIME_LINEAR, K=1, nbeads=0, rho_b=1.0,
+             accel=(0.0, 0.0, 0.0)) -> lb_box_desc:
+    d = lb_box_desc()
+    d.E = int(E)
+    for a in range(3):
+        m = LB_FACE_PERIODIC if periodic[a] else LB_FACE_VELOCITY
+        d.face_mode[2 * a] = m
+        d.face_mode[2 * a + 1] = m
+        d.body_accel[a] = float(accel[a])
+    d.time_interp = int(time_interp)
+    d.K = int(K)
+    d.nbeads = int(nbeads)
+    d.tau = float(tau)
+    d.rho_b = float(rho_b)
+    return d
+
+
+def chain_desc(nbeads, k_fene=30.0, R0=1.5, zeta=1.0, mass=1.0, kT=0.0, seed=0, n_md=50, pin_com=2,
+               f_ext=(0.0, 0.0, 0.0)) -> lb_chain_desc:
+    c = lb_chain_desc()
+    c.nbeads, c.n_md, c.pin_com = int(nbeads), int(n_md), int(pin_com)
+    c.k_fene, c.R0, c.zeta, c.mass, c.kT = float(k_fene), float(R0), float(zeta), float(mass), float(kT)
+    for a in range(3):
+        c.f_ext[a] = float(f_ext[a])
+    c.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    return c
+
+
+class Tracers:
+    """A context of one or more tracer boxes on one GPU.
+
+    boxes: list of lb_box_desc; storage: LB_STORE_*; stream: torch.cuda.Stream
+    (default: a new stream on the current device).
+    """
+
+    def __init__(self, boxes, storage=LB_STORE_F32, stream=None):
+        torch = _torch()
+        lib = load()
+        self.torch = torch
+        self.lib = lib
+        self.storage = storage
+        self.descs = list(boxes)
+        arr = (lb_box_desc * len(self.descs))(*self.descs)
+        self._arr = arr
+        nbytes = _sz()
+        _check(lib.lb_plan(arr, len(self.descs), storage, ctypes.byref(nbytes)))
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.arena = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.stream.device)
+        ctx = _vp()
+        _check(lib.lb_create(arr, len(self.descs), storage, self.arena.data_ptr(), nbytes.value,
+                             self.stream.cuda_stream, ctypes.byref(ctx)))
+        self.ctx = ctx
+        self.real = torch.float64 if storage == LB_STORE_F64 else torch.float32
+        self.np_real = np.float64 if storage == LB_STORE_F64 else np.float32
+
+    # ---- thin wrappers (same names as the C ABI) ----
+    def lb_init(self, box, u0):
+        _check(self.lib.lb_init(self.ctx, box, _ptr(u0)), self.ctx)
+
+    def lb_set_boundary(self, box, j, face_u):
+        _check(self.lib.lb_set_boundary(self.ctx, box, int(j), _ptr(face_u)), self.ctx)
+
+    def chain_couple(self, box, desc: lb_chain_desc, pos0, vel0=None):
+        _check(self.lib.chain_couple(self.ctx, box, ctypes.byref(desc), _ptr(pos0), _ptr(vel0)), self.ctx)
+
+    def lb_step(self, nsteps=1):
+        _check(self.lib.lb_step(self.ctx, int(nsteps)), self.ctx)
+
+    def lb_graph_capture(self, nsteps):
+        _check(self.lib.lb_graph_capture(self.ctx, int(nsteps)), self.ctx)
+
+    def lb_graph_launch(self):
+        _check(self.lib.lb_graph_launch(self.ctx), self.ctx)
+
+    def lb_read_fields(self, box, what, dst):
+        _check(self.lib.lb_read_fields(self.ctx, box, what, _ptr(dst)), self.ctx)
+
+    def lb_conservation(self, box):
+        out = np.zeros(7)
+        _check(self.lib.lb_conservation(self.ctx, box, out.ctypes.data), self.ctx)
+        return out
+
+    def lb_sync(self, timeout_ms=120000):
+        _check(self.lib.lb_sync(self.ctx, int(timeout_ms)), self.ctx)
+
+    def lb_status(self, box):
+        st = _i32()
+        _check(self.lib.lb_status(self.ctx, box, ctypes.byref(st)), self.ctx)
+        return int(st.value)
+
+    def lb_current_step(self):
+        return int(self.lib.lb_current_step(self.ctx))
+
+    def lb_set_launch(self, threads, ctas=0):
+        _check(self.lib.lb_set_launch(self.ctx, int(threads), int(ctas)), self.ctx)
+
+    def lb_profile(self, enable, max_launches=0):
+        _check(self.lib.lb_profile(self.ctx, int(enable), int(max_launches)), self.ctx)
+
+    def lb_profile_read(self):
+        ms, n = _f64(), _i64()
+        _check(self.lib.lb_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n)), self.ctx)
+        return float(ms.value), int(n.value)
+
+    def lb_destroy(self):
+        if self.ctx:
+            self.lib.lb_destroy(self.ctx)
+            self.ctx = None
+
+    # ---- conveniences ----
+    def E(self, box):
+        return self.descs[box].E
+
+    def fields(self, box):
+        """(rho [E,E,E], u [3,E,E,E]) as numpy arrays of the storage's real type."""
+        E = self.E(box)
+        rho = np.zeros((E, E, E), self.np_real)
+        u = np.zeros((3, E, E, E), self.np_real)
+        self.lb_read_fields(box, LB_FIELD_RHO, rho)
+        self.lb_read_fields(box, LB_FIELD_U, u)
+        return rho, u
+
+    def deviations(self, box):
+        E = self.E(box)
+        d = np.zeros((19, E, E, E), self.np_real)
+        self.lb_read_fields(box, LB_FIELD_DEV, d)
+        return d
+
+    def chain(self, box, nbeads):
+        out = np.zeros((2, nbeads, 3))
+        self.lb_read_fields(box, LB_FIELD_CHAIN, out)
+        return out[0], out[1]
+
+    def close(self):
+        self.lb_destroy()
+
+    def __del__(self):
+        try:
+            self.lb_destroy()
+        except Exception:
+            pass
+
+
+def modes_to_device(modes, device="cuda"):
+    """Mode table (inputs.Modes) as four float64 device tensors."""
+    torch = _torch()
+    return tuple(torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(device)
+                 for a in (modes.kvec, modes.amp, modes.omega, modes.phi))
+
+
+def synth_faces(modes, E, K, j0, nsamp, dtype, stream=None, out=None):
+    """Coarse face samples [nsamp][6][3][E][E] of the synthetic flow on the GPU."""
+    torch = _torch()
+    lib = load()
+    stream = stream or torch.cuda.current_stream()
+    kv, am, om, ph = modes_to_device(modes)
+    if out is None:
+        out = torch.empty((nsamp, 6, 3, E, E), dtype=dtype, device="cuda")
+    ws = torch.empty(int(lib.lb_synth_workspace_bytes(modes.M, E)), dtype=torch.uint8, device="cuda")
+    code = LB_STORE_F64 if dtype == torch.float64 else LB_STORE_F32
+    with torch.cuda.stream(stream):
+        _check(lib.lb_synth_faces(kv.data_ptr(), am.data_ptr(), om.data_ptr(), ph.data_ptr(), modes.M, E, K, j0,
+                                  nsamp, code, out.data_ptr(), ws.data_ptr(), stream.cuda_stream))
+    stream.synchronize()
+    return out
+
+
+def synth_volume(modes, E, t, dtype, stream=None):
+    """The synthetic flow on every site at time t: [3][E][E][E] on the GPU."""
+    torch = _torch()
+    lib = load()
+    stream = stream or torch.cuda.current_stream()
+    kv, am, om, ph = modes_to_device(modes)
+    out = torch.empty((3, E, E, E), dtype=dtype, device="cuda")
+    ws = torch.empty(int(lib.lb_synth_workspace_bytes(modes.M, E)), dtype=torch.uint8, device="cuda")
+    code = LB_STORE_F64 if dtype == torch.float64 else LB_STORE_F32
+    _check(lib.lb_synth_volume(kv.data_ptr(), am.data_ptr(), om.data_ptr(), ph.data_ptr(), modes.M, E, float(t),
+                               code, out.data_ptr(), ws.data_ptr(), stream.cuda_stream))
+    stream.synchronize()
+    return out

