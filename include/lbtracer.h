@@ -16,7 +16,8 @@
  *     in time between coarse samples (Sec. 3, after Eq. 1);
  *   - a bead-spring chain coupled to the fluid through a Stokes friction
  *     coefficient (Sec. 1, Ahlrichs-Duenweg hybrid method) with its centre of
- *     mass pinned at the tracer, i.e. the box centre (Sec. 2).
+ *     mass pinned at the tracer, i.e. the box centre (Sec. 2).  The chain is
+ *     the Kremer-Grest model of that method: FENE bonds plus WCA repulsion.
  *
  * Conventions
  *   Lattice units throughout (spacing 1, time step 1, reference density 1).
@@ -67,6 +68,7 @@ extern "C" {
 #define LB_ERR_TIMEOUT 6    /* a bounded wait for the stream expired */
 #define LB_ERR_STATE 7      /* call out of order (e.g. stepping past the last boundary sample) */
 #define LB_ERR_SIZE 8       /* arena too small for the plan */
+#define LB_ERR_CHAIN 9      /* a bead has more WCA neighbours than the per-bead list holds (48) */
 
 /* ---- population storage (one per context) ---- */
 #define LB_STORE_F64 0      /* f_i - w_i in FP64, FP64 arithmetic */
@@ -113,6 +115,8 @@ typedef struct lb_chain_desc {
     double zeta;           /* bead friction coefficient (Stokes friction of the coupling) */
     double mass;           /* bead mass */
     double kT;             /* temperature of the bead noise (0 = none) */
+    double eps;            /* WCA repulsion strength between all bead pairs (0 = FENE bonds only) */
+    double sigma;          /* WCA length; the repulsion acts below 2^(1/6) sigma */
     double f_ext[3];       /* constant external force on every bead */
     uint64_t seed;         /* Philox key of the bead noise */
 } lb_chain_desc;

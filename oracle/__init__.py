@@ -73,6 +73,8 @@ class _Chain(ctypes.Structure):
         ("zeta", ctypes.c_double),
         ("mass", ctypes.c_double),
         ("kT", ctypes.c_double),
+        ("eps", ctypes.c_double),
+        ("sigma", ctypes.c_double),
         ("f_ext", ctypes.c_double * 3),
         ("seed", ctypes.c_uint64),
         ("box_id", ctypes.c_uint64),
@@ -90,7 +92,7 @@ def _load():
         lib.orc_step.restype = ctypes.c_int
         lib.orc_run.restype = ctypes.c_int
         lib.orc_chain_couple.restype = ctypes.c_int
-        lib.orc_fene_forces.restype = ctypes.c_int
+        lib.orc_chain_forces.restype = ctypes.c_int
         lib.orc_interp_velocity.restype = ctypes.c_int
         lib.orc_face_velocity.restype = ctypes.c_int
         lib.orc_round_f16.restype = ctypes.c_double
@@ -143,13 +145,16 @@ class BoxParams:
 
 @dataclass
 class ChainParams:
-    """FENE bead-spring chain coupled by Stokes friction."""
+    """Kremer-Grest bead-spring chain (FENE bonds + WCA repulsion) coupled by
+    Stokes friction; eps = 0 leaves FENE bonds only."""
     nbeads: int
     k_fene: float = 30.0
     R0: float = 1.5
     zeta: float = 1.0
     mass: float = 1.0
     kT: float = 0.0
+    eps: float = 1.0
+    sigma: float = 1.0
     seed: int = 0
     n_md: int = 50
     pin_com: int = 2
@@ -162,6 +167,7 @@ class ChainParams:
         ch.n_md = self.n_md
         ch.pin_com = self.pin_com
         ch.k_fene, ch.R0, ch.zeta, ch.mass, ch.kT = self.k_fene, self.R0, self.zeta, self.mass, self.kT
+        ch.eps, ch.sigma = self.eps, self.sigma
         for a in range(3):
             ch.f_ext[a] = float(self.f_ext[a])
         ch.seed = int(self.seed) & 0xFFFFFFFFFFFFFFFF
@@ -203,11 +209,13 @@ def philox4x64_10(ctr, key):
     return out
 
 
-def fene_forces(pos, k, R0):
+def chain_forces(pos, k, R0, eps=1.0, sigma=1.0):
+    """(status, F [N][3]) of the FENE + WCA chain at positions pos [N][3]."""
     lib = _load()
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     F = np.zeros_like(pos)
-    st = lib.orc_fene_forces(ctypes.c_int(pos.shape[0]), ctypes.c_double(k), ctypes.c_double(R0), _ptr(pos), _ptr(F))
+    st = lib.orc_chain_forces(ctypes.c_int(pos.shape[0]), ctypes.c_double(k), ctypes.c_double(R0),
+                              ctypes.c_double(eps), ctypes.c_double(sigma), _ptr(pos), _ptr(F))
     return st, F
 
 

@@ -83,6 +83,7 @@ typedef struct {
     int32_t pin_com; /* 0 off, 1 position, 2 position and velocity */
     int32_t pad;
     double k_fene, R0, zeta, mass, kT;
+    double eps, sigma; /* WCA repulsion between all bead pairs (eps = 0: FENE only) */
     double f_ext[3]; /* constant external force on every bead (tests only) */
     uint64_t seed;
     uint64_t box_id;
@@ -376,10 +377,15 @@ int orc_interp_velocity(const orc_box *b, const double *A, const double R[3], do
     return ORC_OK;
 }
 
-/* FENE force on every bead of a linear chain: U(r) = -k R0^2/2 ln(1 - r^2/R0^2)
- * per bond, force on bead b+1 is -k r / (1 - r^2/R0^2) with r = R_{b+1} - R_b,
- * and the opposite force on bead b. */
-int orc_fene_forces(int nbeads, double k, double R0, const double *R, double *F)
+/* Kremer-Grest bead-spring forces on every bead of a linear chain (the chain
+ * model of the Ahlrichs-Duenweg hybrid method the paper builds on, Sec. 1):
+ *   FENE per bond, U(r) = -k R0^2/2 ln(1 - r^2/R0^2): force on bead b+1 is
+ *     -k r / (1 - r^2/R0^2) with r = R_{b+1} - R_b, the opposite on bead b;
+ *   WCA between every pair, U(r) = 4 eps ((s/r)^12 - (s/r)^6) + eps for
+ *     r < 2^(1/6) s: force on bead j is 24 eps (2 (s/r)^12 - (s/r)^6) r / r^2
+ *     with r = R_j - R_i, the opposite on bead i.
+ * Bond terms are added first, then pair terms in increasing partner order. */
+int orc_chain_forces(int nbeads, double k, double R0, double eps, double sigma, const double *R, double *F)
 {
     for (int i = 0; i < 3 * nbeads; i++) F[i] = 0.0;
     for (int bb = 0; bb + 1 < nbeads; bb++) {
@@ -395,6 +401,24 @@ int orc_fene_forces(int nbeads, double k, double R0, const double *R, double *F)
             F[3 * (bb + 1) + a] -= fac * r[a];
         }
     }
+    if (eps > 0.0) {
+        double rc2 = cbrt(2.0) * sigma * sigma; /* (2^(1/6) sigma)^2 */
+        for (int i = 0; i < nbeads; i++)
+            for (int j = i + 1; j < nbeads; j++) {
+                double r[3], r2 = 0.0;
+                for (int a = 0; a < 3; a++) {
+                    r[a] = R[3 * j + a] - R[3 * i + a];
+                    r2 += r[a] * r[a];
+                }
+                if (r2 >= rc2) continue;
+                double s2 = sigma * sigma / r2, s6 = s2 * s2 * s2;
+                double fac = 24.0 * eps * (2.0 * s6 * s6 - s6) / r2;
+                for (int a = 0; a < 3; a++) {
+                    F[3 * i + a] -= fac * r[a];
+                    F[3 * j + a] += fac * r[a];
+                }
+            }
+    }
     return ORC_OK;
 }
 
@@ -405,8 +429,8 @@ int orc_fene_forces(int nbeads, double k, double R0, const double *R, double *F)
  *   1. fluid velocity at each bead from the pulled populations of A,
  *      trilinear in the start-of-step position;
  *   2. n_md substeps of symplectic Euler (V += dt F / m, R += dt V), with
- *      FENE + friction -zeta (V - u) + noise sqrt(2 kT zeta / dt) xi + f_ext,
- *      u frozen over the step;
+ *      FENE + WCA + friction -zeta (V - u) + noise sqrt(2 kT zeta / dt) xi
+ *      + f_ext, u frozen over the step;
  *   3. centre of mass pinned at the box centre ((E-1)/2 on each axis);
  *   4. the momentum the beads gave to the fluid, -sum (F_fric + F_noise) dt,
  *      spread with the start-of-step trilinear weights into g[3][E^3]
@@ -444,7 +468,7 @@ int orc_chain_couple(const orc_box *b, const orc_chain *ch, const double *A, lon
     double dt = 1.0 / ch->n_md;
     double noise_amp = ch->kT > 0.0 ? sqrt(2.0 * ch->kT * ch->zeta / dt) : 0.0;
     for (int sub = 0; sub < ch->n_md && !st; sub++) {
-        st = orc_fene_forces(N, ch->k_fene, ch->R0, pos, F);
+        st = orc_chain_forces(N, ch->k_fene, ch->R0, ch->eps, ch->sigma, pos, F);
         if (st) break;
         for (int bb = 0; bb < N; bb++) {
             double xi[3] = {0.0, 0.0, 0.0};

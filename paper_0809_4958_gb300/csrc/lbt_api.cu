@@ -527,7 +527,8 @@ int32_t chain_couple(lb_ctx* ctx, int32_t box, const lb_chain_desc* d, const dou
     const int ci = ctx->boxes[box].chain;
     if (ci < 0) return ctx->fail(LB_ERR_ARG, "box was planned without chain capacity (nbeads = 0)");
     if (d->nbeads < 1 || d->nbeads > ctx->desc[box].nbeads || d->n_md < 1 || !(d->mass > 0) || d->kT < 0 ||
-        !(d->R0 > 0) || d->zeta < 0 || d->pin_com < 0 || d->pin_com > 2)
+        !(d->R0 > 0) || d->zeta < 0 || d->pin_com < 0 || d->pin_com > 2 || d->eps < 0 ||
+        (d->eps > 0 && !(d->sigma > 0)))
         return ctx->fail(LB_ERR_ARG, "invalid chain description");
     ChainDev& ch = ctx->chains[ci];
     ch.nbeads = d->nbeads;
@@ -538,6 +539,8 @@ int32_t chain_couple(lb_ctx* ctx, int32_t box, const lb_chain_desc* d, const dou
     ch.zeta = d->zeta;
     ch.mass = d->mass;
     ch.kT = d->kT;
+    ch.eps = d->eps;
+    ch.sigma = d->sigma;
     for (int a = 0; a < 3; a++) ch.f_ext[a] = d->f_ext[a];
     ch.seed = d->seed;
     const size_t bytes = sizeof(double) * 3 * d->nbeads;

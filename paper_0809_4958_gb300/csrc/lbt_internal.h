@@ -39,6 +39,7 @@ struct ChainDev {
     int64_t bead_off;   // offset in beads into the position / velocity arrays
     int64_t force_off;  // offset in entries into the force list (8 per bead)
     double k_fene, R0, zeta, mass, kT;
+    double eps, sigma;  // WCA repulsion (eps = 0: FENE only)
     double f_ext[3];
     uint64_t seed;
 };

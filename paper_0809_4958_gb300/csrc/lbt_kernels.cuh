@@ -10,6 +10,8 @@
 //   k_forced                          re-collide the forced sites with the
 //                                     bead force, advance the step counter
 #pragma once
+#include <type_traits>
+
 #include "lbt_device.cuh"
 
 namespace lbt {
@@ -252,14 +254,26 @@ __device__ __forceinline__ void moments(const A f[kQ], A& drho, A j[3])
 
 // ---------------------------------------------------------------------------
 // Bead coupling: one block per chain, one thread per bead in the MD phase.
+//
+// Chain model: Kremer-Grest bead-spring chain (FENE bonds plus WCA repulsion
+// between all pairs), coupled to the fluid by Stokes friction.  Positions are
+// FP64; forces, velocities and the momentum handed to the fluid use MT
+// (double for FP64 storage, float otherwise), with pair geometry taken from
+// positions relative to bead 0's start-of-step position.  WCA pairs come from
+// a Verlet list in shared memory, rebuilt whenever a bead has moved more than
+// half the skin since the last build, so no pair within the cut-off is missed.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void set_status(int32_t* st, int code) { atomicCAS(st, 0, code); }
 
+constexpr int kMaxNb = 48;              // Verlet neighbours per bead
+constexpr double kSkin = 0.3;           // Verlet skin (lattice units)
+
 template <int ST>
-__global__ void __launch_bounds__(256) k_bead_couple(BeadParams p)
+__global__ void __launch_bounds__(kMaxBeads) k_bead_couple(BeadParams p)
 {
     using S = Stor<ST>;
     using A = typename S::A;
+    using MT = typename std::conditional<ST == kF64, double, float>::type;
     const ChainDev& ch = p.chains[blockIdx.x];
     const int N = ch.nbeads;
     const int b = ch.box;
@@ -270,30 +284,35 @@ __global__ void __launch_bounds__(256) k_bead_couple(BeadParams p)
     const int64_t n = *p.step;
     const int tid = threadIdx.x;
 
-    __shared__ double sR[kMaxBeads][3];     // current positions (MD)
-    __shared__ double sU[kMaxBeads][3];     // fluid velocity at each bead
-    __shared__ double sP[kMaxBeads][3];     // momentum given to the fluid
-    __shared__ double sW[kMaxBeads][8];     // start-of-step trilinear weights
-    __shared__ int sBase[kMaxBeads][3];     // start-of-step stencil corner
-    __shared__ double sRed[2][32][3];
+    __shared__ double sR[kMaxBeads][3];      // current positions
+    __shared__ MT sX[kMaxBeads][3];          // positions relative to sRc (pair geometry)
+    __shared__ double sD[kMaxBeads][3];      // start-of-step offsets inside the stencil cell
+    __shared__ int sBase[kMaxBeads][3];      // start-of-step stencil corner
+    __shared__ MT sU[kMaxBeads][3];          // fluid velocity at each bead
+    __shared__ MT sP[kMaxBeads][3];          // momentum given to the fluid
+    __shared__ unsigned char sNb[kMaxBeads][kMaxNb];
+    __shared__ int sNbN[kMaxBeads];
+    __shared__ double sRc[3];
+    __shared__ double sRed[2][kMaxBeads / 32][3];
     __shared__ int sErr;
 
     double* pos = p.pos + 3 * ch.bead_off;
     double* vel = p.vel + 3 * ch.bead_off;
-    if (tid == 0) sErr = 0;
+    if (tid == 0) {
+        sErr = 0;
+        for (int a = 0; a < 3; a++) sRc[a] = pos[a];
+    }
     __syncthreads();
 
     // 1. stencil of the start-of-step position
-    double R[3] = {0, 0, 0}, V[3] = {0, 0, 0};
+    double R[3] = {0, 0, 0};
+    MT V[3] = {0, 0, 0};
     if (tid < N) {
         for (int a = 0; a < 3; a++) {
             R[a] = pos[3 * tid + a];
-            V[a] = vel[3 * tid + a];
-        }
-        double d[3];
-        for (int a = 0; a < 3; a++) {
+            V[a] = (MT)vel[3 * tid + a];
             const double fl = floor(R[a]);
-            d[a] = R[a] - fl;
+            sD[tid][a] = R[a] - fl;
             long long i0 = (long long)fl;
             if (!((per >> a) & 1)) {
                 if (i0 < 1 || i0 + 1 > Ei - 2) sErr = LB_ERR_BEAD_OOB;
@@ -302,11 +321,7 @@ __global__ void __launch_bounds__(256) k_bead_couple(BeadParams p)
                 sBase[tid][a] = (int)(((i0 % Ei) + Ei) % Ei);
             }
             sR[tid][a] = R[a];
-            sP[tid][a] = 0.0;
-        }
-        for (int c = 0; c < 8; c++) {
-            const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
-            sW[tid][c] = (cx ? d[0] : 1.0 - d[0]) * (cy ? d[1] : 1.0 - d[1]) * (cz ? d[2] : 1.0 - d[2]);
+            sX[tid][a] = (MT)(R[a] - sRc[a]);
         }
     }
     __syncthreads();
@@ -314,6 +329,10 @@ __global__ void __launch_bounds__(256) k_bead_couple(BeadParams p)
         if (tid == 0) set_status(&p.status[b], sErr);
         return;
     }
+    auto weight = [&](int bb, int c) -> double {
+        const double d0 = sD[bb][0], d1 = sD[bb][1], d2 = sD[bb][2];
+        return ((c & 1) ? d0 : 1.0 - d0) * ((c & 2) ? d1 : 1.0 - d1) * ((c & 4) ? d2 : 1.0 - d2);
+    };
 
     // 2. fluid velocity at the beads: eight threads per bead, one corner each
     const typename S::E* Ab = reinterpret_cast<const typename S::E*>(p.A) + bd.f_off;
@@ -330,11 +349,8 @@ __global__ void __launch_bounds__(256) k_bead_couple(BeadParams p)
             pull_site<ST>(Ab, n3, Ei, per, s[0], s[1], s[2], f);
             moments<A>(f, dr, j);
             const A rho = A(1) + dr;
-            const double wgt8 = sW[bb][c];
-            for (int a = 0; a < 3; a++) {
-                const A ua = (j[a] + A(0.5) * rho * (A)bd.accel[a]) / rho;
-                uc[a] = wgt8 * (double)ua;
-            }
+            const double w8 = weight(bb, c);
+            for (int a = 0; a < 3; a++) uc[a] = w8 * (double)((j[a] + A(0.5) * rho * (A)bd.accel[a]) / rho);
         }
         for (int a = 0; a < 3; a++) {
             uc[a] += __shfl_xor_sync(0xffffffffu, uc[a], 1);
@@ -342,56 +358,114 @@ __global__ void __launch_bounds__(256) k_bead_couple(BeadParams p)
             uc[a] += __shfl_xor_sync(0xffffffffu, uc[a], 4);
         }
         if (act && (e & 7) == 0)
-            for (int a = 0; a < 3; a++) sU[e >> 3][a] = uc[a];
+            for (int a = 0; a < 3; a++) sU[e >> 3][a] = (MT)uc[a];
     }
-    __syncthreads();
 
     // 3. MD substeps (symplectic Euler), fluid velocity frozen over the step
-    const double dt = 1.0 / ch.n_md;
-    const double namp = ch.kT > 0.0 ? sqrt(2.0 * ch.kT * ch.zeta / dt) : 0.0;
-    const double R02 = ch.R0 * ch.R0;
-    double P[3] = {0, 0, 0};
+    const MT dt = MT(1) / (MT)ch.n_md;
+    const double dtd = 1.0 / ch.n_md;
+    const MT namp = ch.kT > 0.0 ? (MT)sqrt(2.0 * ch.kT * ch.zeta / dtd) : MT(0);
+    const MT R02 = (MT)(ch.R0 * ch.R0), kf = (MT)ch.k_fene, zeta = (MT)ch.zeta, dtm = dt / (MT)ch.mass;
+    const bool wca = ch.eps > 0.0;
+    const MT sig2 = (MT)(ch.sigma * ch.sigma), rc2 = (MT)(cbrt(2.0) * ch.sigma * ch.sigma), e24 = (MT)(24.0 * ch.eps);
+    const MT rl = (MT)(sqrt(cbrt(2.0)) * ch.sigma + kSkin), rl2 = rl * rl;  // WCA cut-off 2^(1/6) sigma + skin
+    const MT half_skin2 = (MT)(0.25 * kSkin * kSkin);
+    MT Xref[3] = {0, 0, 0};
+    MT P[3] = {0, 0, 0};
+    bool need_build = true;
+    __syncthreads();
     for (int sub = 0; sub < ch.n_md; sub++) {
-        if (tid < N) {
-            double F[3] = {0, 0, 0};
-            if (tid > 0) {  // bond (tid-1, tid): force -k r / (1 - r^2/R0^2) on the upper bead
-                double r[3], r2 = 0;
+        if (wca) {
+            bool moved = false;
+            if (tid < N && !need_build) {
+                MT d2 = 0;
                 for (int a = 0; a < 3; a++) {
-                    r[a] = sR[tid][a] - sR[tid - 1][a];
+                    const MT d = sX[tid][a] - Xref[a];
+                    d2 += d * d;
+                }
+                moved = d2 > half_skin2;
+            }
+            if (__syncthreads_or(moved) || need_build) {
+                if (tid < N) {
+                    int cnt = 0;
+                    for (int b2 = 0; b2 < N; b2++) {
+                        if (b2 == tid) continue;
+                        MT d2 = 0;
+                        for (int a = 0; a < 3; a++) {
+                            const MT d = sX[tid][a] - sX[b2][a];
+                            d2 += d * d;
+                        }
+                        if (d2 < rl2) {
+                            if (cnt < kMaxNb) sNb[tid][cnt] = (unsigned char)b2;
+                            cnt++;
+                        }
+                    }
+                    if (cnt > kMaxNb) sErr = LB_ERR_CHAIN;  // more neighbours than the list holds
+                    sNbN[tid] = cnt < kMaxNb ? cnt : kMaxNb;
+                    for (int a = 0; a < 3; a++) Xref[a] = sX[tid][a];
+                }
+                need_build = false;
+            }
+        }
+        if (tid < N) {
+            MT F[3] = {0, 0, 0};
+            if (tid > 0) {  // bond (tid-1, tid): force -k r / (1 - r^2/R0^2) on the upper bead
+                MT r[3], r2 = 0;
+                for (int a = 0; a < 3; a++) {
+                    r[a] = sX[tid][a] - sX[tid - 1][a];
                     r2 += r[a] * r[a];
                 }
                 if (r2 >= R02) sErr = LB_ERR_FENE;
-                const double fac = ch.k_fene / (1.0 - r2 / R02);
+                const MT fac = kf / (MT(1) - r2 / R02);
                 for (int a = 0; a < 3; a++) F[a] -= fac * r[a];
             }
             if (tid + 1 < N) {  // bond (tid, tid+1): opposite force on the lower bead
-                double r[3], r2 = 0;
+                MT r[3], r2 = 0;
                 for (int a = 0; a < 3; a++) {
-                    r[a] = sR[tid + 1][a] - sR[tid][a];
+                    r[a] = sX[tid + 1][a] - sX[tid][a];
                     r2 += r[a] * r[a];
                 }
                 if (r2 >= R02) sErr = LB_ERR_FENE;
-                const double fac = ch.k_fene / (1.0 - r2 / R02);
+                const MT fac = kf / (MT(1) - r2 / R02);
                 for (int a = 0; a < 3; a++) F[a] += fac * r[a];
             }
-            double xi[3] = {0, 0, 0};
-            if (namp > 0.0) {
+            if (wca) {  // WCA: 24 eps (2 (s/r)^12 - (s/r)^6) / r^2 along R_tid - R_partner
+                const int cnt = sNbN[tid];
+                for (int k = 0; k < cnt; k++) {
+                    const int b2 = sNb[tid][k];
+                    MT r[3], r2 = 0;
+                    for (int a = 0; a < 3; a++) {
+                        r[a] = sX[tid][a] - sX[b2][a];
+                        r2 += r[a] * r[a];
+                    }
+                    if (r2 < rc2) {
+                        const MT s2 = sig2 / r2, s6 = s2 * s2 * s2;
+                        const MT fac = e24 * (MT(2) * s6 * s6 - s6) / r2;
+                        for (int a = 0; a < 3; a++) F[a] += fac * r[a];
+                    }
+                }
+            }
+            MT xi[3] = {0, 0, 0};
+            if (namp > MT(0)) {
                 uint64_t x[4] = {(uint64_t)n, (uint64_t)sub, (uint64_t)tid, (uint64_t)b};
                 philox4x64_10(x, ch.seed, 0);
-                for (int a = 0; a < 3; a++) xi[a] = unit_uniform(x[a]);
+                for (int a = 0; a < 3; a++) xi[a] = (MT)unit_uniform(x[a]);
             }
             for (int a = 0; a < 3; a++) {
-                const double ffric = -ch.zeta * (V[a] - sU[tid][a]);
-                const double fnoise = namp * xi[a];
-                const double ftot = F[a] + ffric + fnoise + ch.f_ext[a];
-                V[a] += dt / ch.mass * ftot;
-                R[a] += dt * V[a];
+                const MT ffric = -zeta * (V[a] - sU[tid][a]);
+                const MT fnoise = namp * xi[a];
+                const MT ftot = F[a] + ffric + fnoise + (MT)ch.f_ext[a];
+                V[a] += dtm * ftot;
+                R[a] += dtd * (double)V[a];
                 P[a] -= (ffric + fnoise) * dt;
             }
         }
         __syncthreads();
         if (tid < N)
-            for (int a = 0; a < 3; a++) sR[tid][a] = R[a];
+            for (int a = 0; a < 3; a++) {
+                sR[tid][a] = R[a];
+                sX[tid][a] = (MT)(R[a] - sRc[a]);
+            }
         __syncthreads();
         if (sErr) break;
     }
@@ -406,7 +480,7 @@ __global__ void __launch_bounds__(256) k_bead_couple(BeadParams p)
         for (int pass = 0; pass < 2; pass++) {
             double s[3];
             for (int a = 0; a < 3; a++) {
-                s[a] = tid < N ? (pass == 0 ? R[a] : V[a]) : 0.0;
+                s[a] = tid < N ? (pass == 0 ? R[a] : (double)V[a]) : 0.0;
                 for (int o = 16; o > 0; o >>= 1) s[a] += __shfl_xor_sync(0xffffffffu, s[a], o);
             }
             if (lane == 0)
@@ -423,13 +497,13 @@ __global__ void __launch_bounds__(256) k_bead_couple(BeadParams p)
         if (tid < N)
             for (int a = 0; a < 3; a++) {
                 R[a] += centre - com[a] / N;
-                if (ch.pin_com >= 2) V[a] -= vcm[a] / N;
+                if (ch.pin_com >= 2) V[a] = (MT)((double)V[a] - vcm[a] / N);
             }
     }
     if (tid < N) {
         for (int a = 0; a < 3; a++) {
             pos[3 * tid + a] = R[a];
-            vel[3 * tid + a] = V[a];
+            vel[3 * tid + a] = (double)V[a];
             sP[tid][a] = P[a];
         }
     }
@@ -457,8 +531,8 @@ __global__ void __launch_bounds__(256) k_bead_couple(BeadParams p)
             }
             if (!in) continue;
             if (b2 < bb) dup = true;
-            const double w8 = sW[b2][o[0] + 2 * o[1] + 4 * o[2]];
-            for (int a = 0; a < 3; a++) g[a] += w8 * sP[b2][a];
+            const double w8 = weight(b2, o[0] + 2 * o[1] + 4 * o[2]);
+            for (int a = 0; a < 3; a++) g[a] += w8 * (double)sP[b2][a];
         }
         ForceEntry fe;
         fe.site = dup ? -1 : (int32_t)(((int64_t)s[2] * Ei + s[1]) * Ei + s[0]);

@@ -23,8 +23,9 @@ Kolmogorov spectrum stands in for it:
              site, so the maximum is exact for E < 64 and a close lower bound
              of the true maximum above that).
 
-Bead chains start as seeded random walks (bond length 1, directions uniform
-on the sphere) translated so the centre of mass sits at the box centre,
+Bead chains start as seeded self-avoiding random walks (bond length 0.97,
+directions uniform on the sphere, every bead at least 1.0 from all earlier
+non-adjacent beads) translated so the centre of mass sits at the box centre,
 redrawn until every bead lies in [1, E - 2).
 """
 from __future__ import annotations
@@ -111,15 +112,26 @@ def single_mode(E: int, kvec, amp, omega: float = 0.0, phi: float = 0.0) -> Mode
                  omega=np.array([float(omega)]), phi=np.array([float(phi)]), E=E, u_max=0.0)
 
 
-def chain_start(seed: int, nbeads: int, E: int, bond: float = 1.0, max_tries: int = 1000) -> np.ndarray:
-    """Random-walk chain start [nbeads][3] centred at ((E-1)/2)^3, all beads in [1, E-2)."""
+def chain_start(seed: int, nbeads: int, E: int, bond: float = 0.97, min_dist: float = 1.0,
+                max_tries: int = 1000) -> np.ndarray:
+    """Self-avoiding random-walk chain start [nbeads][3] centred at
+    ((E-1)/2)^3, all beads in [1, E-2)."""
     rng = _rng(seed, 2)
     centre = 0.5 * (E - 1)
     for _ in range(max_tries):
-        steps = _unit_vectors(rng, max(nbeads - 1, 0)) * bond
         pos = np.zeros((nbeads, 3))
-        if nbeads > 1:
-            pos[1:] = np.cumsum(steps, axis=0)
+        ok = True
+        for b in range(1, nbeads):
+            for _attempt in range(200):
+                cand = pos[b - 1] + bond * _unit_vectors(rng, 1)[0]
+                if b < 2 or np.min(np.sum((pos[:b - 1] - cand) ** 2, axis=1)) >= min_dist ** 2:
+                    pos[b] = cand
+                    break
+            else:
+                ok = False
+                break
+        if not ok:
+            continue
         pos += centre - pos.mean(axis=0)
         if np.all(pos >= 1.0) and np.all(pos < E - 2):
             return np.ascontiguousarray(pos)

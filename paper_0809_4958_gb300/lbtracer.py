@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_FENE, LB_ERR_BEAD_OOB = 0, 1, 2, 3, 4
-LB_ERR_NONFINITE, LB_ERR_TIMEOUT, LB_ERR_STATE, LB_ERR_SIZE = 5, 6, 7, 8
+LB_ERR_NONFINITE, LB_ERR_TIMEOUT, LB_ERR_STATE, LB_ERR_SIZE, LB_ERR_CHAIN = 5, 6, 7, 8, 9
 LB_STORE_F64, LB_STORE_F32, LB_STORE_F16DEV, LB_STORE_BF16DEV = 0, 1, 2, 3
 LB_FACE_VELOCITY, LB_FACE_PERIODIC = 0, 1
 LB_TIME_LINEAR, LB_TIME_HERMITE, LB_TIME_MLP = 0, 1, 2
@@ -24,7 +24,7 @@ LB_FIELD_RHO, LB_FIELD_U, LB_FIELD_DEV, LB_FIELD_CHAIN, LB_FIELD_ASYNC = 0, 1, 2
 LB_ALL_BOXES = -1
 
 ERROR_NAMES = {0: "LB_OK", 1: "LB_ERR_ARG", 2: "LB_ERR_CUDA", 3: "LB_ERR_FENE", 4: "LB_ERR_BEAD_OOB",
-               5: "LB_ERR_NONFINITE", 6: "LB_ERR_TIMEOUT", 7: "LB_ERR_STATE", 8: "LB_ERR_SIZE"}
+               5: "LB_ERR_NONFINITE", 6: "LB_ERR_TIMEOUT", 7: "LB_ERR_STATE", 8: "LB_ERR_SIZE", 9: "LB_ERR_CHAIN"}
 
 EXPORTS = ["lb_plan", "lb_create", "lb_destroy", "lb_init", "lb_set_boundary", "chain_couple", "lb_step",
            "lb_graph_capture", "lb_graph_launch", "lb_read_fields", "lb_conservation", "lb_sync", "lb_status",
@@ -42,7 +42,8 @@ class lb_chain_desc(ctypes.Structure):
     _fields_ = [("nbeads", ctypes.c_int32), ("n_md", ctypes.c_int32), ("pin_com", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("k_fene", ctypes.c_double), ("R0", ctypes.c_double),
                 ("zeta", ctypes.c_double), ("mass", ctypes.c_double), ("kT", ctypes.c_double),
-                ("f_ext", ctypes.c_double * 3), ("seed", ctypes.c_uint64)]
+                ("eps", ctypes.c_double), ("sigma", ctypes.c_double), ("f_ext", ctypes.c_double * 3),
+                ("seed", ctypes.c_uint64)]
 
 
 class LBError(RuntimeError):
@@ -142,10 +143,11 @@ def box_desc(E, tau, periodic=(False, False, False), time_interp=LB_TIME_LINEAR,
 
 
 def chain_desc(nbeads, k_fene=30.0, R0=1.5, zeta=1.0, mass=1.0, kT=0.0, seed=0, n_md=50, pin_com=2,
-               f_ext=(0.0, 0.0, 0.0)) -> lb_chain_desc:
+               f_ext=(0.0, 0.0, 0.0), eps=1.0, sigma=1.0) -> lb_chain_desc:
     c = lb_chain_desc()
     c.nbeads, c.n_md, c.pin_com = int(nbeads), int(n_md), int(pin_com)
     c.k_fene, c.R0, c.zeta, c.mass, c.kT = float(k_fene), float(R0), float(zeta), float(mass), float(kT)
+    c.eps, c.sigma = float(eps), float(sigma)
     for a in range(3):
         c.f_ext[a] = float(f_ext[a])
     c.seed = int(seed) & 0xFFFFFFFFFFFFFFFF

@@ -87,17 +87,27 @@ def test_philox4x64_matches_numpy(orc):
         0x16554D9ECA36314C, 0xDB20FE9D672D0FDC, 0xD7E772CEE186176B, 0x7E68B68AEC7BA23B]
 
 
-def test_fene_force_is_minus_gradient(orc):
-    pos = inputs.chain_start(3, 8, 16) * 1.0
-    pos[3] += [0.1, -0.2, 0.05]
-    k, R0 = 30.0, 1.5
-    st, F = orc.fene_forces(pos, k, R0)
+@pytest.mark.parametrize("eps", [0.0, 1.0])
+def test_chain_force_is_minus_gradient(orc, eps):
+    # FENE bonds plus WCA pair repulsion (Kremer-Grest): force = -grad U
+    # a folded chain: beads 0 and 3 are a non-bonded contact inside the WCA range
+    pos = 5.0 + np.array([[0, 0, 0], [0.97, 0, 0], [0.97, 0.97, 0], [0.05, 1.0, 0.1], [-0.9, 1.3, 0.2],
+                          [-1.5, 2.1, 0.5], [-1.2, 3.0, 0.9], [-0.6, 3.7, 1.2]])
+    k, R0, sig = 30.0, 1.5, 1.0
+    st, F = orc.chain_forces(pos, k, R0, eps, sig)
     assert st == 0
 
     def U(p):
         r = np.diff(p, axis=0)
         r2 = (r * r).sum(1)
-        return float(np.sum(-0.5 * k * R0 ** 2 * np.log(1 - r2 / R0 ** 2)))
+        u = float(np.sum(-0.5 * k * R0 ** 2 * np.log(1 - r2 / R0 ** 2)))
+        for i in range(len(p)):
+            for j in range(i + 1, len(p)):
+                d2 = float(((p[j] - p[i]) ** 2).sum())
+                if d2 < 2 ** (1 / 3) * sig ** 2:
+                    s6 = (sig ** 2 / d2) ** 3
+                    u += 4 * eps * (s6 * s6 - s6) + eps
+        return u
 
     h = 1e-6
     for b in range(pos.shape[0]):
@@ -107,9 +117,10 @@ def test_fene_force_is_minus_gradient(orc):
             pm[b, a] -= h
             assert abs(-(U(pp) - U(pm)) / (2 * h) - F[b, a]) < 1e-6 * max(1.0, abs(F[b, a]))
     assert np.allclose(F.sum(0), 0.0, atol=1e-12)  # Newton's third law
+    assert float(((pos[3] - pos[0]) ** 2).sum()) < 2 ** (1 / 3)  # the contact is inside the WCA range
     bad = pos.copy()
     bad[5] = bad[4] + [1.6, 0, 0]
-    assert orc.fene_forces(bad, k, R0)[0] == orc.ERR_FENE
+    assert orc.chain_forces(bad, k, R0, eps, sig)[0] == orc.ERR_FENE
 
 
 def _face_series(E, J, fn):
