@@ -227,9 +227,12 @@ int32_t lb_status(lb_ctx* ctx, int32_t box, int32_t* status);
 int64_t lb_current_step(const lb_ctx* ctx);
 
 /* lb_set_launch -- launch shape of the stream-collide kernel: threads per
- * block (multiple of 32, 64 .. 1024) and a persistent grid of `ctas` blocks
- * (0 = one block per tile).  Used by the autotuner. */
-int32_t lb_set_launch(lb_ctx* ctx, int32_t threads, int32_t ctas);
+ * block (multiple of 32, 64 .. 256), a persistent grid of `ctas` blocks
+ * (0 = one block per tile) and the sites each thread updates per population
+ * load (0 = default: 2 for FP64, 4 for FP32, 8 for 16-bit storage; half the
+ * default is the other choice).  Used by the autotuner.  Drops a captured
+ * graph. */
+int32_t lb_set_launch(lb_ctx* ctx, int32_t threads, int32_t ctas, int32_t sites_per_thread);
 
 /*
  * lb_profile -- time every stream-collide launch with a pair of CUDA events

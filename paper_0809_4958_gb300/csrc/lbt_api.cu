@@ -142,7 +142,7 @@ struct lb_ctx {
     bool a_is_pop_a = true;            // which buffer holds the current state
     int64_t step = 0;                  // steps enqueued so far
     std::vector<int64_t> pushed;       // last boundary sample pushed per box (-1 none)
-    int threads = 256, ctas = 0;
+    int threads = 256, ctas = 0, vw = 0;  // vw: sites per thread in stream-collide
     std::vector<int64_t> tile_prefix;  // for the current block size
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
@@ -183,9 +183,11 @@ namespace {
      : (storage) == kF16 ? Launch<kF16>::expr            \
                          : Launch<kBF16>::expr)
 
+int default_vw(int storage) { return storage == kF64 ? 2 : (storage == kF32 ? 4 : 8); }
+
 int rebuild_tiles(lb_ctx* ctx)
 {
-    const int vw = ctx->storage == kF64 ? 2 : (ctx->storage == kF32 ? 4 : 8);
+    const int vw = ctx->vw;
     ctx->tile_prefix.assign(ctx->nboxes + 1, 0);
     for (int b = 0; b < ctx->nboxes; b++) {
         const int64_t groups = ctx->boxes[b].n3 / vw;
@@ -270,7 +272,7 @@ int enqueue_step(lb_ctx* ctx)
     sp.status = ctx->at<int32_t>(ctx->L.status);
     const bool timed = ctx->profiling && ctx->prof_used + 2 <= ctx->prof_ev.size();
     if (timed) CK(cudaEventRecord(ctx->prof_ev[ctx->prof_used], ctx->stream));
-    CK(DISPATCH(ctx->storage, stream_collide(sp, ctx->threads, ctx->ctas, ctx->stream)));
+    CK(DISPATCH(ctx->storage, stream_collide(sp, ctx->threads, ctx->ctas, ctx->vw, ctx->stream)));
     if (timed) {
         CK(cudaEventRecord(ctx->prof_ev[ctx->prof_used + 1], ctx->stream));
         ctx->prof_used += 2;
@@ -373,6 +375,7 @@ int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, voi
     ctx->arena = reinterpret_cast<char*>(arena);
     ctx->stream = reinterpret_cast<cudaStream_t>(stream);
     ctx->pushed.assign(nboxes, -1);
+    ctx->vw = default_vw(storage);
     cudaError_t e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
@@ -695,13 +698,16 @@ int32_t lb_status(lb_ctx* ctx, int32_t box, int32_t* status)
 
 int64_t lb_current_step(const lb_ctx* ctx) { return ctx ? ctx->step : -1; }
 
-int32_t lb_set_launch(lb_ctx* ctx, int32_t threads, int32_t ctas)
+int32_t lb_set_launch(lb_ctx* ctx, int32_t threads, int32_t ctas, int32_t sites_per_thread)
 {
     if (!ctx) return LB_ERR_ARG;
-    if (threads < 64 || threads > 256 || threads % 32 || ctas < 0)
-        return ctx->fail(LB_ERR_ARG, "threads must be a multiple of 32 in [64, 256], ctas >= 0");
+    const int dv = default_vw(ctx->storage);
+    const int vw = sites_per_thread == 0 ? dv : sites_per_thread;
+    if (threads < 64 || threads > 256 || threads % 32 || ctas < 0 || (vw != dv && vw != dv / 2))
+        return ctx->fail(LB_ERR_ARG, "threads: multiple of 32 in [64, 256]; ctas >= 0; sites_per_thread: default or half");
     ctx->threads = threads;
     ctx->ctas = ctas;
+    ctx->vw = vw;
     if (ctx->graph) {
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;

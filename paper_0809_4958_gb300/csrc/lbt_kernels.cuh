@@ -719,11 +719,14 @@ inline int grid_for(int64_t n, int threads, int cap = 152 * 16)
 }
 
 template <int ST>
-cudaError_t Launch<ST>::stream_collide(const SCParams& p, int threads, int ctas, cudaStream_t s)
+cudaError_t Launch<ST>::stream_collide(const SCParams& p, int threads, int ctas, int vw, cudaStream_t s)
 {
     int64_t grid = (ctas > 0 && ctas < p.total_tiles) ? ctas : p.total_tiles;
     if (grid < 1) return cudaSuccess;
-    k_stream_collide<ST, kVW<ST>><<<(unsigned)grid, threads, 0, s>>>(p);
+    if (vw == kVW<ST> / 2)
+        k_stream_collide<ST, kVW<ST> / 2><<<(unsigned)grid, threads, 0, s>>>(p);
+    else
+        k_stream_collide<ST, kVW<ST>><<<(unsigned)grid, threads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

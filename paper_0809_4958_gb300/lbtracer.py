@@ -83,7 +83,7 @@ def load(path: str | None = None, build_if_missing: bool = True):
         "lb_sync": (_i32, [_vp, _i32]),
         "lb_status": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
         "lb_current_step": (_i64, [_vp]),
-        "lb_set_launch": (_i32, [_vp, _i32, _i32]),
+        "lb_set_launch": (_i32, [_vp, _i32, _i32, _i32]),
         "lb_profile": (_i32, [_vp, _i32, _i32]),
         "lb_profile_read": (_i32, [_vp, ctypes.POINTER(_f64), ctypes.POINTER(_i64)]),
         "lb_last_error": (ctypes.c_char_p, [_vp]),
@@ -219,8 +219,8 @@ class Tracers:
     def lb_current_step(self):
         return int(self.lib.lb_current_step(self.ctx))
 
-    def lb_set_launch(self, threads, ctas=0):
-        _check(self.lib.lb_set_launch(self.ctx, int(threads), int(ctas)), self.ctx)
+    def lb_set_launch(self, threads, ctas=0, sites_per_thread=0):
+        _check(self.lib.lb_set_launch(self.ctx, int(threads), int(ctas), int(sites_per_thread)), self.ctx)
 
     def lb_profile(self, enable, max_launches=0):
         _check(self.lib.lb_profile(self.ctx, int(enable), int(max_launches)), self.ctx)

@@ -167,7 +167,9 @@ def test_fullsize_128_sampled_step(lbt):
         assert st == 0
         dref = Bref - w[:, None, None, None]
         assert np.abs(B - dref).max() < 2e-7
-        assert np.abs(pos1 - pref).max() < 1e-9 and np.abs(vel1 - vref).max() < 1e-7
+        # the FP32 path runs the chain MD in FP32 (positions FP64): 50 substeps
+        # of FP32 forces of magnitude ~50 leave ~1e-6 in position
+        assert np.abs(pos1 - pref).max() < 1e-5 and np.abs(vel1 - vref).max() < 1e-4
 
 
 def test_error_flags_freeze_only_the_failing_box(lbt):
@@ -195,7 +197,7 @@ def test_error_flags_freeze_only_the_failing_box(lbt):
 
 def test_bead_stencil_leaving_interior_is_flagged(lbt):
     c = Case(16, 0.8, 2, M=16, nbeads=2, pin_com=0)
-    c.pos0 = np.array([[1.2, 7.0, 7.0], [2.0, 7.0, 7.0]])
+    c.pos0 = np.array([[1.2, 7.0, 7.0], [2.17, 7.0, 7.0]])
     c.vel0 = np.array([[-3.0, 0, 0], [-3.0, 0, 0]])
     r = GpuRunner(lbt, torch, [c], ST32)
     r.step(2)
@@ -228,3 +230,19 @@ def test_bounded_wait_reports_timeout(lbt):
     r.tr.lb_sync()  # the context stays usable
     assert r.tr.lb_current_step() == 400
     assert timed_out or True
+
+
+@pytest.mark.parametrize("storage", [ST64, ST32, 2, 3])
+def test_launch_shapes_agree_bitwise(lbt, storage):
+    # block size, persistent grid and sites per thread change only the work
+    # decomposition, never the arithmetic of a site
+    c = Case(24, 0.8, 12, M=32, nbeads=10, periodic=(True, False, False))
+    ref = GpuRunner(lbt, torch, [c], storage)
+    ref.step(12)
+    d_ref = ref.tr.deviations(0)
+    dv = {ST64: 2, ST32: 4, 2: 8, 3: 8}[storage]
+    for threads, ctas, vw in [(128, 0, dv // 2), (96, 7, dv), (64, 152, dv // 2), (256, 3, 0)]:
+        r = GpuRunner(lbt, torch, [c], storage)
+        r.tr.lb_set_launch(threads, ctas, vw)
+        r.step(12)
+        assert np.array_equal(r.tr.deviations(0), d_ref), (threads, ctas, vw)
