@@ -234,15 +234,22 @@ def test_bounded_wait_reports_timeout(lbt):
 
 @pytest.mark.parametrize("storage", [ST64, ST32, 2, 3])
 def test_launch_shapes_agree_bitwise(lbt, storage):
-    # block size, persistent grid and sites per thread change only the work
-    # decomposition, never the arithmetic of a site
+    # block size and persistent grid change only the work decomposition, so the
+    # result is bitwise the same; the other sites-per-thread instantiation is
+    # separately compiled code whose FMA contraction may differ in the last bit
     c = Case(24, 0.8, 12, M=32, nbeads=10, periodic=(True, False, False))
     ref = GpuRunner(lbt, torch, [c], storage)
     ref.step(12)
     d_ref = ref.tr.deviations(0)
     dv = {ST64: 2, ST32: 4, 2: 8, 3: 8}[storage]
+    scale = np.abs(d_ref).max()
     for threads, ctas, vw in [(128, 0, dv // 2), (96, 7, dv), (64, 152, dv // 2), (256, 3, 0)]:
         r = GpuRunner(lbt, torch, [c], storage)
         r.tr.lb_set_launch(threads, ctas, vw)
         r.step(12)
-        assert np.array_equal(r.tr.deviations(0), d_ref), (threads, ctas, vw)
+        d = r.tr.deviations(0)
+        if vw in (0, dv):
+            assert np.array_equal(d, d_ref), (threads, ctas, vw)
+        else:
+            ulp = {ST64: 1e-15, ST32: 1e-6, 2: 2e-3, 3: 1e-2}[storage]
+            assert np.abs(d - d_ref).max() <= 4 * ulp * scale, (threads, ctas, vw)
