@@ -272,6 +272,33 @@ int32_t lb_synth_volume(const double* kvec, const double* amp, const double* ome
                         int32_t M, int32_t E, double t, int32_t out_dtype, void* out, void* workspace,
                         void* stream);
 
+/*
+ * lb_population_sums_noalloc -- FP64 sums of one box's population buffer,
+ * for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this is a service of the library.
+ *   Who needs it: a caller whose device memory is fully committed before the
+ *   run (a framework caching allocator that has reserved the GPU, or a loop
+ *   that forbids allocations after start-up to keep its footprint and
+ *   latency fixed) cannot give lb_conservation a context arena.  This call
+ *   needs only the populations and an output buffer.
+ *   populations: device, [19][E][E][E] deviations f_i - w_i in `storage`
+ *   format (LB_STORE_*), e.g. a LB_FIELD_DEV read-out.
+ *   out: device, 4 doubles: sum_x sum_i f_i, then sum_x sum_i c_i f_i.
+ *   stream: cudaStream_t the two kernels are enqueued on; no synchronisation.
+ *   Scratch: a fixed array of 512 KiB compiled into the library (partial sums
+ *   of at most 16384 blocks), held by every GPU that loads the library until
+ *   the process exits.  No cudaMalloc, cudaFree or allocating library call.
+ *   The first call on each device looks up the array's device address (one
+ *   cudaGetSymbolAddress with that device current); make that first call
+ *   before any stream capture.  All calls share the array: calls that overlap
+ *   on the GPU race; a call never reads a partial it has not written itself,
+ *   so nothing needs clearing between calls.
+ *   Errors: LB_ERR_SIZE if E^3 exceeds 64 Mi sites (E > 400), LB_ERR_ARG for
+ *   a null pointer or unknown storage, LB_ERR_CUDA if the address look-up or
+ *   a launch fails; lb_last_error(NULL) gives the message.
+ */
+int32_t lb_population_sums_noalloc(const void* populations, int32_t storage, int32_t E, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -327,6 +327,8 @@ constexpr int kDefaultTimeoutMs = 120000;
 
 }  // namespace
 
+void lbt_set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 extern "C" {
 
 int32_t lb_plan(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, size_t* arena_bytes)

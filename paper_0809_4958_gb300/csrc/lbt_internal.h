@@ -123,3 +123,6 @@ cudaError_t launch_synth_volume(const double* kvec, const double* amp, const dou
                                 int M, int E, double t, int out_f64, void* out, void* workspace, cudaStream_t s);
 
 }  // namespace lbt
+
+// Message returned by lb_last_error(NULL) for calls that have no context.
+void lbt_set_last_error(const char* msg);

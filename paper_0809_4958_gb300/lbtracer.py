@@ -29,7 +29,7 @@ ERROR_NAMES = {0: "LB_OK", 1: "LB_ERR_ARG", 2: "LB_ERR_CUDA", 3: "LB_ERR_FENE", 
 EXPORTS = ["lb_plan", "lb_create", "lb_destroy", "lb_init", "lb_set_boundary", "chain_couple", "lb_step",
            "lb_graph_capture", "lb_graph_launch", "lb_read_fields", "lb_conservation", "lb_sync", "lb_status",
            "lb_current_step", "lb_set_launch", "lb_profile", "lb_profile_read", "lb_last_error", "lb_synth_workspace_bytes", "lb_synth_faces",
-           "lb_synth_volume"]
+           "lb_synth_volume", "lb_population_sums_noalloc"]
 
 
 class lb_box_desc(ctypes.Structure):
@@ -90,6 +90,7 @@ def load(path: str | None = None, build_if_missing: bool = True):
         "lb_synth_workspace_bytes": (_sz, [_i32, _i32]),
         "lb_synth_faces": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _i32, _i64, _i64, _i32, _vp, _vp, _vp]),
         "lb_synth_volume": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _f64, _i32, _vp, _vp, _vp]),
+        "lb_population_sums_noalloc": (_i32, [_vp, _i32, _i32, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -267,6 +268,14 @@ class Tracers:
             self.lb_destroy()
         except Exception:
             pass
+
+
+def lb_population_sums_noalloc(populations, storage, E, out, stream=None):
+    """Mass and momentum sums of a device population buffer into the device
+    tensor out (4 doubles) without any device allocation (see the C header)."""
+    torch = _torch()
+    stream = stream or torch.cuda.current_stream()
+    _check(load().lb_population_sums_noalloc(_ptr(populations), int(storage), int(E), _ptr(out), stream.cuda_stream))
 
 
 def modes_to_device(modes, device="cuda"):
