@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--threads", type=int, default=0, help="stream-collide block size (0 = library default)")
     p.add_argument("--ctas", type=int, default=0, help="persistent grid size (0 = one block per tile)")
     p.add_argument("--vw", type=int, default=0, help="sites per thread in stream-collide (0 = default)")
+    p.add_argument("--kernel", default="staged", choices=["staged", "register"],
+                   help="stream-collide kernel: TMA-staged pipeline or register tiles")
     return p.parse_args()
 
 
@@ -255,8 +257,8 @@ def main():
     pos0 = inputs.chain_start(seed + 5, w["nbeads"], E)
     stream = torch.cuda.Stream()
     tr = lbt.Tracers([lbt.box_desc(E, w["tau"], nbeads=w["nbeads"], K=w["K"])], storage, stream=stream)
-    if args.threads or args.ctas or args.vw:
-        tr.lb_set_launch(args.threads or 256, args.ctas, args.vw)
+    kernel = lbt.LB_KERNEL_STAGED if args.kernel == "staged" else lbt.LB_KERNEL_REGISTER
+    tr.lb_set_launch(kernel, args.threads, args.ctas, args.vw)
     torch.cuda.synchronize()
     tr.lb_init(0, u0)
     tr.chain_couple(0, lbt.chain_desc(w["nbeads"], kT=w["kT"], n_md=w["n_md"], seed=seed), pos0)
@@ -356,10 +358,12 @@ def main():
                                "chain kT %g, Kolmogorov velocity boundaries on 6 faces (1024 modes, one sample per "
                                "step)" % (E, w["tau"], args.storage, w["kT"]),
                    "boxes_per_gpu": 1, "sites_per_box": E ** 3, "l2": "working set 2 x %.0f MB > L2, no flush"
-                   % (Q * E ** 3 * s_elem / 1e6), "launch": {"threads": args.threads or 256, "ctas": args.ctas, "sites_per_thread": args.vw or None}},
+                   % (Q * E ** 3 * s_elem / 1e6), "launch": {"kernel": args.kernel, "threads": args.threads or 256, "ctas": args.ctas,
+                              "sites_per_thread": args.vw or None}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(args.storage),
-                     "kernel": "k_stream_collide", "avg_launch_ms": avg_sc, "alg_bytes_per_launch": alg,
+                     "kernel": "k_stream_collide_staged" if args.kernel == "staged" else "k_stream_collide",
+                     "avg_launch_ms": avg_sc, "alg_bytes_per_launch": alg,
                      "peak_kind": peak_kind, "launches_timed": sc_n},
         "clocks": clk,
         "e2e": e2e,

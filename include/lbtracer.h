@@ -226,13 +226,20 @@ int32_t lb_status(lb_ctx* ctx, int32_t box, int32_t* status);
 /* lb_current_step -- number of steps enqueued so far. */
 int64_t lb_current_step(const lb_ctx* ctx);
 
-/* lb_set_launch -- launch shape of the stream-collide kernel: threads per
- * block (multiple of 32, 64 .. 256), a persistent grid of `ctas` blocks
- * (0 = one block per tile) and the sites each thread updates per population
- * load (0 = default: 2 for FP64, 4 for FP32, 8 for 16-bit storage; half the
- * default is the other choice).  Used by the autotuner.  Drops a captured
- * graph. */
-int32_t lb_set_launch(lb_ctx* ctx, int32_t threads, int32_t ctas, int32_t sites_per_thread);
+/* stream-collide kernels */
+#define LB_KERNEL_STAGED 0    /* persistent, tiles staged in shared memory by TMA bulk copies, two-stage pipeline */
+#define LB_KERNEL_REGISTER 1  /* one vector load per population into registers, x-neighbours by warp shuffles */
+
+/* lb_set_launch -- choice and launch shape of the stream-collide kernel.
+ *   kernel LB_KERNEL_STAGED (default): 256 threads, 16 bytes of every
+ *   population row per thread; threads and sites_per_thread must be 0 or
+ *   those values; ctas = persistent grid (0 = one block per SM).
+ *   kernel LB_KERNEL_REGISTER: threads per block (multiple of 32, 64 .. 256),
+ *   ctas = persistent grid (0 = one block per tile), sites_per_thread
+ *   (0 = default: 2 for FP64, 4 for FP32, 8 for 16-bit storage; half the
+ *   default is the other choice).
+ *   Used by the autotuner.  Drops a captured graph. */
+int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas, int32_t sites_per_thread);
 
 /*
  * lb_profile -- time every stream-collide launch with a pair of CUDA events

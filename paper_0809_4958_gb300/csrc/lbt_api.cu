@@ -142,6 +142,7 @@ struct lb_ctx {
     bool a_is_pop_a = true;            // which buffer holds the current state
     int64_t step = 0;                  // steps enqueued so far
     std::vector<int64_t> pushed;       // last boundary sample pushed per box (-1 none)
+    int kernel = LB_KERNEL_STAGED;
     int threads = 256, ctas = 0, vw = 0;  // vw: sites per thread in stream-collide
     std::vector<int64_t> tile_prefix;  // for the current block size
     cudaGraphExec_t graph = nullptr;
@@ -272,7 +273,7 @@ int enqueue_step(lb_ctx* ctx)
     sp.status = ctx->at<int32_t>(ctx->L.status);
     const bool timed = ctx->profiling && ctx->prof_used + 2 <= ctx->prof_ev.size();
     if (timed) CK(cudaEventRecord(ctx->prof_ev[ctx->prof_used], ctx->stream));
-    CK(DISPATCH(ctx->storage, stream_collide(sp, ctx->threads, ctx->ctas, ctx->vw, ctx->stream)));
+    CK(DISPATCH(ctx->storage, stream_collide(sp, ctx->kernel, ctx->threads, ctx->ctas, ctx->vw, ctx->stream)));
     if (timed) {
         CK(cudaEventRecord(ctx->prof_ev[ctx->prof_used + 1], ctx->stream));
         ctx->prof_used += 2;
@@ -700,13 +701,23 @@ int32_t lb_status(lb_ctx* ctx, int32_t box, int32_t* status)
 
 int64_t lb_current_step(const lb_ctx* ctx) { return ctx ? ctx->step : -1; }
 
-int32_t lb_set_launch(lb_ctx* ctx, int32_t threads, int32_t ctas, int32_t sites_per_thread)
+int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas, int32_t sites_per_thread)
 {
     if (!ctx) return LB_ERR_ARG;
     const int dv = default_vw(ctx->storage);
     const int vw = sites_per_thread == 0 ? dv : sites_per_thread;
-    if (threads < 64 || threads > 256 || threads % 32 || ctas < 0 || (vw != dv && vw != dv / 2))
-        return ctx->fail(LB_ERR_ARG, "threads: multiple of 32 in [64, 256]; ctas >= 0; sites_per_thread: default or half");
+    if (threads == 0) threads = 256;
+    if (kernel == LB_KERNEL_STAGED) {
+        if (threads != 256 || vw != dv || ctas < 0)
+            return ctx->fail(LB_ERR_ARG, "staged kernel: 256 threads, default sites per thread, ctas >= 0");
+    } else if (kernel == LB_KERNEL_REGISTER) {
+        if (threads < 64 || threads > 256 || threads % 32 || ctas < 0 || (vw != dv && vw != dv / 2))
+            return ctx->fail(LB_ERR_ARG,
+                             "register kernel: threads multiple of 32 in [64, 256]; ctas >= 0; sites_per_thread default or half");
+    } else {
+        return ctx->fail(LB_ERR_ARG, "unknown stream-collide kernel");
+    }
+    ctx->kernel = kernel;
     ctx->threads = threads;
     ctx->ctas = ctas;
     ctx->vw = vw;

@@ -103,7 +103,7 @@ struct ForcedParams {
 // Host-side launchers, one instantiation per storage type.
 template <int ST>
 struct Launch {
-    static cudaError_t stream_collide(const SCParams& p, int threads, int ctas, int vw, cudaStream_t s);
+    static cudaError_t stream_collide(const SCParams& p, int kernel, int threads, int ctas, int vw, cudaStream_t s);
     static cudaError_t bead_couple(const BeadParams& p, int nchains, cudaStream_t s);
     static cudaError_t forced(const ForcedParams& p, cudaStream_t s);
     static cudaError_t init(void* A, const BoxDev* boxes, int box, int64_t n3, const void* u0, cudaStream_t s);

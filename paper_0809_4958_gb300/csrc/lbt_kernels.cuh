@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "lbt_device.cuh"
+#include "lbt_sc_staged.cuh"
 
 namespace lbt {
 
@@ -267,6 +268,7 @@ __device__ __forceinline__ void set_status(int32_t* st, int code) { atomicCAS(st
 
 constexpr int kMaxNb = 48;              // Verlet neighbours per bead
 constexpr double kSkin = 0.3;           // Verlet skin (lattice units)
+constexpr int kNoiseChunk = 10;         // substeps whose noise is drawn at once
 
 template <int ST>
 __global__ void __launch_bounds__(kMaxBeads) k_bead_couple(BeadParams p)
@@ -361,20 +363,36 @@ __global__ void __launch_bounds__(kMaxBeads) k_bead_couple(BeadParams p)
             for (int a = 0; a < 3; a++) sU[e >> 3][a] = (MT)uc[a];
     }
 
-    // 3. MD substeps (symplectic Euler), fluid velocity frozen over the step
+    // 3. MD substeps (symplectic Euler), fluid velocity frozen over the step.
+    //    The noise of kNoiseChunk substeps is drawn up front by all threads in
+    //    parallel (Philox4x64-10 is independent of the MD state).
     const MT dt = MT(1) / (MT)ch.n_md;
     const double dtd = 1.0 / ch.n_md;
     const MT namp = ch.kT > 0.0 ? (MT)sqrt(2.0 * ch.kT * ch.zeta / dtd) : MT(0);
-    const MT R02 = (MT)(ch.R0 * ch.R0), kf = (MT)ch.k_fene, zeta = (MT)ch.zeta, dtm = dt / (MT)ch.mass;
+    const MT R02 = (MT)(ch.R0 * ch.R0), inv_R02 = MT(1) / R02, kf = (MT)ch.k_fene, zeta = (MT)ch.zeta;
+    const MT dtm = dt / (MT)ch.mass;
     const bool wca = ch.eps > 0.0;
     const MT sig2 = (MT)(ch.sigma * ch.sigma), rc2 = (MT)(cbrt(2.0) * ch.sigma * ch.sigma), e24 = (MT)(24.0 * ch.eps);
     const MT rl = (MT)(sqrt(cbrt(2.0)) * ch.sigma + kSkin), rl2 = rl * rl;  // WCA cut-off 2^(1/6) sigma + skin
     const MT half_skin2 = (MT)(0.25 * kSkin * kSkin);
+    extern __shared__ __align__(16) unsigned char bead_dyn[];
+    MT* sXi = reinterpret_cast<MT*>(bead_dyn);  // [kNoiseChunk][N][3] unit-variance noise
     MT Xref[3] = {0, 0, 0};
     MT P[3] = {0, 0, 0};
     bool need_build = true;
     __syncthreads();
     for (int sub = 0; sub < ch.n_md; sub++) {
+        const int cs = sub % kNoiseChunk;
+        if (namp > MT(0) && cs == 0) {
+            const int nc = min(kNoiseChunk, ch.n_md - sub);
+            for (int q = tid; q < nc * N; q += blockDim.x) {
+                const int sb = q / N, bb = q - sb * N;
+                uint64_t x[4] = {(uint64_t)n, (uint64_t)(sub + sb), (uint64_t)bb, (uint64_t)b};
+                philox4x64_10(x, ch.seed, 0);
+                for (int a = 0; a < 3; a++) sXi[(sb * N + bb) * 3 + a] = (MT)unit_uniform(x[a]);
+            }
+            __syncthreads();
+        }
         if (wca) {
             bool moved = false;
             if (tid < N && !need_build) {
@@ -416,7 +434,7 @@ __global__ void __launch_bounds__(kMaxBeads) k_bead_couple(BeadParams p)
                     r2 += r[a] * r[a];
                 }
                 if (r2 >= R02) sErr = LB_ERR_FENE;
-                const MT fac = kf / (MT(1) - r2 / R02);
+                const MT fac = kf / (MT(1) - r2 * inv_R02);
                 for (int a = 0; a < 3; a++) F[a] -= fac * r[a];
             }
             if (tid + 1 < N) {  // bond (tid, tid+1): opposite force on the lower bead
@@ -426,11 +444,12 @@ __global__ void __launch_bounds__(kMaxBeads) k_bead_couple(BeadParams p)
                     r2 += r[a] * r[a];
                 }
                 if (r2 >= R02) sErr = LB_ERR_FENE;
-                const MT fac = kf / (MT(1) - r2 / R02);
+                const MT fac = kf / (MT(1) - r2 * inv_R02);
                 for (int a = 0; a < 3; a++) F[a] += fac * r[a];
             }
             if (wca) {  // WCA: 24 eps (2 (s/r)^12 - (s/r)^6) / r^2 along R_tid - R_partner
                 const int cnt = sNbN[tid];
+#pragma unroll 4
                 for (int k = 0; k < cnt; k++) {
                     const int b2 = sNb[tid][k];
                     MT r[3], r2 = 0;
@@ -439,21 +458,16 @@ __global__ void __launch_bounds__(kMaxBeads) k_bead_couple(BeadParams p)
                         r2 += r[a] * r[a];
                     }
                     if (r2 < rc2) {
-                        const MT s2 = sig2 / r2, s6 = s2 * s2 * s2;
-                        const MT fac = e24 * (MT(2) * s6 * s6 - s6) / r2;
+                        const MT inv = MT(1) / r2;
+                        const MT s2 = sig2 * inv, s6 = s2 * s2 * s2;
+                        const MT fac = e24 * (MT(2) * s6 * s6 - s6) * inv;
                         for (int a = 0; a < 3; a++) F[a] += fac * r[a];
                     }
                 }
             }
-            MT xi[3] = {0, 0, 0};
-            if (namp > MT(0)) {
-                uint64_t x[4] = {(uint64_t)n, (uint64_t)sub, (uint64_t)tid, (uint64_t)b};
-                philox4x64_10(x, ch.seed, 0);
-                for (int a = 0; a < 3; a++) xi[a] = (MT)unit_uniform(x[a]);
-            }
             for (int a = 0; a < 3; a++) {
                 const MT ffric = -zeta * (V[a] - sU[tid][a]);
-                const MT fnoise = namp * xi[a];
+                const MT fnoise = namp > MT(0) ? namp * sXi[(cs * N + tid) * 3 + a] : MT(0);
                 const MT ftot = F[a] + ffric + fnoise + (MT)ch.f_ext[a];
                 V[a] += dtm * ftot;
                 R[a] += dtd * (double)V[a];
@@ -719,8 +733,28 @@ inline int grid_for(int64_t n, int threads, int cap = 152 * 16)
 }
 
 template <int ST>
-cudaError_t Launch<ST>::stream_collide(const SCParams& p, int threads, int ctas, int vw, cudaStream_t s)
+cudaError_t Launch<ST>::stream_collide(const SCParams& p, int kernel, int threads, int ctas, int vw, cudaStream_t s)
 {
+    if (kernel == LB_KERNEL_STAGED) {
+        static bool attr_set = false;  // per storage instantiation
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(k_stream_collide_staged<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 kStagedSmemBytes);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        int sms = 0;
+        if (ctas <= 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        }
+        int64_t grid = ctas > 0 ? ctas : sms;
+        if (grid > p.total_tiles) grid = p.total_tiles;
+        if (grid < 1) return cudaSuccess;
+        k_stream_collide_staged<ST><<<(unsigned)grid, kStagedThreads, kStagedSmemBytes, s>>>(p);
+        return cudaGetLastError();
+    }
     int64_t grid = (ctas > 0 && ctas < p.total_tiles) ? ctas : p.total_tiles;
     if (grid < 1) return cudaSuccess;
     if (vw == kVW<ST> / 2)
@@ -734,7 +768,15 @@ template <int ST>
 cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, cudaStream_t s)
 {
     if (nchains <= 0) return cudaSuccess;
-    k_bead_couple<ST><<<nchains, kMaxBeads, 0, s>>>(p);
+    using MT = typename std::conditional<ST == kF64, double, float>::type;
+    const size_t dyn = sizeof(MT) * 3 * kNoiseChunk * kMaxBeads;  // noise of one chunk of substeps
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_bead_couple<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_bead_couple<ST><<<nchains, kMaxBeads, dyn, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -22,6 +22,7 @@ LB_FACE_VELOCITY, LB_FACE_PERIODIC = 0, 1
 LB_TIME_LINEAR, LB_TIME_HERMITE, LB_TIME_MLP = 0, 1, 2
 LB_FIELD_RHO, LB_FIELD_U, LB_FIELD_DEV, LB_FIELD_CHAIN, LB_FIELD_ASYNC = 0, 1, 2, 3, 0x100
 LB_ALL_BOXES = -1
+LB_KERNEL_STAGED, LB_KERNEL_REGISTER = 0, 1
 
 ERROR_NAMES = {0: "LB_OK", 1: "LB_ERR_ARG", 2: "LB_ERR_CUDA", 3: "LB_ERR_FENE", 4: "LB_ERR_BEAD_OOB",
                5: "LB_ERR_NONFINITE", 6: "LB_ERR_TIMEOUT", 7: "LB_ERR_STATE", 8: "LB_ERR_SIZE", 9: "LB_ERR_CHAIN"}
@@ -83,7 +84,7 @@ def load(path: str | None = None, build_if_missing: bool = True):
         "lb_sync": (_i32, [_vp, _i32]),
         "lb_status": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
         "lb_current_step": (_i64, [_vp]),
-        "lb_set_launch": (_i32, [_vp, _i32, _i32, _i32]),
+        "lb_set_launch": (_i32, [_vp, _i32, _i32, _i32, _i32]),
         "lb_profile": (_i32, [_vp, _i32, _i32]),
         "lb_profile_read": (_i32, [_vp, ctypes.POINTER(_f64), ctypes.POINTER(_i64)]),
         "lb_last_error": (ctypes.c_char_p, [_vp]),
@@ -220,8 +221,9 @@ class Tracers:
     def lb_current_step(self):
         return int(self.lib.lb_current_step(self.ctx))
 
-    def lb_set_launch(self, threads, ctas=0, sites_per_thread=0):
-        _check(self.lib.lb_set_launch(self.ctx, int(threads), int(ctas), int(sites_per_thread)), self.ctx)
+    def lb_set_launch(self, kernel=LB_KERNEL_STAGED, threads=0, ctas=0, sites_per_thread=0):
+        _check(self.lib.lb_set_launch(self.ctx, int(kernel), int(threads), int(ctas), int(sites_per_thread)),
+               self.ctx)
 
     def lb_profile(self, enable, max_launches=0):
         _check(self.lib.lb_profile(self.ctx, int(enable), int(max_launches)), self.ctx)

@@ -233,23 +233,29 @@ def test_bounded_wait_reports_timeout(lbt):
 
 
 @pytest.mark.parametrize("storage", [ST64, ST32, 2, 3])
-def test_launch_shapes_agree_bitwise(lbt, storage):
-    # block size and persistent grid change only the work decomposition, so the
-    # result is bitwise the same; the other sites-per-thread instantiation is
-    # separately compiled code whose FMA contraction may differ in the last bit
-    c = Case(24, 0.8, 12, M=32, nbeads=10, periodic=(True, False, False))
-    ref = GpuRunner(lbt, torch, [c], storage)
+@pytest.mark.parametrize("periodic", [(True, False, False), (False, False, False), (True, True, True)])
+def test_launch_shapes_agree(lbt, storage, periodic):
+    # grid size and block size change only the work decomposition: bitwise the
+    # same result for one kernel and one sites-per-thread instantiation; other
+    # instantiations are separately compiled code whose FMA contraction may
+    # differ in the last bit of a site's update
+    accel = (1e-5, 0.0, -2e-5) if all(periodic) else (0.0, 0.0, 0.0)
+    c = Case(24, 0.8, 12, M=32, nbeads=10, periodic=periodic, accel=accel, pin_com=0 if all(periodic) else 2)
+    ref = GpuRunner(lbt, torch, [c], storage)  # default: staged kernel, one block per SM
     ref.step(12)
     d_ref = ref.tr.deviations(0)
     dv = {ST64: 2, ST32: 4, 2: 8, 3: 8}[storage]
     scale = np.abs(d_ref).max()
-    for threads, ctas, vw in [(128, 0, dv // 2), (96, 7, dv), (64, 152, dv // 2), (256, 3, 0)]:
+    ulp = {ST64: 1e-15, ST32: 1e-6, 2: 2e-3, 3: 1e-2}[storage]
+    S, Rg = lbt.LB_KERNEL_STAGED, lbt.LB_KERNEL_REGISTER
+    for kernel, threads, ctas, vw, exact in [(S, 0, 3, 0, True), (S, 256, 1, dv, True), (Rg, 256, 0, 0, False),
+                                             (Rg, 128, 0, dv // 2, False), (Rg, 96, 7, dv, False),
+                                             (Rg, 64, 152, dv // 2, False)]:
         r = GpuRunner(lbt, torch, [c], storage)
-        r.tr.lb_set_launch(threads, ctas, vw)
+        r.tr.lb_set_launch(kernel, threads, ctas, vw)
         r.step(12)
         d = r.tr.deviations(0)
-        if vw in (0, dv):
-            assert np.array_equal(d, d_ref), (threads, ctas, vw)
+        if exact:
+            assert np.array_equal(d, d_ref), (kernel, threads, ctas, vw)
         else:
-            ulp = {ST64: 1e-15, ST32: 1e-6, 2: 2e-3, 3: 1e-2}[storage]
-            assert np.abs(d - d_ref).max() <= 4 * ulp * scale, (threads, ctas, vw)
+            assert np.abs(d - d_ref).max() <= 4 * ulp * scale, (kernel, threads, ctas, vw)
