@@ -126,11 +126,14 @@ typedef struct lb_ctx lb_ctx;
 /*
  * lb_plan -- size of the device arena for a context.
  *   boxes[nboxes]: box descriptions (host).  storage: LB_STORE_*.
+ *   ring_slots: coarse samples the boundary ring holds (0 = 4, at most 4096).
+ *   Four slots cover one step at a time; a captured graph of G steps needs
+ *   G / K + 4 slots so that all its samples can be pushed before it runs.
  *   *arena_bytes receives the number of bytes the caller must allocate
  *   (device memory, 256-byte aligned).
  *   Returns LB_ERR_ARG for an invalid description.
  */
-int32_t lb_plan(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, size_t* arena_bytes);
+int32_t lb_plan(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int32_t ring_slots, size_t* arena_bytes);
 
 /*
  * lb_create -- build a context over a caller-owned arena.
@@ -140,7 +143,7 @@ int32_t lb_plan(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, size_
  *   concurrency between the bead kernel and the stream-collide kernel.
  *   Populations are left uninitialised until lb_init.
  */
-int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, void* arena,
+int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int32_t ring_slots, void* arena,
                   size_t arena_bytes, void* stream, lb_ctx** out);
 
 /* lb_destroy -- wait for the stream, release the host context, events, side
@@ -160,12 +163,12 @@ int32_t lb_init(lb_ctx* ctx, int32_t box, const void* u0);
 
 /*
  * lb_set_boundary -- push coarse boundary sample j (taken at t = j K) into
- * the 4-slot ring of the box (Sec. 3: boundary velocities interpolated in
+ * the ring of the box (Sec. 3: boundary velocities interpolated in
  * time between the samples).
  *   face_u: real [6][3][E][E] for one box, or, with box == LB_ALL_BOXES, the
  *   arrays of all boxes back to back in box order; host or device.
  *   Samples must be pushed in order 0, 1, 2, ...; sample j may be pushed
- *   once the step that needs sample j-4 has been enqueued.
+ *   once no step still to be enqueued needs sample j - ring_slots.
  *   The copy is enqueued on the context stream (pinned host memory keeps it
  *   asynchronous).
  */
@@ -231,9 +234,9 @@ int64_t lb_current_step(const lb_ctx* ctx);
 #define LB_KERNEL_REGISTER 1  /* one vector load per population into registers, x-neighbours by warp shuffles */
 
 /* lb_set_launch -- choice and launch shape of the stream-collide kernel.
- *   kernel LB_KERNEL_STAGED (default): 256 threads, 16 bytes of every
- *   population row per thread; threads and sites_per_thread must be 0 or
- *   those values; ctas = persistent grid (0 = one block per SM).
+ *   kernel LB_KERNEL_STAGED (default): 512 threads per block, tiles of 4 KB
+ *   per population row; threads and sites_per_thread must be 0;
+ *   ctas = persistent grid (0 = one block per SM).
  *   kernel LB_KERNEL_REGISTER: threads per block (multiple of 32, 64 .. 256),
  *   ctas = persistent grid (0 = one block per tile), sites_per_thread
  *   (0 = default: 2 for FP64, 4 for FP32, 8 for 16-bit storage; half the

@@ -69,9 +69,10 @@ int validate_boxes(const lb_box_desc* boxes, int nboxes, int storage, std::strin
     return LB_OK;
 }
 
-Layout plan_layout(const lb_box_desc* boxes, int nboxes, int storage)
+Layout plan_layout(const lb_box_desc* boxes, int nboxes, int storage, int ring_slots)
 {
     Layout L{};
+    L.ring_slots = ring_slots;
     size_t off = 0;
     L.boxes = off;
     off = align_up(off + sizeof(BoxDev) * nboxes);
@@ -98,7 +99,7 @@ Layout plan_layout(const lb_box_desc* boxes, int nboxes, int storage)
     L.pop_b = off;
     off = align_up(off + pop);
     L.ring = off;
-    off = align_up(off + kRingSlots * ring * real_bytes(storage));
+    off = align_up(off + (size_t)ring_slots * ring * real_bytes(storage));
     L.pos = off;
     off = align_up(off + sizeof(double) * 3 * (beads + 1));
     L.vel = off;
@@ -112,6 +113,8 @@ Layout plan_layout(const lb_box_desc* boxes, int nboxes, int storage)
     L.status = off;
     off = align_up(off + sizeof(int32_t) * nboxes);
     L.step = off;
+    off = align_up(off + sizeof(int64_t));
+    L.tile_counter = off;
     off = align_up(off + sizeof(int64_t));
     L.total = off;
     return L;
@@ -229,7 +232,7 @@ int check_samples(lb_ctx* ctx, int64_t n0, int64_t nsteps)
         }
         int64_t lo0, hi0;
         needed_samples(ctx, b, n0, lo0, hi0);
-        if (ctx->pushed[b] - kRingSlots >= lo0) {
+        if (ctx->pushed[b] - ctx->L.ring_slots >= lo0) {
             char buf[200];
             snprintf(buf, sizeof buf, "box %d: sample %lld was overwritten before step %lld", b, (long long)lo0,
                      (long long)n0);
@@ -265,11 +268,13 @@ int enqueue_step(lb_ctx* ctx)
     sp.B = B;
     sp.ring = ctx->arena + ctx->L.ring;
     sp.ring_slot_elems = (int64_t)ctx->L.ring_slot_elems;
+    sp.ring_slots = ctx->L.ring_slots;
     sp.boxes = ctx->at<BoxDev>(ctx->L.boxes);
     sp.tile_prefix = ctx->at<int64_t>(ctx->L.tile_prefix);
     sp.nboxes = ctx->nboxes;
     sp.total_tiles = ctx->tile_prefix[ctx->nboxes];
     sp.step = ctx->at<int64_t>(ctx->L.step);
+    sp.tile_counter = ctx->at<int64_t>(ctx->L.tile_counter);
     sp.status = ctx->at<int32_t>(ctx->L.status);
     const bool timed = ctx->profiling && ctx->prof_used + 2 <= ctx->prof_ev.size();
     if (timed) CK(cudaEventRecord(ctx->prof_ev[ctx->prof_used], ctx->stream));
@@ -287,6 +292,7 @@ int enqueue_step(lb_ctx* ctx)
     fp.forces = ctx->at<ForceEntry>(ctx->L.forces);
     fp.status = ctx->at<int32_t>(ctx->L.status);
     fp.step = ctx->at<int64_t>(ctx->L.step);
+    fp.tile_counter = ctx->at<int64_t>(ctx->L.tile_counter);
     fp.nchains = nch;
     CK(DISPATCH(ctx->storage, forced(fp, ctx->stream)));
     ctx->a_is_pop_a = !ctx->a_is_pop_a;
@@ -332,24 +338,29 @@ void lbt_set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
 extern "C" {
 
-int32_t lb_plan(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, size_t* arena_bytes)
+int32_t lb_plan(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int32_t ring_slots, size_t* arena_bytes)
 {
     std::string why;
     int st = validate_boxes(boxes, nboxes, storage, why);
     if (st) {
         g_last_error = why;
         return st;
+    }
+    if (ring_slots == 0) ring_slots = kRingSlots;
+    if (ring_slots < kRingSlots || ring_slots > kMaxRingSlots) {
+        g_last_error = "ring_slots must be 0 (= 4) or in [4, 4096]";
+        return LB_ERR_ARG;
     }
     if (!arena_bytes) {
         g_last_error = "null arena_bytes";
         return LB_ERR_ARG;
     }
-    *arena_bytes = plan_layout(boxes, nboxes, storage).total;
+    *arena_bytes = plan_layout(boxes, nboxes, storage, ring_slots).total;
     return LB_OK;
 }
 
-int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, void* arena, size_t arena_bytes,
-                  void* stream, lb_ctx** out)
+int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int32_t ring_slots, void* arena,
+                  size_t arena_bytes, void* stream, lb_ctx** out)
 {
     std::string why;
     int st = validate_boxes(boxes, nboxes, storage, why);
@@ -357,11 +368,16 @@ int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, voi
         g_last_error = why;
         return st;
     }
+    if (ring_slots == 0) ring_slots = kRingSlots;
+    if (ring_slots < kRingSlots || ring_slots > kMaxRingSlots) {
+        g_last_error = "ring_slots must be 0 (= 4) or in [4, 4096]";
+        return LB_ERR_ARG;
+    }
     if (!out || !arena) {
         g_last_error = "null arena or out";
         return LB_ERR_ARG;
     }
-    Layout L = plan_layout(boxes, nboxes, storage);
+    Layout L = plan_layout(boxes, nboxes, storage, ring_slots);
     if (arena_bytes < L.total) {
         g_last_error = "arena smaller than lb_plan size";
         return LB_ERR_SIZE;
@@ -398,6 +414,7 @@ int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, voi
         bd.n3 = n3;
         bd.ring_off = (int64_t)ring;
         bd.E = d.E;
+        bd.div_magic = ((1ull << 40) + (uint64_t)d.E - 1) / (uint64_t)d.E;
         bd.per_mask = (d.face_mode[0] == LB_FACE_PERIODIC ? 1 : 0) | (d.face_mode[2] == LB_FACE_PERIODIC ? 2 : 0) |
                       (d.face_mode[4] == LB_FACE_PERIODIC ? 4 : 0);
         bd.time_interp = d.time_interp;
@@ -507,14 +524,14 @@ int32_t lb_set_boundary(lb_ctx* ctx, int32_t box, int64_t j, const void* face_u)
         }
         int64_t lo, hi;
         needed_samples(ctx, b, ctx->step, lo, hi);
-        if (j - kRingSlots >= lo && j >= kRingSlots) {
+        if (j - ctx->L.ring_slots >= lo && j >= ctx->L.ring_slots) {
             char buf[160];
             snprintf(buf, sizeof buf, "box %d: sample %lld would overwrite sample %lld still needed at step %lld", b,
-                     (long long)j, (long long)(j - kRingSlots), (long long)ctx->step);
+                     (long long)j, (long long)(j - ctx->L.ring_slots), (long long)ctx->step);
             return ctx->fail(LB_ERR_STATE, buf);
         }
     }
-    char* slot = ctx->arena + ctx->L.ring + (size_t)(j % kRingSlots) * ctx->L.ring_slot_elems * rb;
+    char* slot = ctx->arena + ctx->L.ring + (size_t)(j % ctx->L.ring_slots) * ctx->L.ring_slot_elems * rb;
     const char* src = reinterpret_cast<const char*>(face_u);
     for (int b = b0; b < b1; b++) {
         const int64_t E = ctx->boxes[b].E;
@@ -709,7 +726,7 @@ int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas
     if (threads == 0) threads = 256;
     if (kernel == LB_KERNEL_STAGED) {
         if (threads != 256 || vw != dv || ctas < 0)
-            return ctx->fail(LB_ERR_ARG, "staged kernel: 256 threads, default sites per thread, ctas >= 0");
+            return ctx->fail(LB_ERR_ARG, "staged kernel: threads and sites_per_thread 0 (fixed tiles), ctas >= 0");
     } else if (kernel == LB_KERNEL_REGISTER) {
         if (threads < 64 || threads > 256 || threads % 32 || ctas < 0 || (vw != dv && vw != dv / 2))
             return ctx->fail(LB_ERR_ARG,

@@ -156,7 +156,7 @@ struct TimeWeights {
 };
 
 template <class R>
-__device__ __forceinline__ TimeWeights<R> time_weights(int64_t n, int K, int mode)
+__device__ __forceinline__ TimeWeights<R> time_weights(int64_t n, int K, int mode, int ring_slots)
 {
     TimeWeights<R> tw;
     int64_t j = n / K;
@@ -164,7 +164,7 @@ __device__ __forceinline__ TimeWeights<R> time_weights(int64_t n, int K, int mod
     R th = (R)s / (R)K;
     for (int a = 0; a < 4; a++) {
         int64_t jj = j - 1 + a;
-        tw.slot[a] = (int)(((jj % kRingSlots) + kRingSlots) % kRingSlots);
+        tw.slot[a] = (int)(((jj % ring_slots) + ring_slots) % ring_slots);
         tw.c[a] = R(0);
     }
     if (mode == 0) {

@@ -11,7 +11,8 @@
 namespace lbt {
 
 constexpr int kQ = 19;
-constexpr int kRingSlots = 4;       // coarse samples j-1, j, j+1, j+2 live in slots j mod 4
+constexpr int kRingSlots = 4;       // default ring: samples j-1 .. j+2 live in slots j mod ring_slots
+constexpr int kMaxRingSlots = 4096;
 constexpr int kMaxBeads = 256;      // beads per chain (one CTA per chain, one thread per bead)
 
 // One box as the kernels see it.
@@ -25,6 +26,7 @@ struct BoxDev {
     int32_t K;
     int32_t chain;      // index into the chain table, -1 if none
     int32_t has_accel;
+    uint64_t div_magic; // ceil(2^40 / E): site / E = (site * div_magic) >> 40
     double tau;
     double rho_b;
     double accel[3];
@@ -55,9 +57,10 @@ struct ForceEntry {
 // Arena layout (byte offsets), computed by plan().
 struct Layout {
     size_t boxes, tile_prefix, chains, pop_a, pop_b, ring, pos, vel, forces, cons_partial, cons_out,
-        status, step, total;
+        status, step, tile_counter, total;
     size_t pop_bytes;        // bytes of one population buffer
     size_t ring_slot_elems;  // real elements per ring slot
+    int32_t ring_slots;      // slots in the ring of coarse samples
     int64_t cons_chunks;     // max conservation chunks per box
     int64_t total_beads;
 };
@@ -70,11 +73,13 @@ struct SCParams {
     void* B;
     const void* ring;             // real elements
     int64_t ring_slot_elems;
+    int32_t ring_slots;
     const BoxDev* boxes;
     const int64_t* tile_prefix;   // [nboxes + 1] first tile of each box for the current block size
     int32_t nboxes;
     int64_t total_tiles;
     const int64_t* step;          // device step counter n (state holds step n)
+    int64_t* tile_counter;        // next tile for the persistent staged kernel (zeroed every step)
     int32_t* status;
 };
 
@@ -97,6 +102,7 @@ struct ForcedParams {
     const ForceEntry* forces;
     const int32_t* status;
     int64_t* step;                // incremented once per step by block 0
+    int64_t* tile_counter;        // reset to zero once per step by block 0
     int32_t nchains;
 };
 

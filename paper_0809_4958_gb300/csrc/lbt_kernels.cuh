@@ -133,7 +133,7 @@ __device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, int
         else if (!px) bmask = (xg == 0 ? 1u : 0u) | (xg == gpr - 1 ? (1u << (VW - 1)) : 0u);
     }
     if (bmask) {
-        const TimeWeights<R> tw = time_weights<R>(n, bd.K, bd.time_interp);
+        const TimeWeights<R> tw = time_weights<R>(n, bd.K, bd.time_interp, p.ring_slots);
         const R* ring = reinterpret_cast<const R*>(p.ring);
 #pragma unroll
         for (int k = 0; k < VW; k++) {
@@ -607,7 +607,10 @@ __global__ void __launch_bounds__(256) k_forced(ForcedParams p)
     }
     if (blockIdx.x == 0) {
         __syncthreads();
-        if (threadIdx.x == 0) *p.step += 1;
+        if (threadIdx.x == 0) {
+            *p.step += 1;
+            *p.tile_counter = 0;
+        }
     }
 }
 

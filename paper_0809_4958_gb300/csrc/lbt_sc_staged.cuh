@@ -19,7 +19,7 @@
 
 namespace lbt {
 
-constexpr int kStagedThreads = 256;
+constexpr int kStagedThreads = 512;
 constexpr int kStagedRowBytes = 4096;                          // one population row of a tile
 constexpr int kStagedHaloBytes = 16;                           // x-shift halo on each side
 constexpr int kStagedRowStride = kStagedRowBytes + 2 * kStagedHaloBytes;
@@ -31,7 +31,7 @@ template <int ST>
 struct Staged {
     using E = typename Stor<ST>::E;
     static constexpr int kSites = kStagedRowBytes / (int)sizeof(E);    // sites per tile
-    static constexpr int kSPT = kSites / kStagedThreads;              // sites per thread (16 bytes)
+    static constexpr int kSPT = kSites / kStagedThreads;              // sites per thread
     static constexpr int kHalo = kStagedHaloBytes / (int)sizeof(E);   // halo elements
 };
 
@@ -129,7 +129,13 @@ __device__ __forceinline__ void issue_tile(const SCParams& p, int64_t tile, unsi
     }
 }
 
-// Consumer: every thread collides kSPT consecutive x-sites of the tile.
+// Quotient and remainder of a site index by E with a precomputed multiplier:
+// q = (s * m) >> 40 with m = ceil(2^40 / E), exact for s < 2^31 and E <= 1024.
+__device__ __forceinline__ int div_e(int64_t s, uint64_t m) { return (int)(((uint64_t)s * m) >> 40); }
+
+// Consumer: thread t collides sites t, t + kStagedThreads, ... of the tile,
+// so the lanes of a warp read consecutive shared-memory words (no bank
+// conflicts) and store consecutive global words.
 template <int ST, bool PER, bool ACCEL>
 __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd, int64_t s0, int64_t n,
                                             const unsigned char* stage)
@@ -139,29 +145,40 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
     using A = typename S::A;
     using R = typename S::R;
     constexpr int SPT = Staged<ST>::kSPT, H = Staged<ST>::kHalo;
-    using P = Pack<E, SPT>;
-    using Raw = typename P::Raw;
 
     const int Ei = bd.E;
     const int64_t n3 = bd.n3;
-    const int t0 = threadIdx.x * SPT;  // first site of this thread inside the tile
-    const int64_t s = s0 + t0;
-    const bool active = s < n3;
-    const int64_t sc = active ? s : 0;
-    const int x0 = (int)(sc % Ei);
-    const int y = (int)((sc / Ei) % Ei);
-    const int z = (int)(sc / ((int64_t)Ei * Ei));
+    const uint64_t mE = bd.div_magic;
     const int per = bd.per_mask;
     const bool px = per & 1, py = per & 2, pz = per & 4;
-    const bool row_bnd = (!py && (y == 0 || y == Ei - 1)) || (!pz && (z == 0 || z == Ei - 1));
     const E* Ab = reinterpret_cast<const E*>(p.A) + bd.f_off;
     E* Bb = reinterpret_cast<E*>(p.B) + bd.f_off;
 
-    // f_i pulled into site t0 + k: shared memory, or global memory across a periodic wrap
+    int xs_[SPT], ys_[SPT], zs_[SPT];
+    bool act[SPT], bnd[SPT];
+    bool any_bnd = false;
+#pragma unroll
+    for (int k = 0; k < SPT; k++) {
+        const int64_t s = s0 + threadIdx.x + k * kStagedThreads;
+        act[k] = s < n3;
+        const int64_t sc = act[k] ? s : 0;
+        const int row = div_e(sc, mE);
+        const int x = (int)(sc - (int64_t)row * Ei);
+        const int z = div_e(row, mE);
+        const int y = row - z * Ei;
+        xs_[k] = x;
+        ys_[k] = y;
+        zs_[k] = z;
+        bnd[k] = act[k] && ((!px && (x == 0 || x == Ei - 1)) || (!py && (y == 0 || y == Ei - 1)) ||
+                            (!pz && (z == 0 || z == Ei - 1)));
+        any_bnd |= bnd[k];
+    }
+
+    // f_i pulled into site k: shared memory, or global memory across a periodic wrap
     auto fval = [&](int i, int k) -> A {
         const int cx = cvec(i, 0), cy = cvec(i, 1), cz = cvec(i, 2);
         if (PER) {
-            const int xs = x0 + k - cx, ys = y - cy, zs = z - cz;
+            const int xs = xs_[k] - cx, ys = ys_[k] - cy, zs = zs_[k] - cz;
             const bool wrap = (px && (xs < 0 || xs >= Ei)) || (py && (ys < 0 || ys >= Ei)) ||
                               (pz && (zs < 0 || zs >= Ei));
             if (wrap)
@@ -169,20 +186,14 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
                                 ((int64_t)wrapi(zs, Ei) * Ei + wrapi(ys, Ei)) * Ei + wrapi(xs, Ei)]);
         }
         const E* row = reinterpret_cast<const E*>(stage + i * kStagedRowStride);
-        return S::in(row[H + t0 + k - cx]);
+        return S::in(row[H + threadIdx.x + k * kStagedThreads - cx]);
     };
 
     A drho[SPT], ux[SPT], uy[SPT], uz[SPT];
-    unsigned bmask = 0;
-    if (active) {
-        if (row_bnd) bmask = (1u << SPT) - 1u;
-        else if (!px) bmask = (x0 == 0 ? 1u : 0u) | (x0 + SPT == Ei ? (1u << (SPT - 1)) : 0u);
-    }
-    const bool any_interior = active && !row_bnd;
 #pragma unroll
     for (int k = 0; k < SPT; k++) {
         A r = A(0), jx = A(0), jy = A(0), jz = A(0);
-        if (any_interior) {
+        if (act[k] && !bnd[k]) {
 #pragma unroll
             for (int i = 0; i < kQ; i++) {
                 const A f = fval(i, k);
@@ -204,14 +215,14 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
         uy[k] = jy * inv;
         uz[k] = jz * inv;
     }
-    if (bmask) {
-        const TimeWeights<R> tw = time_weights<R>(n, bd.K, bd.time_interp);
+    if (any_bnd) {
+        const TimeWeights<R> tw = time_weights<R>(n, bd.K, bd.time_interp, p.ring_slots);
         const R* ring = reinterpret_cast<const R*>(p.ring);
 #pragma unroll
         for (int k = 0; k < SPT; k++) {
-            if (bmask & (1u << k)) {
+            if (bnd[k]) {
                 int pp, qq;
-                const int f = owning_face(x0 + k, y, z, Ei, per, pp, qq);
+                const int f = owning_face(xs_[k], ys_[k], zs_[k], Ei, per, pp, qq);
                 R ub[3];
                 boundary_velocity<R>(ring, p.ring_slot_elems, bd.ring_off, Ei, f, pp, qq, tw, ub);
                 drho[k] = (A)bd.rho_b - A(1);
@@ -233,7 +244,6 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
     for (int i = 0; i < kQ; i++) {
         const A w = wgt<A>(i);
         const int cx = cvec(i, 0), cy = cvec(i, 1), cz = cvec(i, 2);
-        P o;
 #pragma unroll
         for (int k = 0; k < SPT; k++) {
             const A rho = A(1) + drho[k];
@@ -243,7 +253,7 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
             if (cz) cu += cz * uz[k];
             const A deq = w * (drho[k] + rho * (A(3) * cu + A(4.5) * cu * cu - usq[k]));
             A val = deq;
-            if (!(bmask & (1u << k))) {
+            if (!bnd[k]) {
                 const A f = fval(i, k);
                 val = f + om * (deq - f);
                 if (ACCEL) {
@@ -251,33 +261,36 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
                     val += srcfac * w * rho * (A(3) * (ca - ua[k]) + A(9) * cu * ca);
                 }
             }
-            o.e[k] = S::out(val);
+            if (act[k]) Bb[(int64_t)i * n3 + s0 + threadIdx.x + k * kStagedThreads] = S::out(val);
         }
-        if (active) reinterpret_cast<Raw*>(Bb + (int64_t)i * n3 + s)[0] = o.raw;
     }
 }
 
+// Persistent blocks take tiles from a global counter (reset to zero by the
+// forced re-collision at the end of every step), so a block that starts late
+// -- its SM still busy with the bead kernel -- simply takes fewer tiles.
 template <int ST>
 __global__ void __launch_bounds__(kStagedThreads, 1) k_stream_collide_staged(SCParams p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kStagedStages * kStagedStageBytes);
+    __shared__ int64_t sTile[kStagedStages];
     constexpr int T = Staged<ST>::kSites;
     const int64_t n = *p.step;
     if (threadIdx.x == 0) {
         for (int st = 0; st < kStagedStages; st++) mbar_init(&bar[st], 1);
         fence_mbar_init();
+        for (int st = 0; st < kStagedStages; st++) {
+            const int64_t t = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(p.tile_counter), 1ull);
+            sTile[st] = t < p.total_tiles ? t : -1;
+            if (t < p.total_tiles) issue_tile<ST>(p, t, smem + st * kStagedStageBytes, &bar[st]);
+        }
     }
     __syncthreads();
-    // prologue: the first two tiles of this block
-    if (threadIdx.x == 0)
-        for (int st = 0; st < kStagedStages; st++) {
-            const int64_t tile = blockIdx.x + (int64_t)st * gridDim.x;
-            if (tile < p.total_tiles) issue_tile<ST>(p, tile, smem + st * kStagedStageBytes, &bar[st]);
-        }
-    int k = 0;
-    for (int64_t tile = blockIdx.x; tile < p.total_tiles; tile += gridDim.x, k++) {
+    for (int k = 0;; k++) {
         const int st = k & 1;
+        const int64_t tile = sTile[st];
+        if (tile < 0) break;  // later fetches are larger: nothing else is in flight
         const uint32_t phase = (uint32_t)((k >> 1) & 1);
         const int b = locate_box(p, tile);
         const BoxDev& bd = p.boxes[b];
@@ -308,10 +321,11 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_stream_collide_staged(SCP
         }
         __syncthreads();  // every thread is done with this stage
         if (threadIdx.x == 0) {
-            const int64_t next = tile + (int64_t)kStagedStages * gridDim.x;
-            if (next < p.total_tiles) {
+            const int64_t t = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(p.tile_counter), 1ull);
+            sTile[st] = t < p.total_tiles ? t : -1;
+            if (t < p.total_tiles) {
                 fence_proxy_async_smem();
-                issue_tile<ST>(p, next, smem + st * kStagedStageBytes, &bar[st]);
+                issue_tile<ST>(p, t, smem + st * kStagedStageBytes, &bar[st]);
             }
         }
     }

@@ -70,8 +70,8 @@ def load(path: str | None = None, build_if_missing: bool = True):
             _build.build()
     lib = ctypes.CDLL(path)
     sig = {
-        "lb_plan": (_i32, [ctypes.POINTER(lb_box_desc), _i32, _i32, ctypes.POINTER(_sz)]),
-        "lb_create": (_i32, [ctypes.POINTER(lb_box_desc), _i32, _i32, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+        "lb_plan": (_i32, [ctypes.POINTER(lb_box_desc), _i32, _i32, _i32, ctypes.POINTER(_sz)]),
+        "lb_create": (_i32, [ctypes.POINTER(lb_box_desc), _i32, _i32, _i32, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
         "lb_destroy": (_i32, [_vp]),
         "lb_init": (_i32, [_vp, _i32, _vp]),
         "lb_set_boundary": (_i32, [_vp, _i32, _i64, _vp]),
@@ -160,10 +160,11 @@ class Tracers:
     """A context of one or more tracer boxes on one GPU.
 
     boxes: list of lb_box_desc; storage: LB_STORE_*; stream: torch.cuda.Stream
-    (default: a new stream on the current device).
+    (default: a new stream on the current device); ring_slots: depth of the
+    boundary-sample ring (0 = 4).
     """
 
-    def __init__(self, boxes, storage=LB_STORE_F32, stream=None):
+    def __init__(self, boxes, storage=LB_STORE_F32, stream=None, ring_slots=0):
         torch = _torch()
         lib = load()
         self.torch = torch
@@ -173,11 +174,11 @@ class Tracers:
         arr = (lb_box_desc * len(self.descs))(*self.descs)
         self._arr = arr
         nbytes = _sz()
-        _check(lib.lb_plan(arr, len(self.descs), storage, ctypes.byref(nbytes)))
+        _check(lib.lb_plan(arr, len(self.descs), storage, int(ring_slots), ctypes.byref(nbytes)))
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.arena = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.stream.device)
         ctx = _vp()
-        _check(lib.lb_create(arr, len(self.descs), storage, self.arena.data_ptr(), nbytes.value,
+        _check(lib.lb_create(arr, len(self.descs), storage, int(ring_slots), self.arena.data_ptr(), nbytes.value,
                              self.stream.cuda_stream, ctypes.byref(ctx)))
         self.ctx = ctx
         self.real = torch.float64 if storage == LB_STORE_F64 else torch.float32

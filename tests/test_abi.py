@@ -34,14 +34,18 @@ def test_plan_validates_without_a_gpu():
     lib = lbt.load()
     n = ctypes.c_size_t()
     good = (lbt.lb_box_desc * 1)(lbt.box_desc(32, 0.8, nbeads=16))
-    assert lib.lb_plan(good, 1, lbt.LB_STORE_F32, ctypes.byref(n)) == lbt.LB_OK
+    assert lib.lb_plan(good, 1, lbt.LB_STORE_F32, 0, ctypes.byref(n)) == lbt.LB_OK
     # two population buffers of 19 * 32^3 floats dominate the arena
     assert n.value >= 2 * 19 * 32 ** 3 * 4
     for bad in (lbt.box_desc(30, 0.8), lbt.box_desc(32, 0.5), lbt.box_desc(32, 0.8, K=0),
                 lbt.box_desc(32, 0.8, nbeads=300)):
         arr = (lbt.lb_box_desc * 1)(bad)
-        assert lib.lb_plan(arr, 1, lbt.LB_STORE_F32, ctypes.byref(n)) == lbt.LB_ERR_ARG
+        assert lib.lb_plan(arr, 1, lbt.LB_STORE_F32, 0, ctypes.byref(n)) == lbt.LB_ERR_ARG
     mixed = lbt.box_desc(32, 0.8)
     mixed.face_mode[0] = lbt.LB_FACE_PERIODIC  # x- periodic but x+ velocity
-    assert lib.lb_plan((lbt.lb_box_desc * 1)(mixed), 1, lbt.LB_STORE_F32, ctypes.byref(n)) == lbt.LB_ERR_ARG
+    assert lib.lb_plan((lbt.lb_box_desc * 1)(mixed), 1, lbt.LB_STORE_F32, 0, ctypes.byref(n)) == lbt.LB_ERR_ARG
     assert b"periodic" in lib.lb_last_error(None).lower() or b"axis" in lib.lb_last_error(None)
+    assert lib.lb_plan(good, 1, lbt.LB_STORE_F32, 3, ctypes.byref(n)) == lbt.LB_ERR_ARG  # ring shorter than 4
+    n20 = ctypes.c_size_t()
+    assert lib.lb_plan(good, 1, lbt.LB_STORE_F32, 20, ctypes.byref(n20)) == lbt.LB_OK
+    assert n20.value >= n.value + 16 * 6 * 3 * 32 * 32 * 4  # 16 more slots of six 32^2 faces
