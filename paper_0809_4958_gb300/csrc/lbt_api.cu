@@ -146,6 +146,7 @@ struct lb_ctx {
     int64_t step = 0;                  // steps enqueued so far
     std::vector<int64_t> pushed;       // last boundary sample pushed per box (-1 none)
     int kernel = LB_KERNEL_STAGED;
+    int max_beads = 0;  // largest chain capacity of the context
     int threads = 256, ctas = 0, vw = 0;  // vw: sites per thread in stream-collide
     std::vector<int64_t> tile_prefix;  // for the current block size
     cudaGraphExec_t graph = nullptr;
@@ -191,12 +192,12 @@ int default_vw(int storage) { return storage == kF64 ? 2 : (storage == kF32 ? 4 
 
 int rebuild_tiles(lb_ctx* ctx)
 {
-    const int vw = ctx->vw;
+    // sites per tile: fixed by the staged kernel's geometry, threads x sites per thread otherwise
+    const int64_t T = ctx->kernel == LB_KERNEL_STAGED ? lbt_staged_tile_sites(ctx->storage)
+                                                      : (int64_t)ctx->threads * ctx->vw;
     ctx->tile_prefix.assign(ctx->nboxes + 1, 0);
-    for (int b = 0; b < ctx->nboxes; b++) {
-        const int64_t groups = ctx->boxes[b].n3 / vw;
-        ctx->tile_prefix[b + 1] = ctx->tile_prefix[b] + (groups + ctx->threads - 1) / ctx->threads;
-    }
+    for (int b = 0; b < ctx->nboxes; b++)
+        ctx->tile_prefix[b + 1] = ctx->tile_prefix[b] + (ctx->boxes[b].n3 + T - 1) / T;
     CK(cudaMemcpyAsync(ctx->at<int64_t>(ctx->L.tile_prefix), ctx->tile_prefix.data(),
                        sizeof(int64_t) * (ctx->nboxes + 1), cudaMemcpyHostToDevice, ctx->stream));
     // the host vector must outlive the copy: synchronise (set-up path only)
@@ -260,7 +261,7 @@ int enqueue_step(lb_ctx* ctx)
         bp.forces = ctx->at<ForceEntry>(ctx->L.forces);
         bp.step = ctx->at<int64_t>(ctx->L.step);
         bp.status = ctx->at<int32_t>(ctx->L.status);
-        CK(DISPATCH(ctx->storage, bead_couple(bp, nch, ctx->side)));
+        CK(DISPATCH(ctx->storage, bead_couple(bp, nch, ctx->max_beads, ctx->side)));
         CK(cudaEventRecord(ctx->ev_join, ctx->side));
     }
     SCParams sp;
@@ -277,10 +278,14 @@ int enqueue_step(lb_ctx* ctx)
     sp.tile_counter = ctx->at<int64_t>(ctx->L.tile_counter);
     sp.status = ctx->at<int32_t>(ctx->L.status);
     const bool timed = ctx->profiling && ctx->prof_used + 2 <= ctx->prof_ev.size();
-    if (timed) CK(cudaEventRecord(ctx->prof_ev[ctx->prof_used], ctx->stream));
+    // inside a stream capture the timing events must become event-record nodes of the graph
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (timed) CK(cudaStreamIsCapturing(ctx->stream, &cap));
+    const unsigned evflags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (timed) CK(cudaEventRecordWithFlags(ctx->prof_ev[ctx->prof_used], ctx->stream, evflags));
     CK(DISPATCH(ctx->storage, stream_collide(sp, ctx->kernel, ctx->threads, ctx->ctas, ctx->vw, ctx->stream)));
     if (timed) {
-        CK(cudaEventRecord(ctx->prof_ev[ctx->prof_used + 1], ctx->stream));
+        CK(cudaEventRecordWithFlags(ctx->prof_ev[ctx->prof_used + 1], ctx->stream, evflags));
         ctx->prof_used += 2;
     }
     if (nch > 0) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
@@ -434,6 +439,7 @@ int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int
             ch.mass = 1.0;
             bd.chain = (int)ctx->chains.size();
             ctx->chains.push_back(ch);
+            if (d.nbeads > ctx->max_beads) ctx->max_beads = d.nbeads;
             beads += d.nbeads;
         }
         ctx->boxes.push_back(bd);
@@ -533,6 +539,18 @@ int32_t lb_set_boundary(lb_ctx* ctx, int32_t box, int64_t j, const void* face_u)
     }
     char* slot = ctx->arena + ctx->L.ring + (size_t)(j % ctx->L.ring_slots) * ctx->L.ring_slot_elems * rb;
     const char* src = reinterpret_cast<const char*>(face_u);
+    // boxes whose ring regions are packed back to back take one copy
+    size_t packed = 0;
+    bool contiguous = true;
+    for (int b = b0; b < b1 && contiguous; b++) {
+        contiguous = (size_t)ctx->boxes[b].ring_off * rb == (size_t)ctx->boxes[b0].ring_off * rb + packed;
+        packed += 6 * 3 * (size_t)ctx->boxes[b].E * ctx->boxes[b].E * rb;
+    }
+    if (contiguous && b1 - b0 > 1) {
+        CK(cudaMemcpyAsync(slot + ctx->boxes[b0].ring_off * rb, src, packed, cudaMemcpyDefault, ctx->stream));
+        for (int b = b0; b < b1; b++) ctx->pushed[b] = j;
+        return LB_OK;
+    }
     for (int b = b0; b < b1; b++) {
         const int64_t E = ctx->boxes[b].E;
         const size_t bytes = 6 * 3 * E * E * rb;

@@ -110,7 +110,7 @@ struct ForcedParams {
 template <int ST>
 struct Launch {
     static cudaError_t stream_collide(const SCParams& p, int kernel, int threads, int ctas, int vw, cudaStream_t s);
-    static cudaError_t bead_couple(const BeadParams& p, int nchains, cudaStream_t s);
+    static cudaError_t bead_couple(const BeadParams& p, int nchains, int max_beads, cudaStream_t s);
     static cudaError_t forced(const ForcedParams& p, cudaStream_t s);
     static cudaError_t init(void* A, const BoxDev* boxes, int box, int64_t n3, const void* u0, cudaStream_t s);
     static cudaError_t fields(const void* A, const BoxDev* boxes, int box, int64_t n3, int what, void* dst,
@@ -132,3 +132,6 @@ cudaError_t launch_synth_volume(const double* kvec, const double* amp, const dou
 
 // Message returned by lb_last_error(NULL) for calls that have no context.
 void lbt_set_last_error(const char* msg);
+
+// Sites per tile of the staged stream-collide kernel for a storage format.
+int lbt_staged_tile_sites(int storage);

@@ -266,12 +266,23 @@ __device__ __forceinline__ void moments(const A f[kQ], A& drho, A j[3])
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void set_status(int32_t* st, int code) { atomicCAS(st, 0, code); }
 
-constexpr int kMaxNb = 48;              // Verlet neighbours per bead
+constexpr int kMaxNb = 48;              // Verlet neighbours per bead (a quarter per lane)
+constexpr int kNbPerLane = kMaxNb / 4;
 constexpr double kSkin = 0.3;           // Verlet skin (lattice units)
 constexpr int kNoiseChunk = 10;         // substeps whose noise is drawn at once
+constexpr int kBeadThreadsMax = 4 * kMaxBeads;
+
+// Dynamic shared memory of the bead kernel: positions relative to bead 0's
+// start-of-step position, double-buffered over substeps, and the noise of
+// one chunk of substeps.
+template <class MT>
+constexpr size_t bead_dyn_bytes()
+{
+    return sizeof(MT) * (2 * 3 * kMaxBeads + 3 * kNoiseChunk * kMaxBeads);
+}
 
 template <int ST>
-__global__ void __launch_bounds__(kMaxBeads) k_bead_couple(BeadParams p)
+__global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
 {
     using S = Stor<ST>;
     using A = typename S::A;
@@ -284,19 +295,22 @@ __global__ void __launch_bounds__(kMaxBeads) k_bead_couple(BeadParams p)
     const int Ei = bd.E, per = bd.per_mask;
     const int64_t n3 = bd.n3;
     const int64_t n = *p.step;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, nthr = blockDim.x;
 
-    __shared__ double sR[kMaxBeads][3];      // current positions
-    __shared__ MT sX[kMaxBeads][3];          // positions relative to sRc (pair geometry)
+    __shared__ double sR[kMaxBeads][3];      // start-of-step, then end-of-step positions
     __shared__ double sD[kMaxBeads][3];      // start-of-step offsets inside the stencil cell
     __shared__ int sBase[kMaxBeads][3];      // start-of-step stencil corner
     __shared__ MT sU[kMaxBeads][3];          // fluid velocity at each bead
+    __shared__ MT sV[kMaxBeads][3];          // velocities
     __shared__ MT sP[kMaxBeads][3];          // momentum given to the fluid
-    __shared__ unsigned char sNb[kMaxBeads][kMaxNb];
-    __shared__ int sNbN[kMaxBeads];
+    __shared__ unsigned char sNb[kMaxBeads][4][kNbPerLane];
+    __shared__ unsigned char sNbN[kMaxBeads][4];
     __shared__ double sRc[3];
-    __shared__ double sRed[2][kMaxBeads / 32][3];
+    __shared__ double sRed[2][kBeadThreadsMax / 32][3];
     __shared__ int sErr;
+    extern __shared__ __align__(16) unsigned char bead_dyn[];
+    MT* sXbuf = reinterpret_cast<MT*>(bead_dyn);       // [2][kMaxBeads][3]
+    MT* sXi = sXbuf + 2 * 3 * kMaxBeads;               // [kNoiseChunk][N][3]
 
     double* pos = p.pos + 3 * ch.bead_off;
     double* vel = p.vel + 3 * ch.bead_off;
@@ -306,24 +320,22 @@ __global__ void __launch_bounds__(kMaxBeads) k_bead_couple(BeadParams p)
     }
     __syncthreads();
 
-    // 1. stencil of the start-of-step position
-    double R[3] = {0, 0, 0};
-    MT V[3] = {0, 0, 0};
-    if (tid < N) {
+    // 1. stencil of the start-of-step position (one thread per bead)
+    for (int bb = tid; bb < N; bb += nthr) {
         for (int a = 0; a < 3; a++) {
-            R[a] = pos[3 * tid + a];
-            V[a] = (MT)vel[3 * tid + a];
-            const double fl = floor(R[a]);
-            sD[tid][a] = R[a] - fl;
+            const double R = pos[3 * bb + a];
+            sR[bb][a] = R;
+            sV[bb][a] = (MT)vel[3 * bb + a];
+            const double fl = floor(R);
+            sD[bb][a] = R - fl;
             long long i0 = (long long)fl;
             if (!((per >> a) & 1)) {
                 if (i0 < 1 || i0 + 1 > Ei - 2) sErr = LB_ERR_BEAD_OOB;
-                sBase[tid][a] = (int)i0;
+                sBase[bb][a] = (int)i0;
             } else {
-                sBase[tid][a] = (int)(((i0 % Ei) + Ei) % Ei);
+                sBase[bb][a] = (int)(((i0 % Ei) + Ei) % Ei);
             }
-            sR[tid][a] = R[a];
-            sX[tid][a] = (MT)(R[a] - sRc[a]);
+            sXbuf[3 * bb + a] = (MT)(R - sRc[a]);
         }
     }
     __syncthreads();
@@ -338,7 +350,7 @@ __global__ void __launch_bounds__(kMaxBeads) k_bead_couple(BeadParams p)
 
     // 2. fluid velocity at the beads: eight threads per bead, one corner each
     const typename S::E* Ab = reinterpret_cast<const typename S::E*>(p.A) + bd.f_off;
-    for (int base = 0; base < 8 * N; base += blockDim.x) {
+    for (int base = 0; base < 8 * N; base += nthr) {
         const int e = base + tid;
         const bool act = e < 8 * N;
         double uc[3] = {0, 0, 0};
@@ -362,99 +374,105 @@ __global__ void __launch_bounds__(kMaxBeads) k_bead_couple(BeadParams p)
         if (act && (e & 7) == 0)
             for (int a = 0; a < 3; a++) sU[e >> 3][a] = (MT)uc[a];
     }
+    __syncthreads();
 
     // 3. MD substeps (symplectic Euler), fluid velocity frozen over the step.
-    //    The noise of kNoiseChunk substeps is drawn up front by all threads in
-    //    parallel (Philox4x64-10 is independent of the MD state).
+    //    Four lanes per bead: lane q holds coordinate q of the velocity, of the
+    //    displacement since the start of the step and of the momentum handed to
+    //    the fluid, and a quarter of the bead's WCA neighbours; the force is
+    //    summed over the four lanes by shuffles.  Positions inside the step are
+    //    start + displacement, relative to bead 0's start-of-step position;
+    //    the FP64 position is updated once at the end.  The noise of
+    //    kNoiseChunk substeps is drawn up front by all threads.
+    const int q = tid & 3, bead = tid >> 2;
+    const bool own = bead < N;
+    const bool comp = own && q < 3;
     const MT dt = MT(1) / (MT)ch.n_md;
-    const double dtd = 1.0 / ch.n_md;
-    const MT namp = ch.kT > 0.0 ? (MT)sqrt(2.0 * ch.kT * ch.zeta / dtd) : MT(0);
+    const MT namp = ch.kT > 0.0 ? (MT)sqrt(2.0 * ch.kT * ch.zeta / (1.0 / ch.n_md)) : MT(0);
     const MT R02 = (MT)(ch.R0 * ch.R0), inv_R02 = MT(1) / R02, kf = (MT)ch.k_fene, zeta = (MT)ch.zeta;
-    const MT dtm = dt / (MT)ch.mass;
+    const MT dtm = dt / (MT)ch.mass, fext = comp ? (MT)ch.f_ext[q] : MT(0);
     const bool wca = ch.eps > 0.0;
     const MT sig2 = (MT)(ch.sigma * ch.sigma), rc2 = (MT)(cbrt(2.0) * ch.sigma * ch.sigma), e24 = (MT)(24.0 * ch.eps);
     const MT rl = (MT)(sqrt(cbrt(2.0)) * ch.sigma + kSkin), rl2 = rl * rl;  // WCA cut-off 2^(1/6) sigma + skin
     const MT half_skin2 = (MT)(0.25 * kSkin * kSkin);
-    extern __shared__ __align__(16) unsigned char bead_dyn[];
-    MT* sXi = reinterpret_cast<MT*>(bead_dyn);  // [kNoiseChunk][N][3] unit-variance noise
-    MT Xref[3] = {0, 0, 0};
-    MT P[3] = {0, 0, 0};
+    const MT X0 = comp ? sXbuf[3 * bead + q] : MT(0);
+    const MT Uq = comp ? sU[bead][q] : MT(0);
+    MT Vq = comp ? sV[bead][q] : MT(0);
+    MT Dq = MT(0), Pq = MT(0), Xref = X0;
     bool need_build = true;
-    __syncthreads();
     for (int sub = 0; sub < ch.n_md; sub++) {
+        const MT* Xc = sXbuf + (sub & 1) * 3 * kMaxBeads;
+        MT* Xn = sXbuf + ((sub + 1) & 1) * 3 * kMaxBeads;
         const int cs = sub % kNoiseChunk;
         if (namp > MT(0) && cs == 0) {
             const int nc = min(kNoiseChunk, ch.n_md - sub);
-            for (int q = tid; q < nc * N; q += blockDim.x) {
-                const int sb = q / N, bb = q - sb * N;
+            for (int w = tid; w < nc * N; w += nthr) {
+                const int sb = w / N, bb = w - sb * N;
                 uint64_t x[4] = {(uint64_t)n, (uint64_t)(sub + sb), (uint64_t)bb, (uint64_t)b};
                 philox4x64_10(x, ch.seed, 0);
                 for (int a = 0; a < 3; a++) sXi[(sb * N + bb) * 3 + a] = (MT)unit_uniform(x[a]);
             }
-            __syncthreads();
         }
-        if (wca) {
-            bool moved = false;
-            if (tid < N && !need_build) {
-                MT d2 = 0;
-                for (int a = 0; a < 3; a++) {
-                    const MT d = sX[tid][a] - Xref[a];
-                    d2 += d * d;
-                }
-                moved = d2 > half_skin2;
-            }
-            if (__syncthreads_or(moved) || need_build) {
-                if (tid < N) {
-                    int cnt = 0;
-                    for (int b2 = 0; b2 < N; b2++) {
-                        if (b2 == tid) continue;
-                        MT d2 = 0;
-                        for (int a = 0; a < 3; a++) {
-                            const MT d = sX[tid][a] - sX[b2][a];
-                            d2 += d * d;
-                        }
-                        if (d2 < rl2) {
-                            if (cnt < kMaxNb) sNb[tid][cnt] = (unsigned char)b2;
-                            cnt++;
-                        }
+        // has any bead moved more than half the skin since the last list?
+        MT d2 = MT(0);
+        if (comp && !need_build) {
+            const MT d = Xc[3 * bead + q] - Xref;
+            d2 = d * d;
+        }
+        d2 += __shfl_xor_sync(0xffffffffu, d2, 1);
+        d2 += __shfl_xor_sync(0xffffffffu, d2, 2);
+        const bool rebuild = __syncthreads_or(own && d2 > half_skin2) || need_build;  // also orders Xn writes
+        if (sErr) break;
+        if (wca && rebuild) {
+            if (own) {
+                int cnt = 0;
+                for (int b2 = q; b2 < N; b2 += 4) {
+                    if (b2 == bead) continue;
+                    MT e2 = MT(0);
+                    for (int a = 0; a < 3; a++) {
+                        const MT d = Xc[3 * bead + a] - Xc[3 * b2 + a];
+                        e2 += d * d;
                     }
-                    if (cnt > kMaxNb) sErr = LB_ERR_CHAIN;  // more neighbours than the list holds
-                    sNbN[tid] = cnt < kMaxNb ? cnt : kMaxNb;
-                    for (int a = 0; a < 3; a++) Xref[a] = sX[tid][a];
+                    if (e2 < rl2) {
+                        if (cnt < kNbPerLane) sNb[bead][q][cnt] = (unsigned char)b2;
+                        cnt++;
+                    }
                 }
-                need_build = false;
+                if (cnt > kNbPerLane) sErr = LB_ERR_CHAIN;  // more neighbours than the list holds
+                sNbN[bead][q] = (unsigned char)(cnt < kNbPerLane ? cnt : kNbPerLane);
+                if (comp) Xref = Xc[3 * bead + q];
             }
+            need_build = false;
         }
-        if (tid < N) {
-            MT F[3] = {0, 0, 0};
-            if (tid > 0) {  // bond (tid-1, tid): force -k r / (1 - r^2/R0^2) on the upper bead
+        MT F[3] = {0, 0, 0};
+        if (own) {
+            if (q == 0 && bead > 0) {  // bond (bead-1, bead): force -k r / (1 - r^2/R0^2) on the upper bead
                 MT r[3], r2 = 0;
                 for (int a = 0; a < 3; a++) {
-                    r[a] = sX[tid][a] - sX[tid - 1][a];
+                    r[a] = Xc[3 * bead + a] - Xc[3 * (bead - 1) + a];
                     r2 += r[a] * r[a];
                 }
                 if (r2 >= R02) sErr = LB_ERR_FENE;
                 const MT fac = kf / (MT(1) - r2 * inv_R02);
                 for (int a = 0; a < 3; a++) F[a] -= fac * r[a];
             }
-            if (tid + 1 < N) {  // bond (tid, tid+1): opposite force on the lower bead
+            if (q == 1 && bead + 1 < N) {  // bond (bead, bead+1): opposite force on the lower bead
                 MT r[3], r2 = 0;
                 for (int a = 0; a < 3; a++) {
-                    r[a] = sX[tid + 1][a] - sX[tid][a];
+                    r[a] = Xc[3 * (bead + 1) + a] - Xc[3 * bead + a];
                     r2 += r[a] * r[a];
                 }
                 if (r2 >= R02) sErr = LB_ERR_FENE;
                 const MT fac = kf / (MT(1) - r2 * inv_R02);
                 for (int a = 0; a < 3; a++) F[a] += fac * r[a];
             }
-            if (wca) {  // WCA: 24 eps (2 (s/r)^12 - (s/r)^6) / r^2 along R_tid - R_partner
-                const int cnt = sNbN[tid];
-#pragma unroll 4
+            if (wca) {  // WCA: 24 eps (2 (s/r)^12 - (s/r)^6) / r^2 along R_bead - R_partner
+                const int cnt = sNbN[bead][q];
                 for (int k = 0; k < cnt; k++) {
-                    const int b2 = sNb[tid][k];
+                    const int b2 = sNb[bead][q][k];
                     MT r[3], r2 = 0;
                     for (int a = 0; a < 3; a++) {
-                        r[a] = sX[tid][a] - sX[b2][a];
+                        r[a] = Xc[3 * bead + a] - Xc[3 * b2 + a];
                         r2 += r[a] * r[a];
                     }
                     if (r2 < rc2) {
@@ -465,36 +483,48 @@ __global__ void __launch_bounds__(kMaxBeads) k_bead_couple(BeadParams p)
                     }
                 }
             }
-            for (int a = 0; a < 3; a++) {
-                const MT ffric = -zeta * (V[a] - sU[tid][a]);
-                const MT fnoise = namp > MT(0) ? namp * sXi[(cs * N + tid) * 3 + a] : MT(0);
-                const MT ftot = F[a] + ffric + fnoise + (MT)ch.f_ext[a];
-                V[a] += dtm * ftot;
-                R[a] += dtd * (double)V[a];
-                P[a] -= (ffric + fnoise) * dt;
-            }
         }
-        __syncthreads();
-        if (tid < N)
-            for (int a = 0; a < 3; a++) {
-                sR[tid][a] = R[a];
-                sX[tid][a] = (MT)(R[a] - sRc[a]);
-            }
-        __syncthreads();
-        if (sErr) break;
+        for (int a = 0; a < 3; a++) {
+            F[a] += __shfl_xor_sync(0xffffffffu, F[a], 1);
+            F[a] += __shfl_xor_sync(0xffffffffu, F[a], 2);
+        }
+        if (comp) {
+            const MT Fq = q == 0 ? F[0] : (q == 1 ? F[1] : F[2]);
+            const MT ffric = -zeta * (Vq - Uq);
+            const MT fnoise = namp > MT(0) ? namp * sXi[(cs * N + bead) * 3 + q] : MT(0);
+            const MT ftot = Fq + ffric + fnoise + fext;
+            Vq += dtm * ftot;
+            Dq += dt * Vq;
+            Pq -= (ffric + fnoise) * dt;
+            Xn[3 * bead + q] = X0 + Dq;
+        }
+        if (namp > MT(0) && (sub + 1) % kNoiseChunk == 0) __syncthreads();  // noise chunk consumed
     }
+    __syncthreads();
     if (sErr) {
         if (tid == 0) set_status(&p.status[b], sErr);
         return;
     }
+    if (comp) {
+        sR[bead][q] += (double)Dq;
+        sV[bead][q] = Vq;
+        sP[bead][q] = Pq;
+    }
+    __syncthreads();
 
-    // 4. centre of mass pinned at the box centre
+    // 4. centre of mass pinned at the box centre (one thread per bead)
+    double R[3] = {0, 0, 0}, V[3] = {0, 0, 0};
+    if (tid < N)
+        for (int a = 0; a < 3; a++) {
+            R[a] = sR[tid][a];
+            V[a] = (double)sV[tid][a];
+        }
     if (ch.pin_com >= 1) {
         const int warp = tid >> 5, lane = tid & 31;
         for (int pass = 0; pass < 2; pass++) {
             double s[3];
             for (int a = 0; a < 3; a++) {
-                s[a] = tid < N ? (pass == 0 ? R[a] : (double)V[a]) : 0.0;
+                s[a] = tid < N ? (pass == 0 ? R[a] : V[a]) : 0.0;
                 for (int o = 16; o > 0; o >>= 1) s[a] += __shfl_xor_sync(0xffffffffu, s[a], o);
             }
             if (lane == 0)
@@ -502,7 +532,7 @@ __global__ void __launch_bounds__(kMaxBeads) k_bead_couple(BeadParams p)
         }
         __syncthreads();
         double com[3] = {0, 0, 0}, vcm[3] = {0, 0, 0};
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++)
+        for (int w = 0; w < (nthr >> 5); w++)
             for (int a = 0; a < 3; a++) {
                 com[a] += sRed[0][w][a];
                 vcm[a] += sRed[1][w][a];
@@ -511,23 +541,20 @@ __global__ void __launch_bounds__(kMaxBeads) k_bead_couple(BeadParams p)
         if (tid < N)
             for (int a = 0; a < 3; a++) {
                 R[a] += centre - com[a] / N;
-                if (ch.pin_com >= 2) V[a] = (MT)((double)V[a] - vcm[a] / N);
+                if (ch.pin_com >= 2) V[a] = (double)(MT)(V[a] - vcm[a] / N);
             }
     }
-    if (tid < N) {
+    if (tid < N)
         for (int a = 0; a < 3; a++) {
             pos[3 * tid + a] = R[a];
-            vel[3 * tid + a] = (double)V[a];
-            sP[tid][a] = P[a];
+            vel[3 * tid + a] = V[a];
         }
-    }
-    __syncthreads();
 
     // 5. force density at the stencil sites: every entry sums, in bead order,
     //    the contributions of all beads whose stencil holds its site; entries
     //    whose site an earlier bead already holds are marked duplicates.
     ForceEntry* fl = p.forces + ch.force_off;
-    for (int e = tid; e < 8 * N; e += blockDim.x) {
+    for (int e = tid; e < 8 * N; e += nthr) {
         const int bb = e >> 3, c = e & 7;
         int s[3] = {sBase[bb][0] + (c & 1), sBase[bb][1] + ((c >> 1) & 1), sBase[bb][2] + ((c >> 2) & 1)};
         for (int a = 0; a < 3; a++)
@@ -742,7 +769,7 @@ cudaError_t Launch<ST>::stream_collide(const SCParams& p, int kernel, int thread
         static bool attr_set = false;  // per storage instantiation
         if (!attr_set) {
             cudaError_t e = cudaFuncSetAttribute(k_stream_collide_staged<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 kStagedSmemBytes);
+                                                 Staged<ST>::kSmemBytes);
             if (e != cudaSuccess) return e;
             attr_set = true;
         }
@@ -755,7 +782,7 @@ cudaError_t Launch<ST>::stream_collide(const SCParams& p, int kernel, int thread
         int64_t grid = ctas > 0 ? ctas : sms;
         if (grid > p.total_tiles) grid = p.total_tiles;
         if (grid < 1) return cudaSuccess;
-        k_stream_collide_staged<ST><<<(unsigned)grid, kStagedThreads, kStagedSmemBytes, s>>>(p);
+        k_stream_collide_staged<ST><<<(unsigned)grid, kStagedThreads, Staged<ST>::kSmemBytes, s>>>(p);
         return cudaGetLastError();
     }
     int64_t grid = (ctas > 0 && ctas < p.total_tiles) ? ctas : p.total_tiles;
@@ -768,18 +795,20 @@ cudaError_t Launch<ST>::stream_collide(const SCParams& p, int kernel, int thread
 }
 
 template <int ST>
-cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, cudaStream_t s)
+cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, int max_beads, cudaStream_t s)
 {
     if (nchains <= 0) return cudaSuccess;
     using MT = typename std::conditional<ST == kF64, double, float>::type;
-    const size_t dyn = sizeof(MT) * 3 * kNoiseChunk * kMaxBeads;  // noise of one chunk of substeps
+    const size_t dyn = bead_dyn_bytes<MT>();
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_bead_couple<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_bead_couple<ST><<<nchains, kMaxBeads, dyn, s>>>(p);
+    int threads = (4 * max_beads + 31) / 32 * 32;  // four lanes per bead
+    if (threads < 64) threads = 64;
+    k_bead_couple<ST><<<nchains, threads, dyn, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -20,20 +20,31 @@
 namespace lbt {
 
 constexpr int kStagedThreads = 512;
-constexpr int kStagedRowBytes = 4096;                          // one population row of a tile
 constexpr int kStagedHaloBytes = 16;                           // x-shift halo on each side
-constexpr int kStagedRowStride = kStagedRowBytes + 2 * kStagedHaloBytes;
-constexpr int kStagedStageBytes = kQ * kStagedRowStride;       // 78 432 B
-constexpr int kStagedStages = 2;
-constexpr int kStagedSmemBytes = kStagedStages * kStagedStageBytes + 64;
 
+// Tile geometry per storage: FP64 keeps two stages of 4 KB rows (one site per
+// thread); the narrower formats run four stages of 2 KB rows so that three
+// tiles are in flight while one is computed.
 template <int ST>
 struct Staged {
     using E = typename Stor<ST>::E;
-    static constexpr int kSites = kStagedRowBytes / (int)sizeof(E);    // sites per tile
-    static constexpr int kSPT = kSites / kStagedThreads;              // sites per thread
-    static constexpr int kHalo = kStagedHaloBytes / (int)sizeof(E);   // halo elements
+    static constexpr int kRowBytes = ST == kF64 ? 4096 : 2048;              // one population row of a tile
+    static constexpr int kStages = ST == kF64 ? 2 : 4;
+    static constexpr int kRowStride = kRowBytes + 2 * kStagedHaloBytes;
+    static constexpr int kStageBytes = kQ * kRowStride;
+    static constexpr int kSmemBytes = kStages * kStageBytes + 64;          // + mbarriers
+    static constexpr int kSites = kRowBytes / (int)sizeof(E);              // sites per tile
+    static constexpr int kSPT = kSites / kStagedThreads;                   // sites per thread
+    static constexpr int kHalo = kStagedHaloBytes / (int)sizeof(E);        // halo elements
+    static_assert(kSPT >= 1, "tile smaller than the block");
 };
+
+// Sites per tile of the staged kernel (host side, for the tile table).
+inline int staged_tile_sites(int storage)
+{
+    return storage == kF64 ? Staged<kF64>::kSites
+                           : (storage == kF32 ? Staged<kF32>::kSites : Staged<kF16>::kSites);
+}
 
 // ---- PTX helpers (mbarrier + bulk copy) ----
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -124,7 +135,7 @@ __device__ __forceinline__ void issue_tile(const SCParams& p, int64_t tile, unsi
     for (int i = 0; i < kQ; i++) {
         if (hi[i] <= lo[i]) continue;
         const int64_t start = s0 - (cvec(i, 1) * Ei + cvec(i, 2) * Ei * Ei) - H;
-        bulk_load(stage + i * kStagedRowStride + (lo[i] - start) * sizeof(E), Ab + (int64_t)i * n3 + lo[i],
+        bulk_load(stage + i * Staged<ST>::kRowStride + (lo[i] - start) * sizeof(E), Ab + (int64_t)i * n3 + lo[i],
                   (uint32_t)((hi[i] - lo[i]) * sizeof(E)), bar);
     }
 }
@@ -185,7 +196,7 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
                 return S::in(Ab[(int64_t)i * n3 +
                                 ((int64_t)wrapi(zs, Ei) * Ei + wrapi(ys, Ei)) * Ei + wrapi(xs, Ei)]);
         }
-        const E* row = reinterpret_cast<const E*>(stage + i * kStagedRowStride);
+        const E* row = reinterpret_cast<const E*>(stage + i * Staged<ST>::kRowStride);
         return S::in(row[H + threadIdx.x + k * kStagedThreads - cx]);
     };
 
@@ -272,6 +283,8 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
 template <int ST>
 __global__ void __launch_bounds__(kStagedThreads, 1) k_stream_collide_staged(SCParams p)
 {
+    constexpr int kStagedStages = Staged<ST>::kStages;
+    constexpr int kStagedStageBytes = Staged<ST>::kStageBytes;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kStagedStages * kStagedStageBytes);
     __shared__ int64_t sTile[kStagedStages];
@@ -288,10 +301,10 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_stream_collide_staged(SCP
     }
     __syncthreads();
     for (int k = 0;; k++) {
-        const int st = k & 1;
+        const int st = k % kStagedStages;
         const int64_t tile = sTile[st];
         if (tile < 0) break;  // later fetches are larger: nothing else is in flight
-        const uint32_t phase = (uint32_t)((k >> 1) & 1);
+        const uint32_t phase = (uint32_t)((k / kStagedStages) & 1);
         const int b = locate_box(p, tile);
         const BoxDev& bd = p.boxes[b];
         const bool arrived = mbar_wait_bounded(&bar[st], phase);

@@ -189,3 +189,5 @@ __global__ void k_cons_final(const BoxDev* boxes, const ChainDev* chains, int nb
 }
 
 }  // namespace lbt
+
+int lbt_staged_tile_sites(int storage) { return lbt::staged_tile_sites(storage); }

@@ -1,0 +1,92 @@
+"""Reduced-precision storage (binary16 / bfloat16 deviations f_i - w_i, FP32
+arithmetic) against the FP64 oracle, through the C ABI.
+
+Two references: the plain FP64 oracle (the benchmark spec's bound for 16-bit
+storage is 2e-3 relative L2 on velocity) and the oracle with the same
+round-to-nearest-even storage emulated in FP64 arithmetic.  The GPU rounds
+FP32 results and the oracle rounds FP64 results, so an occasional value sits
+on the other side of a 16-bit rounding boundary; the one-step comparison
+counts those one-ulp flips instead of demanding bitwise equality.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpucases import Case, GpuRunner, interior, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+F16, BF16 = 2, 3
+
+
+@pytest.fixture(scope="module")
+def lbt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0809_4958_gb300 import lbtracer
+    lbtracer.load()
+    return lbtracer
+
+
+@pytest.fixture(scope="module")
+def cfg0_refs():
+    c = Case(32, 0.8, 500, seed=0, M=256, k_max=16, nbeads=16)
+    plain = c.run_oracle().fields()[1]
+    emul = {F16: c.run_oracle(storage=oracle.STORE_F16).fields()[1],
+            BF16: c.run_oracle(storage=oracle.STORE_BF16).fields()[1]}
+    return c, plain, emul
+
+
+@pytest.mark.parametrize("storage,bound_plain", [(F16, 2e-3), (BF16, 2e-2)])
+def test_16bit_storage_against_fp64_oracle(lbt, cfg0_refs, storage, bound_plain):
+    # 32^3 box with chain, 500 steps.  binary16 meets the 2e-3 bound; bfloat16
+    # (8-bit significand) does not and is held to 2e-2 (its measured error is
+    # recorded in the design doc)
+    c, plain, emul = cfg0_refs
+    r = GpuRunner(lbt, torch, [c], storage)
+    r.step(c.nsteps)
+    u = r.tr.fields(0)[1]
+    e_plain = rel_l2(interior(u), interior(plain))
+    e_emul = rel_l2(interior(u), interior(emul[storage]))
+    print("storage %d: rel L2 vs FP64 oracle %.3e, vs oracle with storage emulation %.3e" % (storage, e_plain, e_emul))
+    assert e_plain <= bound_plain
+    # the emulating oracle is closer to the GPU than the plain one: the error
+    # is the storage rounding, which both share
+    assert e_emul < e_plain
+
+
+@pytest.mark.parametrize("storage", [F16, BF16])
+def test_16bit_one_step_sitewise_at_256(lbt, storage):
+    # 256^3 box (2048 modes, |k| in [1, 128]): from the GPU state after some
+    # steps, one GPU step against one oracle step with the same storage
+    # rounding, site by site
+    from paper_0809_4958_gb300 import inputs
+    E = 256
+    c = Case.__new__(Case)
+    c.E, c.tau, c.K, c.time_interp, c.periodic, c.accel = E, 0.8, 1, 0, (False, False, False), (0.0, 0.0, 0.0)
+    c.nsteps, c.nbeads, c.kT, c.n_md, c.pin_com, c.chain_seed, c.vel0 = 6, 0, 0.0, 50, 2, 0, None
+    c.modes = inputs.mode_table(3, 2048, 1.0, 128.0, E)
+    c.J = 8
+    c.samples = lbt.synth_faces(c.modes, E, 1, 0, c.J, torch.float64).cpu().numpy()
+    c.u0 = lbt.synth_volume(c.modes, E, 0.0, torch.float64).cpu().numpy()
+    c.pos0 = None
+    r = GpuRunner(lbt, torch, [c], storage)
+    r.step(5)
+    A = r.tr.deviations(0).astype(np.float64)
+    r.step(1)
+    B = r.tr.deviations(0).astype(np.float64)
+    _, w = oracle.lattice()
+    box = c.oracle_box(oracle.STORE_F16 if storage == F16 else oracle.STORE_BF16)
+    st, Bref, *_ = oracle.step_from(box, A + w[:, None, None, None], c.samples, 5)
+    assert st == 0
+    dref = Bref - w[:, None, None, None]
+    diff = np.abs(B - dref)
+    # one storage ulp of the value (binary16: 2^-10, bfloat16: 2^-7 of the magnitude)
+    rel_ulp = 2.0 ** -10 if storage == F16 else 2.0 ** -7
+    tol = rel_ulp * np.maximum(np.abs(dref), 2.0 ** -14) * 1.01 + 1e-17
+    assert np.all(diff <= tol)
+    flips = np.count_nonzero(diff > 1e-17)
+    print("storage %d: %d of %d values differ by one storage ulp" % (storage, flips, diff.size))
+    assert flips < 0.01 * diff.size
