@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--storage", default="f32", choices=["f32", "f64", "f16", "bf16"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-tune", action="store_true", help="skip the launch autotuner (use --kernel/--threads/...)")
     p.add_argument("--threads", type=int, default=0, help="stream-collide block size (0 = library default)")
     p.add_argument("--ctas", type=int, default=0, help="persistent grid size (0 = one block per tile)")
     p.add_argument("--vw", type=int, default=0, help="sites per thread in stream-collide (0 = default)")
@@ -263,8 +264,11 @@ def main():
     seed = w["seed"] + rank  # one independent tracer box per GPU
 
     # ---- inputs (untimed): boundary record, initial field, chain ----
+    from paper_0809_4958_gb300 import autotune
     modes = inputs.mode_table(seed, w["M"], w["k_min"], w["k_max"], E)
-    nsamp = args.warmup + args.steps + 2
+    ncand = 0 if args.no_tune else len(autotune.candidates(storage, torch.cuda.get_device_properties(dev).multi_processor_count))
+    tune_steps = 7 * ncand
+    nsamp = args.warmup + tune_steps + args.steps + 2
     faces = lbt.synth_faces(modes, E, w["K"], 0, nsamp, real)
     u0 = lbt.synth_volume(modes, E, 0.0, real)
     pos0 = inputs.chain_start(seed + 5, w["nbeads"], E)
@@ -283,9 +287,17 @@ def main():
             tr.lb_set_boundary(0, pushed[0], src(pushed[0]))
 
     dev_src = lambda j: faces[j]  # noqa: E731
-    for n in range(args.warmup):
-        push_until(n + 1, dev_src)
-        tr.lb_step(1)
+
+    def step(k):
+        for _ in range(k):
+            push_until(tr.lb_current_step() + 1, dev_src)
+            tr.lb_step(1)
+
+    table = []
+    choice = (kernel, args.threads, args.ctas, args.vw)
+    if not args.no_tune:  # the autotuner steps the simulation; its steps are untimed warm-up
+        choice, table = autotune.tune(tr, step, steps_per_candidate=6, use_cache=False)
+    step(args.warmup)
     tr.lb_sync()
 
     # ---- timed region (device-resident inputs) ----
@@ -298,10 +310,7 @@ def main():
     clocks.start()
     time.sleep(0.3)  # let the sampler take its first reading
     ev0.record(stream)
-    n0 = args.warmup
-    for n in range(n0, n0 + args.steps):
-        push_until(n + 1, dev_src)
-        tr.lb_step(1)
+    step(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -320,12 +329,13 @@ def main():
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     if not args.no_e2e:
-        e2e_steps = min(args.steps, 2000)
+        e2e_steps = min(args.steps, 2000, nsamp - 2)
         host_faces = torch.empty((e2e_steps + 2, 6, 3, E, E), dtype=real, pin_memory=True)
         host_faces.copy_(faces[:e2e_steps + 2].cpu())
         host_chain = torch.empty((e2e_steps, 2, w["nbeads"], 3), dtype=torch.float64, pin_memory=True)
         # fresh context so the pushed samples line up with the host record
         tr2 = lbt.Tracers([lbt.box_desc(E, w["tau"], nbeads=w["nbeads"], K=w["K"])], storage, stream=stream)
+        tr2.lb_set_launch(*choice)
         torch.cuda.synchronize()
         tr2.lb_init(0, u0)
         tr2.chain_couple(0, lbt.chain_desc(w["nbeads"], kT=w["kT"], n_md=w["n_md"], seed=seed), pos0)
@@ -371,11 +381,12 @@ def main():
                                "chain kT %g, Kolmogorov velocity boundaries on 6 faces (1024 modes, one sample per "
                                "step)" % (E, w["tau"], args.storage, w["kT"]),
                    "boxes_per_gpu": 1, "sites_per_box": E ** 3, "l2": "working set 2 x %.0f MB > L2, no flush"
-                   % (Q * E ** 3 * s_elem / 1e6), "launch": {"kernel": args.kernel, "threads": args.threads or 256, "ctas": args.ctas,
-                              "sites_per_thread": args.vw or None}},
+                   % (Q * E ** 3 * s_elem / 1e6), "launch": {"kernel": ["staged", "register"][choice[0]], "threads": choice[1], "ctas": choice[2],
+                              "sites_per_thread": choice[3]},
+                   "autotune": [[list(c), t] for c, t in table]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(args.storage),
-                     "kernel": "k_stream_collide_staged" if args.kernel == "staged" else "k_stream_collide",
+                     "kernel": "k_stream_collide_staged" if choice[0] == lbt.LB_KERNEL_STAGED else "k_stream_collide",
                      "avg_launch_ms": avg_sc, "alg_bytes_per_launch": alg,
                      "peak_kind": peak_kind, "launches_timed": sc_n},
         "clocks": clk,
@@ -535,12 +546,13 @@ def run_precision(args):
 
     def stress_neq(d):
         # non-equilibrium momentum flux of the stored populations (analysis only)
-        f = d.double() + wts[:, None]
+        f = d.double() + wts[:, None, None, None]
         rho = f.sum(0)
-        j = cvec.T @ f
+        j = torch.einsum("ia,ixyz->axyz", cvec, f)
         u = j / rho
-        Pi = torch.einsum("ia,ib,is->abs", cvec, cvec, f)
-        return Pi - rho * (torch.eye(3, dtype=torch.float64, device="cuda")[:, :, None] / 3 + u[:, None] * u[None, :])
+        Pi = torch.einsum("ia,ib,ixyz->abxyz", cvec, cvec, f)
+        eye = torch.eye(3, dtype=torch.float64, device="cuda")[:, :, None, None, None]
+        return Pi - rho * (eye / 3 + u[:, None] * u[None, :])
 
     results = {}
     fields = {}

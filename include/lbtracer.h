@@ -239,8 +239,8 @@ int64_t lb_current_step(const lb_ctx* ctx);
  *   ctas = persistent grid (0 = one block per SM).
  *   kernel LB_KERNEL_REGISTER: threads per block (multiple of 32, 64 .. 256),
  *   ctas = persistent grid (0 = one block per tile), sites_per_thread
- *   (0 = default: 2 for FP64, 4 for FP32, 8 for 16-bit storage; half the
- *   default is the other choice).
+ *   (0 = default: 2 for FP64, 4 for FP32, 8 for 16-bit storage; half or a
+ *   quarter of the default, at least 1, are the other choices).
  *   Used by the autotuner.  Drops a captured graph. */
 int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas, int32_t sites_per_thread);
 

@@ -23,9 +23,8 @@ def candidates(storage: int, sms: int):
     dv = {lbt.LB_STORE_F64: 2, lbt.LB_STORE_F32: 4, lbt.LB_STORE_F16DEV: 8, lbt.LB_STORE_BF16DEV: 8}[storage]
     out = [(lbt.LB_KERNEL_STAGED, 0, 0, 0)]
     for threads in (128, 256):
-        for vw in (dv, dv // 2):
-            for ctas in (0, 4 * sms):
-                out.append((lbt.LB_KERNEL_REGISTER, threads, ctas, vw))
+        for vw in sorted({dv, max(dv // 2, 1), max(dv // 4, 1)}):
+            out.append((lbt.LB_KERNEL_REGISTER, threads, 0, vw))
     return out
 
 

@@ -746,9 +746,10 @@ int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas
         if (threads != 256 || vw != dv || ctas < 0)
             return ctx->fail(LB_ERR_ARG, "staged kernel: threads and sites_per_thread 0 (fixed tiles), ctas >= 0");
     } else if (kernel == LB_KERNEL_REGISTER) {
-        if (threads < 64 || threads > 256 || threads % 32 || ctas < 0 || (vw != dv && vw != dv / 2))
-            return ctx->fail(LB_ERR_ARG,
-                             "register kernel: threads multiple of 32 in [64, 256]; ctas >= 0; sites_per_thread default or half");
+        const int v4 = dv / 4 > 0 ? dv / 4 : 1;
+        if (threads < 64 || threads > 256 || threads % 32 || ctas < 0 || (vw != dv && vw != dv / 2 && vw != v4))
+            return ctx->fail(LB_ERR_ARG, "register kernel: threads multiple of 32 in [64, 256]; ctas >= 0; "
+                                         "sites_per_thread the default, half or a quarter of it");
     } else {
         return ctx->fail(LB_ERR_ARG, "unknown stream-collide kernel");
     }

@@ -787,10 +787,13 @@ cudaError_t Launch<ST>::stream_collide(const SCParams& p, int kernel, int thread
     }
     int64_t grid = (ctas > 0 && ctas < p.total_tiles) ? ctas : p.total_tiles;
     if (grid < 1) return cudaSuccess;
-    if (vw == kVW<ST> / 2)
-        k_stream_collide<ST, kVW<ST> / 2><<<(unsigned)grid, threads, 0, s>>>(p);
+    constexpr int V0 = kVW<ST>, V1 = kVW<ST> / 2 > 0 ? kVW<ST> / 2 : 1, V2 = kVW<ST> / 4 > 0 ? kVW<ST> / 4 : 1;
+    if (vw == V2)
+        k_stream_collide<ST, V2><<<(unsigned)grid, threads, 0, s>>>(p);
+    else if (vw == V1)
+        k_stream_collide<ST, V1><<<(unsigned)grid, threads, 0, s>>>(p);
     else
-        k_stream_collide<ST, kVW<ST>><<<(unsigned)grid, threads, 0, s>>>(p);
+        k_stream_collide<ST, V0><<<(unsigned)grid, threads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

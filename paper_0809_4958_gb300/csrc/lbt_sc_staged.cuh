@@ -22,14 +22,14 @@ namespace lbt {
 constexpr int kStagedThreads = 512;
 constexpr int kStagedHaloBytes = 16;                           // x-shift halo on each side
 
-// Tile geometry per storage: FP64 keeps two stages of 4 KB rows (one site per
-// thread); the narrower formats run four stages of 2 KB rows so that three
-// tiles are in flight while one is computed.
+// Tile geometry: two stages of 4 KB rows.  (Four stages of 2 KB rows measured
+// slower on GB300: the cost per bulk copy and per tile grows faster than the
+// gain from the deeper pipeline.)
 template <int ST>
 struct Staged {
     using E = typename Stor<ST>::E;
-    static constexpr int kRowBytes = ST == kF64 ? 4096 : 2048;              // one population row of a tile
-    static constexpr int kStages = ST == kF64 ? 2 : 4;
+    static constexpr int kRowBytes = 4096;                                  // one population row of a tile
+    static constexpr int kStages = 2;
     static constexpr int kRowStride = kRowBytes + 2 * kStagedHaloBytes;
     static constexpr int kStageBytes = kQ * kRowStride;
     static constexpr int kSmemBytes = kStages * kStageBytes + 64;          // + mbarriers

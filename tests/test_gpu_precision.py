@@ -39,11 +39,11 @@ def cfg0_refs():
     return c, plain, emul
 
 
-@pytest.mark.parametrize("storage,bound_plain", [(F16, 2e-3), (BF16, 2e-2)])
+@pytest.mark.parametrize("storage,bound_plain", [(F16, 2e-3), (BF16, 2e-3)])
 def test_16bit_storage_against_fp64_oracle(lbt, cfg0_refs, storage, bound_plain):
-    # 32^3 box with chain, 500 steps.  binary16 meets the 2e-3 bound; bfloat16
-    # (8-bit significand) does not and is held to 2e-2 (its measured error is
-    # recorded in the design doc)
+    # 32^3 box with chain, 500 steps: both 16-bit formats stay within the
+    # 2e-3 relative L2 bound on velocity (measured: binary16 1.1e-4,
+    # bfloat16 8.5e-4)
     c, plain, emul = cfg0_refs
     r = GpuRunner(lbt, torch, [c], storage)
     r.step(c.nsteps)
