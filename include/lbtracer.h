@@ -83,7 +83,7 @@ extern "C" {
 /* ---- time interpolation of the coarse boundary samples ---- */
 #define LB_TIME_LINEAR 0    /* linear between samples j and j+1 (the paper's form) */
 #define LB_TIME_HERMITE 1   /* cubic Hermite, Catmull-Rom tangents, one-sided on the first interval */
-#define LB_TIME_MLP 2       /* Hermite plus a learned residual (reserved, not built) */
+#define LB_TIME_MLP 2       /* Hermite plus the residual of the learned upsampler (lb_mlp_bind), K = 8 or 16 */
 
 /* ---- fields for lb_read_fields ---- */
 #define LB_FIELD_RHO 0      /* real [E^3] density */
@@ -281,6 +281,58 @@ int32_t lb_synth_faces(const double* kvec, const double* amp, const double* omeg
 int32_t lb_synth_volume(const double* kvec, const double* amp, const double* omega, const double* phi,
                         int32_t M, int32_t E, double t, int32_t out_dtype, void* out, void* workspace,
                         void* stream);
+
+/*
+ * Learned boundary upsampler (boxes with LB_TIME_MLP).  The paper
+ * interpolates the DNS boundary linearly in time (Sec. 3); this added form
+ * predicts, per face site and coarse interval j, the residual of the boundary
+ * velocity over the cubic Hermite interpolant at the K substeps from the
+ * samples j-1 (clamped to 0), j, j+1, j+2 and the in-face differences of
+ * samples j and j+1 (24 features divided by u_max, zero-padded to 32).
+ * Network 32 -> 128 -> 128 -> 3K with ReLU; bf16 weights and activations on
+ * the tensor cores, f32 accumulation; output row r = (f E + q) E + p holds
+ * residual / u_max at [3 (s-1) + c].
+ *
+ * Inference parameters (device, lb_mlp_param_bytes(K) bytes, 256-byte
+ * aligned sections): bf16 W1t [128][32], W2t [128][128], W3t [3K][128]
+ * (output-major), then f32 b1 [128], b2 [128], b3 [3K].
+ * Master parameters (f32, input-major like the CPU oracle): W1 [32][128],
+ * b1 [128], W2 [128][128], b2 [128], W3 [128][3K], b3 [3K].
+ *
+ * lb_mlp_bind: boxes with LB_TIME_MLP use these parameters (borrowed until
+ *   the context is destroyed or rebound); u_max scales features and output.
+ *   At every interval start lb_step first builds the features of those boxes
+ *   from the ring and runs the network.
+ * lb_mlp_features: feature matrix bf16 [6 E^2][32] of one face set from four
+ *   samples [6][3][E][E] (real_dtype LB_STORE_F64 or LB_STORE_F32, device).
+ * lb_mlp_targets: training targets f32 [6 E^2][3K]: (fine - Hermite) / u_max
+ *   with fine [K + 1][6][3][E][E] the boundary at t = jK .. jK + K;
+ *   first_interval = 1 uses the one-sided tangent of interval 0.
+ * lb_mlp_forward: Y f32 [rows][3K] from features X bf16 [rows][32].
+ * Training (workspace of lb_mlp_train_bytes(K, batch_rows) bytes, device,
+ * caller-owned): lb_mlp_train_init copies master parameters (host or device)
+ * and clears the Adam moments; lb_mlp_grad runs forward and backward on
+ * rows <= batch_rows of (X, T) and writes the f32 gradient in master layout
+ * and the MSE loss (device pointers, either may be NULL); lb_mlp_train_step
+ * does the same and applies one Adam step (lr, step t >= 1, betas 0.9 and
+ * 0.999, eps 1e-8); lb_mlp_export writes the inference parameters.
+ * All enqueue on `stream` without synchronising.
+ */
+size_t lb_mlp_param_bytes(int32_t K);
+int32_t lb_mlp_bind(lb_ctx* ctx, const void* params, double u_max);
+size_t lb_mlp_train_bytes(int32_t K, int64_t batch_rows);
+int32_t lb_mlp_train_init(void* ws, int32_t K, int64_t batch_rows, const float* master, void* stream);
+int32_t lb_mlp_features(const void* s_prev, const void* s0, const void* s1, const void* s2, int32_t real_dtype,
+                        int32_t E, double u_max, void* X, void* stream);
+int32_t lb_mlp_targets(const void* s_prev, const void* s0, const void* s1, const void* s2, const void* fine,
+                       int32_t real_dtype, int32_t E, int32_t K, int32_t first_interval, double u_max, float* T,
+                       void* stream);
+int32_t lb_mlp_forward(const void* params, int32_t K, const void* X, int64_t rows, float* Y, void* stream);
+int32_t lb_mlp_grad(void* ws, int32_t K, int64_t batch_rows, const void* X, const float* T, int64_t rows,
+                    float* grad_out, double* loss_out, void* stream);
+int32_t lb_mlp_train_step(void* ws, int32_t K, int64_t batch_rows, const void* X, const float* T, int64_t rows,
+                          float lr, int64_t t, double* loss_out, void* stream);
+int32_t lb_mlp_export(const void* ws, int32_t K, int64_t batch_rows, void* params, void* stream);
 
 /*
  * lb_population_sums_noalloc -- FP64 sums of one box's population buffer,

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "lbt_internal.h"
+#include "lbt_mlp.h"
 
 using namespace lbt;
 
@@ -55,10 +56,22 @@ int validate_boxes(const lb_box_desc* boxes, int nboxes, int storage, std::strin
                 return LB_ERR_ARG;
             }
         }
-        if (d.time_interp != LB_TIME_LINEAR && d.time_interp != LB_TIME_HERMITE) {
+        if (d.time_interp != LB_TIME_LINEAR && d.time_interp != LB_TIME_HERMITE && d.time_interp != LB_TIME_MLP) {
             snprintf(buf, sizeof buf, "box %d: time_interp %d not available", b, d.time_interp);
             why = buf;
             return LB_ERR_ARG;
+        }
+        if (d.time_interp == LB_TIME_MLP) {
+            if (d.K != 8 && d.K != 16) {
+                snprintf(buf, sizeof buf, "box %d: the upsampler supports K = 8 or 16 (got %d)", b, d.K);
+                why = buf;
+                return LB_ERR_ARG;
+            }
+            for (int b2 = 0; b2 < b; b2++)
+                if (boxes[b2].time_interp == LB_TIME_MLP && boxes[b2].K != d.K) {
+                    why = "all upsampler boxes of a context share one K";
+                    return LB_ERR_ARG;
+                }
         }
         if (d.K < 1 || d.nbeads < 0 || d.nbeads > kMaxBeads || !(d.rho_b > 0.0)) {
             snprintf(buf, sizeof buf, "box %d: need K >= 1, 0 <= nbeads <= %d, rho_b > 0", b, kMaxBeads);
@@ -116,6 +129,22 @@ Layout plan_layout(const lb_box_desc* boxes, int nboxes, int storage, int ring_s
     off = align_up(off + sizeof(int64_t));
     L.tile_counter = off;
     off = align_up(off + sizeof(int64_t));
+    // upsampler: feature-set table, bf16 features and f32 outputs of all its boxes
+    L.mlp_rows = 0;
+    L.mlp_boxes = 0;
+    L.mlp_K = 0;
+    for (int b = 0; b < nboxes; b++)
+        if (boxes[b].time_interp == LB_TIME_MLP) {
+            L.mlp_rows += 6LL * boxes[b].E * boxes[b].E;
+            L.mlp_boxes++;
+            L.mlp_K = boxes[b].K;
+        }
+    L.mlp_sets = off;
+    off = align_up(off + sizeof(MlpFeatureSet) * L.mlp_boxes);
+    L.mlp_x = off;
+    off = align_up(off + 2 * (size_t)kMlpIn * L.mlp_rows);
+    L.mlp_y = off;
+    off = align_up(off + 4 * (size_t)3 * L.mlp_K * L.mlp_rows);
     L.total = off;
     return L;
 }
@@ -153,6 +182,9 @@ struct lb_ctx {
     int graph_steps = 0;
     bool graph_parity = true;
     bool profiling = false;
+    const void* mlp_params = nullptr;  // bound upsampler parameters (device, caller-owned)
+    double mlp_umax = 0.0;
+    int64_t graph_step0 = 0;
     std::vector<cudaEvent_t> prof_ev;  // pairs around stream-collide launches
     size_t prof_used = 0;
     std::string err;
@@ -243,12 +275,24 @@ int check_samples(lb_ctx* ctx, int64_t n0, int64_t nsteps)
     return LB_OK;
 }
 
-// Enqueue one step n -> n+1 for every box; swaps the buffers.
-int enqueue_step(lb_ctx* ctx)
+// Enqueue one step n -> n+1 for every box; swaps the buffers.  At the start
+// of a coarse interval the upsampler boxes first get their residuals.
+int enqueue_step(lb_ctx* ctx, int64_t n)
 {
     const int nch = (int)ctx->chains.size();
     void* A = ctx->curA();
     void* B = ctx->curB();
+    if (ctx->L.mlp_boxes > 0 && n % ctx->L.mlp_K == 0) {
+        const size_t rb = real_bytes(ctx->storage);
+        MlpFeatureSet* sets = ctx->at<MlpFeatureSet>(ctx->L.mlp_sets);
+        CK(mlp_sets_from_ring(sets, ctx->L.mlp_boxes, ctx->at<BoxDev>(ctx->L.boxes), ctx->arena + ctx->L.ring,
+                              (int64_t)(ctx->L.ring_slot_elems * rb), ctx->L.ring_slots, (int)rb,
+                              ctx->at<int64_t>(ctx->L.step), ctx->stream));
+        CK(mlp_features(sets, ctx->L.mlp_boxes, ctx->L.mlp_rows, ctx->mlp_umax, ctx->storage == kF64,
+                        ctx->arena + ctx->L.mlp_x, ctx->stream));
+        CK(mlp_forward(ctx->arena + ctx->L.mlp_x, ctx->L.mlp_rows, ctx->mlp_params, ctx->L.mlp_K,
+                       ctx->at<float>(ctx->L.mlp_y), nullptr, nullptr, ctx->stream));
+    }
     if (nch > 0) {
         CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
         CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
@@ -270,6 +314,9 @@ int enqueue_step(lb_ctx* ctx)
     sp.ring = ctx->arena + ctx->L.ring;
     sp.ring_slot_elems = (int64_t)ctx->L.ring_slot_elems;
     sp.ring_slots = ctx->L.ring_slots;
+    sp.mlp_y = ctx->at<float>(ctx->L.mlp_y);
+    sp.mlp_nout = 3 * ctx->L.mlp_K;
+    sp.mlp_umax = (float)ctx->mlp_umax;
     sp.boxes = ctx->at<BoxDev>(ctx->L.boxes);
     sp.tile_prefix = ctx->at<int64_t>(ctx->L.tile_prefix);
     sp.nboxes = ctx->nboxes;
@@ -410,7 +457,8 @@ int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int
     }
     // box and chain tables
     size_t pop = 0, ring = 0;
-    int64_t beads = 0;
+    int64_t beads = 0, mlp_rows = 0;
+    std::vector<MlpFeatureSet> mlp_sets;
     for (int b = 0; b < nboxes; b++) {
         const lb_box_desc& d = boxes[b];
         BoxDev bd{};
@@ -420,6 +468,16 @@ int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int
         bd.ring_off = (int64_t)ring;
         bd.E = d.E;
         bd.div_magic = ((1ull << 40) + (uint64_t)d.E - 1) / (uint64_t)d.E;
+        bd.mlp_row = -1;
+        if (d.time_interp == LB_TIME_MLP) {
+            MlpFeatureSet fs{};
+            fs.row_off = mlp_rows;
+            fs.E = d.E;
+            fs.box = b;
+            bd.mlp_row = mlp_rows;
+            mlp_sets.push_back(fs);
+            mlp_rows += 6LL * d.E * d.E;
+        }
         bd.per_mask = (d.face_mode[0] == LB_FACE_PERIODIC ? 1 : 0) | (d.face_mode[2] == LB_FACE_PERIODIC ? 2 : 0) |
                       (d.face_mode[4] == LB_FACE_PERIODIC ? 4 : 0);
         bd.time_interp = d.time_interp;
@@ -453,6 +511,9 @@ int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int
                             cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess && !ctx->chains.empty())
         e = cudaMemcpyAsync(ctx->at<ChainDev>(L.chains), ctx->chains.data(), sizeof(ChainDev) * ctx->chains.size(),
+                            cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && !mlp_sets.empty())
+        e = cudaMemcpyAsync(ctx->at<MlpFeatureSet>(L.mlp_sets), mlp_sets.data(), sizeof(MlpFeatureSet) * mlp_sets.size(),
                             cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
@@ -602,8 +663,10 @@ int32_t lb_step(lb_ctx* ctx, int32_t nsteps)
     if (nsteps == 0) return LB_OK;
     int st = check_samples(ctx, ctx->step, nsteps);
     if (st) return st;
+    if (ctx->L.mlp_boxes > 0 && !ctx->mlp_params)
+        return ctx->fail(LB_ERR_STATE, "upsampler boxes need parameters (lb_mlp_bind) before stepping");
     for (int k = 0; k < nsteps; k++) {
-        st = enqueue_step(ctx);
+        st = enqueue_step(ctx, ctx->step);
         if (st) return st;
         ctx->step++;
     }
@@ -617,10 +680,15 @@ int32_t lb_graph_capture(lb_ctx* ctx, int32_t nsteps)
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;
     }
+    if (ctx->L.mlp_boxes > 0) {
+        if (!ctx->mlp_params) return ctx->fail(LB_ERR_STATE, "upsampler boxes need parameters (lb_mlp_bind)");
+        if (nsteps % ctx->L.mlp_K || ctx->step % ctx->L.mlp_K)
+            return ctx->fail(LB_ERR_ARG, "with upsampler boxes a graph covers whole coarse intervals from an interval start");
+    }
     const bool parity = ctx->a_is_pop_a;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     int st = LB_OK;
-    for (int k = 0; k < nsteps && st == LB_OK; k++) st = enqueue_step(ctx);
+    for (int k = 0; k < nsteps && st == LB_OK; k++) st = enqueue_step(ctx, ctx->step + k);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
     ctx->a_is_pop_a = parity;
@@ -634,6 +702,7 @@ int32_t lb_graph_capture(lb_ctx* ctx, int32_t nsteps)
     if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaGraphInstantiate");
     ctx->graph_steps = nsteps;
     ctx->graph_parity = parity;
+    ctx->graph_step0 = ctx->step;
     return LB_OK;
 }
 
@@ -641,6 +710,8 @@ int32_t lb_graph_launch(lb_ctx* ctx)
 {
     if (!ctx || !ctx->graph) return ctx ? ctx->fail(LB_ERR_STATE, "no captured graph") : LB_ERR_ARG;
     if (ctx->a_is_pop_a != ctx->graph_parity) return ctx->fail(LB_ERR_STATE, "buffer parity differs from capture");
+    if (ctx->L.mlp_boxes > 0 && (ctx->step - ctx->graph_step0) % ctx->L.mlp_K)
+        return ctx->fail(LB_ERR_STATE, "graph with upsampler boxes launched away from an interval start");
     int st = check_samples(ctx, ctx->step, ctx->graph_steps);
     if (st) return st;
     CK(cudaGraphLaunch(ctx->graph, ctx->stream));
@@ -832,6 +903,145 @@ int32_t lb_synth_volume(const double* kvec, const double* amp, const double* ome
         return e == cudaErrorInvalidValue ? LB_ERR_ARG : LB_ERR_CUDA;
     }
     return LB_OK;
+}
+
+size_t lb_mlp_param_bytes(int32_t K) { return (K == 8 || K == 16) ? mlp_layout(K).bytes : 0; }
+
+int32_t lb_mlp_bind(lb_ctx* ctx, const void* params, double u_max)
+{
+    if (!ctx || !params || !(u_max > 0)) return ctx ? ctx->fail(LB_ERR_ARG, "lb_mlp_bind: null parameters or u_max <= 0") : LB_ERR_ARG;
+    if (ctx->L.mlp_boxes == 0) return ctx->fail(LB_ERR_ARG, "no box of this context uses the upsampler");
+    ctx->mlp_params = params;
+    ctx->mlp_umax = u_max;
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    return LB_OK;
+}
+
+size_t lb_mlp_train_bytes(int32_t K, int64_t batch_rows)
+{
+    if ((K != 8 && K != 16) || batch_rows < 1) return 0;
+    return mlp_train_layout(K, batch_rows).bytes;
+}
+
+static int mlp_check(int32_t K, int64_t batch, const char* who)
+{
+    if ((K != 8 && K != 16) || batch < 1) {
+        g_last_error = std::string(who) + ": K must be 8 or 16 and batch_rows >= 1";
+        return LB_ERR_ARG;
+    }
+    return LB_OK;
+}
+
+static int cuda_status(cudaError_t e, const char* who)
+{
+    if (e == cudaSuccess) return LB_OK;
+    g_last_error = std::string(who) + ": " + cudaGetErrorString(e);
+    return LB_ERR_CUDA;
+}
+
+int32_t lb_mlp_train_init(void* ws, int32_t K, int64_t batch_rows, const float* master, void* stream)
+{
+    if (int st = mlp_check(K, batch_rows, "lb_mlp_train_init")) return st;
+    if (!ws || !master) return LB_ERR_ARG;
+    const MlpTrain W = mlp_train_layout(K, batch_rows);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    float* f = reinterpret_cast<float*>(ws);
+    cudaError_t e = cudaMemcpyAsync(f + W.master, master, sizeof(float) * W.L.nmaster, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f + W.m, 0, sizeof(float) * W.L.nmaster, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f + W.v, 0, sizeof(float) * W.L.nmaster, s);
+    if (e == cudaSuccess) e = mlp_export(f + W.master, K, reinterpret_cast<unsigned char*>(ws) + W.params_byte, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the master copy may come from pageable host memory
+    return cuda_status(e, "lb_mlp_train_init");
+}
+
+int32_t lb_mlp_features(const void* s_prev, const void* s0, const void* s1, const void* s2, int32_t real_dtype,
+                        int32_t E, double u_max, void* X, void* stream)
+{
+    if (!s_prev || !s0 || !s1 || !s2 || !X || E < 2 || !(u_max > 0) ||
+        (real_dtype != LB_STORE_F64 && real_dtype != LB_STORE_F32)) {
+        g_last_error = "lb_mlp_features: bad argument";
+        return LB_ERR_ARG;
+    }
+    MlpFeatureSet fs{};
+    fs.row_off = 0;
+    fs.smp[0] = s_prev;
+    fs.smp[1] = s0;
+    fs.smp[2] = s1;
+    fs.smp[3] = s2;
+    fs.E = E;
+    return cuda_status(mlp_features_one(fs, u_max, real_dtype == LB_STORE_F64, X, reinterpret_cast<cudaStream_t>(stream)),
+                       "lb_mlp_features");
+}
+
+int32_t lb_mlp_targets(const void* s_prev, const void* s0, const void* s1, const void* s2, const void* fine,
+                       int32_t real_dtype, int32_t E, int32_t K, int32_t first_interval, double u_max, float* T,
+                       void* stream)
+{
+    if (!s_prev || !s0 || !s1 || !s2 || !fine || !T || E < 2 || K < 1 || !(u_max > 0) ||
+        (real_dtype != LB_STORE_F64 && real_dtype != LB_STORE_F32)) {
+        g_last_error = "lb_mlp_targets: bad argument";
+        return LB_ERR_ARG;
+    }
+    const void* smp[4] = {s_prev, s0, s1, s2};
+    return cuda_status(mlp_targets(smp, fine, E, K, first_interval, u_max, real_dtype == LB_STORE_F64, T,
+                                   reinterpret_cast<cudaStream_t>(stream)),
+                       "lb_mlp_targets");
+}
+
+int32_t lb_mlp_forward(const void* params, int32_t K, const void* X, int64_t rows, float* Y, void* stream)
+{
+    if (int st = mlp_check(K, 1, "lb_mlp_forward")) return st;
+    if (!params || !X || !Y || rows < 0) return LB_ERR_ARG;
+    return cuda_status(mlp_forward(X, rows, params, K, Y, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream)),
+                       "lb_mlp_forward");
+}
+
+int32_t lb_mlp_grad(void* ws, int32_t K, int64_t batch_rows, const void* X, const float* T, int64_t rows,
+                    float* grad_out, double* loss_out, void* stream)
+{
+    if (int st = mlp_check(K, batch_rows, "lb_mlp_grad")) return st;
+    if (!ws || !X || !T || rows < 1 || rows > batch_rows) {
+        g_last_error = "lb_mlp_grad: null pointer or rows outside [1, batch_rows]";
+        return LB_ERR_ARG;
+    }
+    const MlpTrain W = mlp_train_layout(K, batch_rows);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = mlp_grad(reinterpret_cast<unsigned char*>(ws), W, X, T, rows, s);
+    float* f = reinterpret_cast<float*>(ws);
+    if (e == cudaSuccess && grad_out)
+        e = cudaMemcpyAsync(grad_out, f + W.grad, sizeof(float) * W.L.nmaster, cudaMemcpyDefault, s);
+    if (e == cudaSuccess && loss_out) e = cudaMemcpyAsync(loss_out, f + W.loss, sizeof(double), cudaMemcpyDefault, s);
+    return cuda_status(e, "lb_mlp_grad");
+}
+
+int32_t lb_mlp_train_step(void* ws, int32_t K, int64_t batch_rows, const void* X, const float* T, int64_t rows,
+                          float lr, int64_t t, double* loss_out, void* stream)
+{
+    if (int st = mlp_check(K, batch_rows, "lb_mlp_train_step")) return st;
+    if (!ws || !X || !T || rows < 1 || rows > batch_rows || t < 1 || !(lr > 0)) {
+        g_last_error = "lb_mlp_train_step: bad argument";
+        return LB_ERR_ARG;
+    }
+    const MlpTrain W = mlp_train_layout(K, batch_rows);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = mlp_grad(reinterpret_cast<unsigned char*>(ws), W, X, T, rows, s);
+    if (e == cudaSuccess) e = mlp_adam(reinterpret_cast<unsigned char*>(ws), W, lr, t, s);
+    if (e == cudaSuccess && loss_out)
+        e = cudaMemcpyAsync(loss_out, reinterpret_cast<float*>(ws) + W.loss, sizeof(double), cudaMemcpyDefault, s);
+    return cuda_status(e, "lb_mlp_train_step");
+}
+
+int32_t lb_mlp_export(const void* ws, int32_t K, int64_t batch_rows, void* params, void* stream)
+{
+    if (int st = mlp_check(K, batch_rows, "lb_mlp_export")) return st;
+    if (!ws || !params) return LB_ERR_ARG;
+    const MlpTrain W = mlp_train_layout(K, batch_rows);
+    return cuda_status(cudaMemcpyAsync(params, reinterpret_cast<const char*>(ws) + W.params_byte, W.L.bytes,
+                                       cudaMemcpyDeviceToDevice, reinterpret_cast<cudaStream_t>(stream)),
+                       "lb_mlp_export");
 }
 
 }  // extern "C"

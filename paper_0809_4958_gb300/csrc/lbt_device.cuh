@@ -189,6 +189,18 @@ __device__ __forceinline__ TimeWeights<R> time_weights(int64_t n, int K, int mod
     return tw;
 }
 
+// Learned residual of the boundary velocity (upsampler boxes): output row of
+// the face site, substep s = n + 1 - jK.
+template <class R>
+__device__ __forceinline__ void add_mlp_residual(const SCParams& p, const BoxDev& bd, int64_t n, int f, int pp, int qq,
+                                                 R ub[3])
+{
+    if (bd.mlp_row < 0) return;
+    const int s = (int)(n + 1 - (n / bd.K) * bd.K);
+    const float* y = p.mlp_y + (bd.mlp_row + ((int64_t)f * bd.E + qq) * bd.E + pp) * p.mlp_nout + 3 * (s - 1);
+    for (int c = 0; c < 3; c++) ub[c] += (R)(p.mlp_umax * y[c]);
+}
+
 // Owning face of a boundary site (first velocity face containing it in the
 // order x-, x+, y-, y+, z-, z+) and its in-face coordinates.
 __device__ __forceinline__ int owning_face(int x, int y, int z, int E, int per, int& p, int& q)

@@ -27,6 +27,7 @@ struct BoxDev {
     int32_t chain;      // index into the chain table, -1 if none
     int32_t has_accel;
     uint64_t div_magic; // ceil(2^40 / E): site / E = (site * div_magic) >> 40
+    int64_t mlp_row;    // first row of the box in the upsampler output, -1 if the box does not use it
     double tau;
     double rho_b;
     double accel[3];
@@ -57,12 +58,15 @@ struct ForceEntry {
 // Arena layout (byte offsets), computed by plan().
 struct Layout {
     size_t boxes, tile_prefix, chains, pop_a, pop_b, ring, pos, vel, forces, cons_partial, cons_out,
-        status, step, tile_counter, total;
+        status, step, tile_counter, mlp_sets, mlp_x, mlp_y, total;
     size_t pop_bytes;        // bytes of one population buffer
     size_t ring_slot_elems;  // real elements per ring slot
     int32_t ring_slots;      // slots in the ring of coarse samples
     int64_t cons_chunks;     // max conservation chunks per box
     int64_t total_beads;
+    int64_t mlp_rows;        // face rows of all boxes that use the upsampler
+    int32_t mlp_boxes;
+    int32_t mlp_K;
 };
 
 enum Storage { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
@@ -74,6 +78,9 @@ struct SCParams {
     const void* ring;             // real elements
     int64_t ring_slot_elems;
     int32_t ring_slots;
+    const float* mlp_y;           // upsampler output [rows][mlp_nout] of the current interval
+    int32_t mlp_nout;
+    float mlp_umax;
     const BoxDev* boxes;
     const int64_t* tile_prefix;   // [nboxes + 1] first tile of each box for the current block size
     int32_t nboxes;

@@ -236,6 +236,7 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
                 const int f = owning_face(xs_[k], ys_[k], zs_[k], Ei, per, pp, qq);
                 R ub[3];
                 boundary_velocity<R>(ring, p.ring_slot_elems, bd.ring_off, Ei, f, pp, qq, tw, ub);
+                add_mlp_residual<R>(p, bd, n, f, pp, qq, ub);
                 drho[k] = (A)bd.rho_b - A(1);
                 ux[k] = (A)ub[0];
                 uy[k] = (A)ub[1];

@@ -30,7 +30,9 @@ ERROR_NAMES = {0: "LB_OK", 1: "LB_ERR_ARG", 2: "LB_ERR_CUDA", 3: "LB_ERR_FENE", 
 EXPORTS = ["lb_plan", "lb_create", "lb_destroy", "lb_init", "lb_set_boundary", "chain_couple", "lb_step",
            "lb_graph_capture", "lb_graph_launch", "lb_read_fields", "lb_conservation", "lb_sync", "lb_status",
            "lb_current_step", "lb_set_launch", "lb_profile", "lb_profile_read", "lb_last_error", "lb_synth_workspace_bytes", "lb_synth_faces",
-           "lb_synth_volume", "lb_population_sums_noalloc"]
+           "lb_synth_volume", "lb_population_sums_noalloc", "lb_mlp_param_bytes", "lb_mlp_bind", "lb_mlp_train_bytes",
+           "lb_mlp_train_init", "lb_mlp_features", "lb_mlp_targets", "lb_mlp_forward", "lb_mlp_grad",
+           "lb_mlp_train_step", "lb_mlp_export"]
 
 
 class lb_box_desc(ctypes.Structure):
@@ -92,6 +94,16 @@ def load(path: str | None = None, build_if_missing: bool = True):
         "lb_synth_faces": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _i32, _i64, _i64, _i32, _vp, _vp, _vp]),
         "lb_synth_volume": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _f64, _i32, _vp, _vp, _vp]),
         "lb_population_sums_noalloc": (_i32, [_vp, _i32, _i32, _vp, _vp]),
+        "lb_mlp_param_bytes": (_sz, [_i32]),
+        "lb_mlp_bind": (_i32, [_vp, _vp, _f64]),
+        "lb_mlp_train_bytes": (_sz, [_i32, _i64]),
+        "lb_mlp_train_init": (_i32, [_vp, _i32, _i64, _vp, _vp]),
+        "lb_mlp_features": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _f64, _vp, _vp]),
+        "lb_mlp_targets": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32, _i32, _f64, _vp, _vp]),
+        "lb_mlp_forward": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp]),
+        "lb_mlp_grad": (_i32, [_vp, _i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp]),
+        "lb_mlp_train_step": (_i32, [_vp, _i32, _i64, _vp, _vp, _i64, ctypes.c_float, _i64, _vp, _vp]),
+        "lb_mlp_export": (_i32, [_vp, _i32, _i64, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -234,6 +246,9 @@ class Tracers:
         _check(self.lib.lb_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n)), self.ctx)
         return float(ms.value), int(n.value)
 
+    def lb_mlp_bind(self, params, u_max):
+        _check(self.lib.lb_mlp_bind(self.ctx, _ptr(params), float(u_max)), self.ctx)
+
     def lb_destroy(self):
         if self.ctx:
             self.lib.lb_destroy(self.ctx)
@@ -279,6 +294,76 @@ def lb_population_sums_noalloc(populations, storage, E, out, stream=None):
     torch = _torch()
     stream = stream or torch.cuda.current_stream()
     _check(load().lb_population_sums_noalloc(_ptr(populations), int(storage), int(E), _ptr(out), stream.cuda_stream))
+
+
+class Upsampler:
+    """Training and inference of the learned boundary upsampler on the GPU
+    (thin wrapper of the lb_mlp_* calls; torch tensors hold the buffers)."""
+
+    def __init__(self, K=16, batch_rows=16384, master=None, seed=0):
+        torch = _torch()
+        lib = load()
+        self.torch, self.lib, self.K, self.batch = torch, lib, int(K), int(batch_rows)
+        self.ws = torch.zeros(int(lib.lb_mlp_train_bytes(self.K, self.batch)), dtype=torch.uint8, device="cuda")
+        self.params = torch.zeros(int(lib.lb_mlp_param_bytes(self.K)), dtype=torch.uint8, device="cuda")
+        if master is None:
+            raise ValueError("master parameters (float32, master layout) are required")
+        m = torch.as_tensor(np.ascontiguousarray(master, np.float32)).to("cuda")
+        self.stream = torch.cuda.current_stream()
+        _check(lib.lb_mlp_train_init(self.ws.data_ptr(), self.K, self.batch, m.data_ptr(), self.stream.cuda_stream))
+        self.t = 0
+        self.loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def nmaster(self):
+        return 32 * 128 + 128 + 128 * 128 + 128 + 128 * 3 * self.K + 3 * self.K
+
+    def grad(self, X, T, rows=None):
+        rows = X.shape[0] if rows is None else rows
+        g = self.torch.zeros(self.nmaster(), dtype=self.torch.float32, device="cuda")
+        _check(self.lib.lb_mlp_grad(self.ws.data_ptr(), self.K, self.batch, X.data_ptr(), T.data_ptr(), int(rows),
+                                    g.data_ptr(), self.loss.data_ptr(), self.stream.cuda_stream))
+        return g, self.loss
+
+    def step(self, X, T, lr, rows=None):
+        rows = X.shape[0] if rows is None else rows
+        self.t += 1
+        _check(self.lib.lb_mlp_train_step(self.ws.data_ptr(), self.K, self.batch, X.data_ptr(), T.data_ptr(),
+                                          int(rows), float(lr), self.t, self.loss.data_ptr(), self.stream.cuda_stream))
+        return self.loss
+
+    def export(self):
+        _check(self.lib.lb_mlp_export(self.ws.data_ptr(), self.K, self.batch, self.params.data_ptr(),
+                                      self.stream.cuda_stream))
+        return self.params
+
+
+def mlp_features(s_prev, s0, s1, s2, E, u_max, out=None):
+    """bf16 features [6 E^2][32] of one face set (four [6][3][E][E] tensors)."""
+    torch = _torch()
+    X = out if out is not None else torch.empty((6 * E * E, 32), dtype=torch.bfloat16, device="cuda")
+    code = LB_STORE_F64 if s0.dtype == torch.float64 else LB_STORE_F32
+    _check(load().lb_mlp_features(s_prev.data_ptr(), s0.data_ptr(), s1.data_ptr(), s2.data_ptr(), code, int(E),
+                                  float(u_max), X.data_ptr(), torch.cuda.current_stream().cuda_stream))
+    return X
+
+
+def mlp_targets(s_prev, s0, s1, s2, fine, E, K, first_interval, u_max, out=None):
+    """f32 targets [6 E^2][3K]; fine [K+1][6][3][E][E] from t = jK."""
+    torch = _torch()
+    T = out if out is not None else torch.empty((6 * E * E, 3 * K), dtype=torch.float32, device="cuda")
+    code = LB_STORE_F64 if s0.dtype == torch.float64 else LB_STORE_F32
+    _check(load().lb_mlp_targets(s_prev.data_ptr(), s0.data_ptr(), s1.data_ptr(), s2.data_ptr(), fine.data_ptr(),
+                                 code, int(E), int(K), int(first_interval), float(u_max), T.data_ptr(),
+                                 torch.cuda.current_stream().cuda_stream))
+    return T
+
+
+def mlp_forward(params, K, X):
+    torch = _torch()
+    Y = torch.empty((X.shape[0], 3 * K), dtype=torch.float32, device="cuda")
+    _check(load().lb_mlp_forward(params.data_ptr(), int(K), X.data_ptr(), int(X.shape[0]), Y.data_ptr(),
+                                 torch.cuda.current_stream().cuda_stream))
+    return Y
 
 
 def modes_to_device(modes, device="cuda"):
