@@ -52,8 +52,9 @@ def parse():
     p.add_argument("--vw", type=int, default=0, help="sites per thread in stream-collide (0 = default)")
     p.add_argument("--kernel", default="staged", choices=["staged", "register"],
                    help="stream-collide kernel: TMA-staged pipeline or register tiles")
-    p.add_argument("--config", default="single", choices=["single", "batch", "precision"],
-                   help="single 128^3 box (default), 512 uneven boxes under a CUDA graph, or 256^3 16-bit storage")
+    p.add_argument("--config", default="single", choices=["single", "batch", "precision", "mlp"],
+                   help="single 128^3 box (default), 512 uneven boxes under a CUDA graph, 256^3 16-bit storage, "
+                        "or 256 boxes of 64^3 with the learned boundary upsampler (K = 16)")
     return p.parse_args()
 
 
@@ -230,7 +231,7 @@ def run_reference(args):
 
 def main():
     args = parse()
-    defaults = {"single": (10000, 50), "batch": (1008, 112), "precision": (5000, 20)}[args.config]
+    defaults = {"single": (10000, 50), "batch": (1008, 112), "precision": (5000, 20), "mlp": (1024, 64)}[args.config]
     if args.steps is None:
         args.steps = defaults[0]
     if args.warmup is None:
@@ -243,6 +244,9 @@ def main():
         return
     if args.config == "precision":
         run_precision(args)
+        return
+    if args.config == "mlp":
+        run_mlp(args)
         return
     import torch
     import torch.distributed as dist
@@ -615,6 +619,142 @@ def run_precision(args):
                          "frac": results["f16"]["hbm_frac"], "traffic": None, "kernel": "stream-collide",
                          "peak_kind": peak_kind},
             "e2e": None, "gpu_launches": args.steps * 2}
+    print(json.dumps(line), flush=True)
+
+
+MLP = dict(nboxes=256, E=64, tau=0.8, M=256, k_min=1.0, k_max=32.0, K=16, u_max=0.05, train_boxes=8,
+           train_intervals=10, train_steps=1500, batch=16384, lr=2e-3, eval_boxes=4, eval_steps=256, seed=500)
+
+
+def run_mlp(args):
+    """256 boxes of 64^3 with coarse boundary samples every K = 16 steps.
+    The upsampler is trained on the GPU on every-step boundary data of
+    training seeds, its gain is measured on held-out boxes (interior velocity
+    error against the run that sees the boundary every step, for linear,
+    Hermite and Hermite + learned residual), and the throughput of all boxes
+    is timed with the network in the step (and with Hermite alone)."""
+    import torch
+
+    from paper_0809_4958_gb300 import inputs, lbtracer as lbt
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    w = MLP
+    E, K = w["E"], w["K"]
+    # ---- training data: every-step boundary of the training boxes ----
+    Xs, Ts = [], []
+    for b in range(w["train_boxes"]):
+        modes = inputs.mode_table(w["seed"] + b, w["M"], w["k_min"], w["k_max"], E)
+        fine = lbt.synth_faces(modes, E, 1, 0, (w["train_intervals"] + 3) * K + 1, torch.float32)
+        coarse = fine[::K]
+        for j in range(1, w["train_intervals"] + 1):
+            Xs.append(lbt.mlp_features(coarse[j - 1], coarse[j], coarse[j + 1], coarse[j + 2], E, w["u_max"]))
+            Ts.append(lbt.mlp_targets(coarse[j - 1], coarse[j], coarse[j + 1], coarse[j + 2],
+                                      fine[j * K:j * K + K + 1].contiguous(), E, K, 0, w["u_max"]))
+        del fine
+    X = torch.cat(Xs)
+    T = torch.cat(Ts)
+    del Xs, Ts
+    up = lbt.Upsampler(K=K, batch_rows=w["batch"], master=inputs.mlp_init(w["seed"], K))
+    gen = torch.Generator(device="cuda").manual_seed(w["seed"])
+    t0 = time.perf_counter()
+    first = None
+    for it in range(w["train_steps"]):
+        idx = torch.randint(0, X.shape[0], (w["batch"],), device="cuda", generator=gen)
+        up.step(X[idx].contiguous(), T[idx].contiguous(), w["lr"])
+        if it == 0:
+            first = up.loss.item()
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    final = up.loss.item()
+    params = up.export()
+    torch.cuda.synchronize()
+
+    def run_boxes(seeds, time_interp, Kb, nsteps, timed=False, graph=True):
+        descs = [lbt.box_desc(E, w["tau"], time_interp=time_interp, K=Kb) for _ in seeds]
+        G = K if graph else 1
+        stream = torch.cuda.Stream()
+        tr = lbt.Tracers(descs, lbt.LB_STORE_F32, stream=stream, ring_slots=G // Kb + 4 if Kb else 4)
+        fs = 18 * E * E
+        nsamp = nsteps // Kb + 4
+        faces = torch.empty((nsamp, len(seeds) * fs), dtype=torch.float32, device="cuda")
+        for b, sd in enumerate(seeds):
+            modes = inputs.mode_table(sd, w["M"], w["k_min"], w["k_max"], E)
+            faces[:, b * fs:(b + 1) * fs] = lbt.synth_faces(modes, E, Kb, 0, nsamp, torch.float32).view(nsamp, -1)
+            u0 = lbt.synth_volume(modes, E, 0.0, torch.float32)
+            torch.cuda.synchronize()
+            tr.lb_init(b, u0)
+            tr.lb_sync()
+        if time_interp == lbt.LB_TIME_MLP:
+            tr.lb_mlp_bind(params, w["u_max"])
+        pushed = [-1]
+
+        def push_until(j):
+            while pushed[0] < j:
+                pushed[0] += 1
+                tr.lb_set_boundary(lbt.LB_ALL_BOXES, pushed[0], faces[pushed[0]])
+
+        need = lambda n: n // Kb + (1 if time_interp == lbt.LB_TIME_LINEAR else 2)  # noqa: E731
+        ms = None
+        if timed:
+            warm = args.warmup // G * G
+            for n in range(warm):
+                push_until(need(n))
+                tr.lb_step(1)
+            tr.lb_graph_capture(G)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(nsteps // G):
+                push_until(need(tr.lb_current_step() + G - 1))
+                tr.lb_graph_launch()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+        else:
+            for n in range(nsteps):
+                push_until(need(n))
+                tr.lb_step(1)
+        us = []
+        if not timed:
+            for b in range(len(seeds)):
+                u = torch.empty((3, E, E, E), dtype=torch.float32, device="cuda")
+                tr.lb_read_fields(b, lbt.LB_FIELD_U, u)
+                us.append(u[:, 1:-1, 1:-1, 1:-1].double())
+        tr.close()
+        del faces
+        torch.cuda.synchronize()
+        return ms, us
+
+    # ---- gain on held-out boxes ----
+    eval_seeds = [w["seed"] + 10000 + b for b in range(w["eval_boxes"])]
+    _, u_ref = run_boxes(eval_seeds, lbt.LB_TIME_LINEAR, 1, w["eval_steps"], graph=False)
+    errs = {}
+    for name, ti in (("linear", lbt.LB_TIME_LINEAR), ("hermite", lbt.LB_TIME_HERMITE), ("mlp", lbt.LB_TIME_MLP)):
+        _, u = run_boxes(eval_seeds, ti, K, w["eval_steps"], graph=False)
+        errs[name] = float(np.mean([float(torch.linalg.norm(a - r) / torch.linalg.norm(r)) for a, r in zip(u, u_ref)]))
+    # ---- throughput of all boxes: network in the step vs Hermite alone ----
+    all_seeds = [w["seed"] + 20000 + b for b in range(w["nboxes"])]
+    steps = args.steps // K * K
+    ms_mlp, _ = run_boxes(all_seeds, lbt.LB_TIME_MLP, K, steps, timed=True)
+    ms_her, _ = run_boxes(all_seeds, lbt.LB_TIME_HERMITE, K, steps, timed=True)
+    sites = w["nboxes"] * E ** 3
+    value = sites * steps / (ms_mlp * 1e-3) / 1e6
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup // K * K,
+            "ms_per_step": ms_mlp / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%d boxes of %d^3, tau %.2f, FP32, Kolmogorov boundaries (256 modes, |k| in [1,32]) "
+                                   "sampled every K = %d steps; learned upsampler (32-128-128-48, bf16 tensor cores) "
+                                   "in the step, CUDA graph of one interval" % (w["nboxes"], E, w["tau"], K),
+                       "hermite_only_MLUPS": sites * steps / (ms_her * 1e-3) / 1e6,
+                       "interior_velocity_error_vs_every_step_boundary": errs,
+                       "eval": "%d held-out boxes, %d steps" % (w["eval_boxes"], w["eval_steps"]),
+                       "training": {"boxes": w["train_boxes"], "intervals_per_box": w["train_intervals"],
+                                    "rows": int(X.shape[0]), "adam_steps": w["train_steps"], "batch": w["batch"],
+                                    "lr": w["lr"], "loss_first": first, "loss_final": final, "seconds": train_s}},
+            "roofline": None, "e2e": None, "gpu_launches": None}
     print(json.dumps(line), flush=True)
 
 

@@ -145,6 +145,24 @@ __device__ __forceinline__ double unit_uniform(uint64_t v)
     return sqrt(3.0) * (2.0 * u01 - 1.0);
 }
 
+// The same in the precision of the bead dynamics: FP64 from the top 53 bits,
+// FP32 from the top 24 bits (exact uniform grid, scaled by sqrt 3).
+template <class T>
+__device__ __forceinline__ T unit_uniform_t(uint64_t v);
+template <>
+__device__ __forceinline__ double unit_uniform_t<double>(uint64_t v) { return unit_uniform(v); }
+template <>
+__device__ __forceinline__ float unit_uniform_t<float>(uint64_t v)
+{
+    const float u01 = (float)(uint32_t)(v >> 40) * (1.0f / 16777216.0f);  // 2^-24
+    return 1.7320508075688772f * (2.0f * u01 - 1.0f);
+}
+
+// Reciprocal: correctly rounded division in FP64, the single-rounding
+// reciprocal instruction sequence in FP32.
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+
 __device__ __forceinline__ int wrapi(int v, int E) { return v < 0 ? v + E : (v >= E ? v - E : v); }
 
 // Time-interpolation weights of the four ring samples j-1, j, j+1, j+2 for

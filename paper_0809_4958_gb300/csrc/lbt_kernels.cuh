@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     const int tid = threadIdx.x, nthr = blockDim.x;
 
     __shared__ double sR[kMaxBeads][3];      // start-of-step, then end-of-step positions
-    __shared__ double sD[kMaxBeads][3];      // start-of-step offsets inside the stencil cell
+    __shared__ MT sD[kMaxBeads][3];          // start-of-step offsets inside the stencil cell
     __shared__ int sBase[kMaxBeads][3];      // start-of-step stencil corner
     __shared__ MT sU[kMaxBeads][3];          // fluid velocity at each bead
     __shared__ MT sV[kMaxBeads][3];          // velocities
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
             sR[bb][a] = R;
             sV[bb][a] = (MT)vel[3 * bb + a];
             const double fl = floor(R);
-            sD[bb][a] = R - fl;
+            sD[bb][a] = (MT)(R - fl);
             long long i0 = (long long)fl;
             if (!((per >> a) & 1)) {
                 if (i0 < 1 || i0 + 1 > Ei - 2) sErr = LB_ERR_BEAD_OOB;
@@ -344,9 +344,10 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
         if (tid == 0) set_status(&p.status[b], sErr);
         return;
     }
-    auto weight = [&](int bb, int c) -> double {
-        const double d0 = sD[bb][0], d1 = sD[bb][1], d2 = sD[bb][2];
-        return ((c & 1) ? d0 : 1.0 - d0) * ((c & 2) ? d1 : 1.0 - d1) * ((c & 4) ? d2 : 1.0 - d2);
+    // trilinear weight of corner c of bead bb (MT precision: FP32 on the reduced paths)
+    auto weight = [&](int bb, int c) -> MT {
+        const MT d0 = sD[bb][0], d1 = sD[bb][1], d2 = sD[bb][2];
+        return ((c & 1) ? d0 : MT(1) - d0) * ((c & 2) ? d1 : MT(1) - d1) * ((c & 4) ? d2 : MT(1) - d2);
     };
 
     // 2. fluid velocity at the beads: eight threads per bead, one corner each
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     for (int base = 0; base < 8 * N; base += nthr) {
         const int e = base + tid;
         const bool act = e < 8 * N;
-        double uc[3] = {0, 0, 0};
+        MT uc[3] = {0, 0, 0};
         if (act) {
             const int bb = e >> 3, c = e & 7;
             int s[3] = {sBase[bb][0] + (c & 1), sBase[bb][1] + ((c >> 1) & 1), sBase[bb][2] + ((c >> 2) & 1)};
@@ -364,8 +365,8 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
             pull_site<ST>(Ab, n3, Ei, per, s[0], s[1], s[2], f);
             moments<A>(f, dr, j);
             const A rho = A(1) + dr;
-            const double w8 = weight(bb, c);
-            for (int a = 0; a < 3; a++) uc[a] = w8 * (double)((j[a] + A(0.5) * rho * (A)bd.accel[a]) / rho);
+            const MT w8 = weight(bb, c);
+            for (int a = 0; a < 3; a++) uc[a] = w8 * (MT)((j[a] + A(0.5) * rho * (A)bd.accel[a]) / rho);
         }
         for (int a = 0; a < 3; a++) {
             uc[a] += __shfl_xor_sync(0xffffffffu, uc[a], 1);
@@ -411,7 +412,7 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
                 const int sb = w / N, bb = w - sb * N;
                 uint64_t x[4] = {(uint64_t)n, (uint64_t)(sub + sb), (uint64_t)bb, (uint64_t)b};
                 philox4x64_10(x, ch.seed, 0);
-                for (int a = 0; a < 3; a++) sXi[(sb * N + bb) * 3 + a] = (MT)unit_uniform(x[a]);
+                for (int a = 0; a < 3; a++) sXi[(sb * N + bb) * 3 + a] = unit_uniform_t<MT>(x[a]);
             }
         }
         // has any bead moved more than half the skin since the last list?
@@ -454,7 +455,7 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
                     r2 += r[a] * r[a];
                 }
                 if (r2 >= R02) sErr = LB_ERR_FENE;
-                const MT fac = kf / (MT(1) - r2 * inv_R02);
+                const MT fac = kf * recip(MT(1) - r2 * inv_R02);
                 for (int a = 0; a < 3; a++) F[a] -= fac * r[a];
             }
             if (q == 1 && bead + 1 < N) {  // bond (bead, bead+1): opposite force on the lower bead
@@ -464,7 +465,7 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
                     r2 += r[a] * r[a];
                 }
                 if (r2 >= R02) sErr = LB_ERR_FENE;
-                const MT fac = kf / (MT(1) - r2 * inv_R02);
+                const MT fac = kf * recip(MT(1) - r2 * inv_R02);
                 for (int a = 0; a < 3; a++) F[a] += fac * r[a];
             }
             if (wca) {  // WCA: 24 eps (2 (s/r)^12 - (s/r)^6) / r^2 along R_bead - R_partner
@@ -477,7 +478,7 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
                         r2 += r[a] * r[a];
                     }
                     if (r2 < rc2) {
-                        const MT inv = MT(1) / r2;
+                        const MT inv = recip(r2);
                         const MT s2 = sig2 * inv, s6 = s2 * s2 * s2;
                         const MT fac = e24 * (MT(2) * s6 * s6 - s6) * inv;
                         for (int a = 0; a < 3; a++) F[a] += fac * r[a];
@@ -560,7 +561,7 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
         int s[3] = {sBase[bb][0] + (c & 1), sBase[bb][1] + ((c >> 1) & 1), sBase[bb][2] + ((c >> 2) & 1)};
         for (int a = 0; a < 3; a++)
             if ((per >> a) & 1) s[a] = wrapi(s[a], Ei);
-        double g[3] = {0, 0, 0};
+        MT g[3] = {0, 0, 0};
         bool dup = false;
         for (int b2 = 0; b2 < N; b2++) {
             int o[3];
@@ -573,13 +574,13 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
             }
             if (!in) continue;
             if (b2 < bb) dup = true;
-            const double w8 = weight(b2, o[0] + 2 * o[1] + 4 * o[2]);
-            for (int a = 0; a < 3; a++) g[a] += w8 * (double)sP[b2][a];
+            const MT w8 = weight(b2, o[0] + 2 * o[1] + 4 * o[2]);
+            for (int a = 0; a < 3; a++) g[a] += w8 * sP[b2][a];
         }
         ForceEntry fe;
         fe.site = dup ? -1 : (int32_t)(((int64_t)s[2] * Ei + s[1]) * Ei + s[0]);
         fe.pad = 0;
-        for (int a = 0; a < 3; a++) fe.g[a] = g[a];
+        for (int a = 0; a < 3; a++) fe.g[a] = (double)g[a];
         fl[e] = fe;
     }
 }

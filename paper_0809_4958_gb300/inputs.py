@@ -150,3 +150,17 @@ def batch_chain_lengths(seed: int, edges) -> np.ndarray:
     edges = np.asarray(edges)
     hi = np.minimum(128, 2 * edges)
     return (32 + np.floor(rng.uniform(0.0, 1.0, edges.shape[0]) * (hi - 32 + 1))).astype(np.int64)
+
+
+def mlp_init(seed: int, K: int, scale: float = 1.0) -> np.ndarray:
+    """Seeded initial weights of the learned boundary upsampler as one float32
+    vector in master layout: W1 [32][128] (rows 24..31 zero: padding inputs),
+    b1 [128], W2 [128][128], b2 [128], W3 [128][3K], b3 [3K]; He-style normal
+    draws, biases zero, the output layer scaled down by 10."""
+    rng = _rng(seed, 5)
+    W1 = rng.normal(0.0, np.sqrt(2.0 / 24), (32, 128)) * scale
+    W1[24:] = 0.0
+    W2 = rng.normal(0.0, np.sqrt(2.0 / 128), (128, 128)) * scale
+    W3 = rng.normal(0.0, np.sqrt(1.0 / 128), (128, 3 * K)) * scale * 0.1
+    return np.concatenate([W1.ravel(), np.zeros(128), W2.ravel(), np.zeros(128), W3.ravel(),
+                           np.zeros(3 * K)]).astype(np.float32)

@@ -133,8 +133,8 @@ def _dataset(lbt, seeds, E, nint):
 
 
 def train(lbt, X, T, steps, lr=2e-3, batch=8192, seed=0):
-    p = omlp.init_params(seed, K)
-    up = lbt.Upsampler(K=K, batch_rows=batch, master=master_vector(p))
+    from paper_0809_4958_gb300 import inputs
+    up = lbt.Upsampler(K=K, batch_rows=batch, master=inputs.mlp_init(seed, K))
     gen = torch.Generator(device="cuda").manual_seed(seed)
     losses = []
     for it in range(steps):
