@@ -88,20 +88,21 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for rel in ("paper_0809_4958_gb300/csrc/lbt_kernels.cuh", "paper_0809_4958_gb300/csrc/lbt_device.cuh"):
+    for rel in ("paper_0809_4958_gb300/csrc/lbt_kernels.cuh", "paper_0809_4958_gb300/csrc/lbt_device.cuh",
+                "paper_0809_4958_gb300/csrc/lbt_sc_staged.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(storage):
-    """DRAM bytes per stream-collide launch from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
+def ncu_traffic(storage, kernel):
+    """DRAM bytes per stream-collide launch of `kernel` from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        ent = d.get(storage)
+        ent = d.get("%s/%s" % (storage, kernel))
         if ent and ent.get("kernel_hash") == kernel_source_hash():
             return float(ent["bytes_per_launch_full_size"])
     except Exception:
@@ -377,6 +378,7 @@ def main():
     alg = alg_bytes_per_launch(E, s_elem, s_real)
     avg_sc = sc_ms / max(sc_n, 1)
     achieved = alg / (avg_sc * 1e-3) / 1e9
+    sc_kernel = "k_stream_collide_staged" if choice[0] == lbt.LB_KERNEL_STAGED else "k_stream_collide"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -389,8 +391,8 @@ def main():
                               "sites_per_thread": choice[3]},
                    "autotune": [[list(c), t] for c, t in table]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": ncu_traffic(args.storage),
-                     "kernel": "k_stream_collide_staged" if choice[0] == lbt.LB_KERNEL_STAGED else "k_stream_collide",
+                     "frac": achieved / peak, "traffic": ncu_traffic(args.storage, sc_kernel),
+                     "kernel": sc_kernel,
                      "avg_launch_ms": avg_sc, "alg_bytes_per_launch": alg,
                      "peak_kind": peak_kind, "launches_timed": sc_n},
         "clocks": clk,
@@ -622,8 +624,8 @@ def run_precision(args):
     print(json.dumps(line), flush=True)
 
 
-MLP = dict(nboxes=256, E=64, tau=0.8, M=256, k_min=1.0, k_max=32.0, K=16, u_max=0.05, train_boxes=8,
-           train_intervals=10, train_steps=1500, batch=16384, lr=2e-3, eval_boxes=4, eval_steps=256, seed=500)
+MLP = dict(nboxes=256, E=64, tau=0.8, M=256, k_min=1.0, k_max=32.0, K=16, u_max=0.05, train_boxes=12,
+           train_intervals=10, train_steps=3000, batch=16384, lr=2e-3, eval_boxes=4, eval_steps=256, seed=500)
 
 
 def run_mlp(args):
@@ -643,27 +645,31 @@ def run_mlp(args):
     torch.cuda.set_device(local)
     w = MLP
     E, K = w["E"], w["K"]
+    def boundary_data(seeds, nint):
+        # features and targets of intervals 0 .. nint-1 from every-step boundary data
+        Xs, Ts = [], []
+        for sd in seeds:
+            modes = inputs.mode_table(sd, w["M"], w["k_min"], w["k_max"], E)
+            fine = lbt.synth_faces(modes, E, 1, 0, (nint + 3) * K + 1, torch.float32)
+            coarse = fine[::K]
+            for j in range(0, nint):
+                jm = max(j - 1, 0)
+                Xs.append(lbt.mlp_features(coarse[jm], coarse[j], coarse[j + 1], coarse[j + 2], E, w["u_max"]))
+                Ts.append(lbt.mlp_targets(coarse[jm], coarse[j], coarse[j + 1], coarse[j + 2],
+                                          fine[j * K:j * K + K + 1].contiguous(), E, K, int(j == 0), w["u_max"]))
+            del fine
+        return torch.cat(Xs), torch.cat(Ts)
+
     # ---- training data: every-step boundary of the training boxes ----
-    Xs, Ts = [], []
-    for b in range(w["train_boxes"]):
-        modes = inputs.mode_table(w["seed"] + b, w["M"], w["k_min"], w["k_max"], E)
-        fine = lbt.synth_faces(modes, E, 1, 0, (w["train_intervals"] + 3) * K + 1, torch.float32)
-        coarse = fine[::K]
-        for j in range(1, w["train_intervals"] + 1):
-            Xs.append(lbt.mlp_features(coarse[j - 1], coarse[j], coarse[j + 1], coarse[j + 2], E, w["u_max"]))
-            Ts.append(lbt.mlp_targets(coarse[j - 1], coarse[j], coarse[j + 1], coarse[j + 2],
-                                      fine[j * K:j * K + K + 1].contiguous(), E, K, 0, w["u_max"]))
-        del fine
-    X = torch.cat(Xs)
-    T = torch.cat(Ts)
-    del Xs, Ts
+    X, T = boundary_data([w["seed"] + b for b in range(w["train_boxes"])], w["train_intervals"])
     up = lbt.Upsampler(K=K, batch_rows=w["batch"], master=inputs.mlp_init(w["seed"], K))
     gen = torch.Generator(device="cuda").manual_seed(w["seed"])
     t0 = time.perf_counter()
     first = None
     for it in range(w["train_steps"]):
         idx = torch.randint(0, X.shape[0], (w["batch"],), device="cuda", generator=gen)
-        up.step(X[idx].contiguous(), T[idx].contiguous(), w["lr"])
+        lr = w["lr"] * 0.5 * (1.0 + np.cos(np.pi * it / w["train_steps"]))  # cosine decay
+        up.step(X[idx].contiguous(), T[idx].contiguous(), lr)
         if it == 0:
             first = up.loss.item()
     torch.cuda.synchronize()
@@ -678,7 +684,8 @@ def run_mlp(args):
         stream = torch.cuda.Stream()
         tr = lbt.Tracers(descs, lbt.LB_STORE_F32, stream=stream, ring_slots=G // Kb + 4 if Kb else 4)
         fs = 18 * E * E
-        nsamp = nsteps // Kb + 4
+        warm = args.warmup // G * G if timed else 0
+        nsamp = (warm + nsteps) // Kb + 4
         faces = torch.empty((nsamp, len(seeds) * fs), dtype=torch.float32, device="cuda")
         for b, sd in enumerate(seeds):
             modes = inputs.mode_table(sd, w["M"], w["k_min"], w["k_max"], E)
@@ -699,7 +706,6 @@ def run_mlp(args):
         need = lambda n: n // Kb + (1 if time_interp == lbt.LB_TIME_LINEAR else 2)  # noqa: E731
         ms = None
         if timed:
-            warm = args.warmup // G * G
             for n in range(warm):
                 push_until(need(n))
                 tr.lb_step(1)
@@ -730,6 +736,10 @@ def run_mlp(args):
 
     # ---- gain on held-out boxes ----
     eval_seeds = [w["seed"] + 10000 + b for b in range(w["eval_boxes"])]
+    Xh, Th = boundary_data(eval_seeds, w["eval_steps"] // K)
+    Yh = lbt.mlp_forward(params, K, Xh)
+    resid_ratio = float(((Yh - Th) ** 2).mean() / (Th ** 2).mean())
+    del Xh, Th, Yh
     _, u_ref = run_boxes(eval_seeds, lbt.LB_TIME_LINEAR, 1, w["eval_steps"], graph=False)
     errs = {}
     for name, ti in (("linear", lbt.LB_TIME_LINEAR), ("hermite", lbt.LB_TIME_HERMITE), ("mlp", lbt.LB_TIME_MLP)):
@@ -750,6 +760,7 @@ def run_mlp(args):
                                    "in the step, CUDA graph of one interval" % (w["nboxes"], E, w["tau"], K),
                        "hermite_only_MLUPS": sites * steps / (ms_her * 1e-3) / 1e6,
                        "interior_velocity_error_vs_every_step_boundary": errs,
+                       "heldout_boundary_residual_mse_vs_hermite": resid_ratio,
                        "eval": "%d held-out boxes, %d steps" % (w["eval_boxes"], w["eval_steps"]),
                        "training": {"boxes": w["train_boxes"], "intervals_per_box": w["train_intervals"],
                                     "rows": int(X.shape[0]), "adam_steps": w["train_steps"], "batch": w["batch"],

@@ -291,7 +291,9 @@ int32_t lb_synth_volume(const double* kvec, const double* amp, const double* ome
  * samples j and j+1 (24 features divided by u_max, zero-padded to 32).
  * Network 32 -> 128 -> 128 -> 3K with ReLU; bf16 weights and activations on
  * the tensor cores, f32 accumulation; output row r = (f E + q) E + p holds
- * residual / u_max at [3 (s-1) + c].
+ * the residual of component c at substep s in units of u_max / 64 at
+ * [3 (s-1) + c] (the residual is a few thousandths of u_max; a finer output
+ * unit keeps the output weights at a scale Adam trains well).
  *
  * Inference parameters (device, lb_mlp_param_bytes(K) bytes, 256-byte
  * aligned sections): bf16 W1t [128][32], W2t [128][128], W3t [3K][128]
@@ -300,12 +302,13 @@ int32_t lb_synth_volume(const double* kvec, const double* amp, const double* ome
  * b1 [128], W2 [128][128], b2 [128], W3 [128][3K], b3 [3K].
  *
  * lb_mlp_bind: boxes with LB_TIME_MLP use these parameters (borrowed until
- *   the context is destroyed or rebound); u_max scales features and output.
+ *   the context is destroyed or rebound); u_max scales features (1/u_max)
+ *   and output (u_max/64).
  *   At every interval start lb_step first builds the features of those boxes
  *   from the ring and runs the network.
  * lb_mlp_features: feature matrix bf16 [6 E^2][32] of one face set from four
  *   samples [6][3][E][E] (real_dtype LB_STORE_F64 or LB_STORE_F32, device).
- * lb_mlp_targets: training targets f32 [6 E^2][3K]: (fine - Hermite) / u_max
+ * lb_mlp_targets: training targets f32 [6 E^2][3K]: (fine - Hermite) * 64 / u_max
  *   with fine [K + 1][6][3][E][E] the boundary at t = jK .. jK + K;
  *   first_interval = 1 uses the one-sided tangent of interval 0.
  * lb_mlp_forward: Y f32 [rows][3K] from features X bf16 [rows][32].

@@ -14,7 +14,12 @@ Network (one row per face site and interval):
   h1 = relu(x W1 + b1)   (128)
   h2 = relu(h1 W2 + b2)  (128)
   y  = h2 W3 + b3        (3 K), y[3 (s - 1) + c] = residual of component c at
-                          substep s, in units of u_max.
+                          substep s, in units of u_max / OUT_DIV.
+
+The output unit is a fraction of u_max because the Hermite residual is a few
+thousandths of u_max: with targets that small, Adam's step (a fixed fraction
+of a weight's scale per update) is large against the output weights the fit
+needs, and training stalls at a noisy fit.
 
 Rows are ordered face-major: row = (f E + q) E + p, faces x-, x+, y-, y+, z-, z+
 with the in-face coordinates of the sample layout ([6][3][E][E], (q, p)).
@@ -26,6 +31,7 @@ import numpy as np
 NFEAT = 24
 NIN = 32
 HIDDEN = 128
+OUT_DIV = 64.0  # network output unit: u_max / OUT_DIV
 
 
 def _face_grad(U):
@@ -77,12 +83,13 @@ def hermite(samples, j, s, K):
 
 
 def targets(fine, samples, j, K, u_max):
-    """Target matrix [6 E^2][3 K]: (fine boundary velocity - Hermite) / u_max at
-    t = jK + s, s = 1..K.  fine: [T][6][3][E][E] sampled every step."""
+    """Target matrix [6 E^2][3 K]: (fine boundary velocity - Hermite) in units
+    of u_max / OUT_DIV at t = jK + s, s = 1..K.  fine: [T][6][3][E][E] sampled
+    every step."""
     E = np.asarray(samples).shape[-1]
     T = np.zeros((6 * E * E, 3 * K))
     for s in range(1, K + 1):
-        r = (np.asarray(fine[j * K + s], np.float64) - hermite(samples, j, s, K)) / u_max
+        r = (np.asarray(fine[j * K + s], np.float64) - hermite(samples, j, s, K)) * (OUT_DIV / u_max)
         for c in range(3):
             T[:, 3 * (s - 1) + c] = r[:, c].reshape(-1)
     return T
@@ -142,5 +149,5 @@ def residual_block(p, samples, j, K, u_max):
     R = np.zeros((6, 3, K, E, E))
     for s in range(K):
         for c in range(3):
-            R[:, c, s] = (y[:, 3 * s + c] * u_max).reshape(6, E, E)
+            R[:, c, s] = (y[:, 3 * s + c] * (u_max / OUT_DIV)).reshape(6, E, E)
     return R

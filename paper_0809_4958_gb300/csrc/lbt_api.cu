@@ -316,7 +316,7 @@ int enqueue_step(lb_ctx* ctx, int64_t n)
     sp.ring_slots = ctx->L.ring_slots;
     sp.mlp_y = ctx->at<float>(ctx->L.mlp_y);
     sp.mlp_nout = 3 * ctx->L.mlp_K;
-    sp.mlp_umax = (float)ctx->mlp_umax;
+    sp.mlp_yunit = (float)(ctx->mlp_umax / kMlpOutDiv);
     sp.boxes = ctx->at<BoxDev>(ctx->L.boxes);
     sp.tile_prefix = ctx->at<int64_t>(ctx->L.tile_prefix);
     sp.nboxes = ctx->nboxes;

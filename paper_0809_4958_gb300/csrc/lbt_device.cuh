@@ -216,7 +216,7 @@ __device__ __forceinline__ void add_mlp_residual(const SCParams& p, const BoxDev
     if (bd.mlp_row < 0) return;
     const int s = (int)(n + 1 - (n / bd.K) * bd.K);
     const float* y = p.mlp_y + (bd.mlp_row + ((int64_t)f * bd.E + qq) * bd.E + pp) * p.mlp_nout + 3 * (s - 1);
-    for (int c = 0; c < 3; c++) ub[c] += (R)(p.mlp_umax * y[c]);
+    for (int c = 0; c < 3; c++) ub[c] += (R)(p.mlp_yunit * y[c]);
 }
 
 // Owning face of a boundary site (first velocity face containing it in the

@@ -80,7 +80,7 @@ struct SCParams {
     int32_t ring_slots;
     const float* mlp_y;           // upsampler output [rows][mlp_nout] of the current interval
     int32_t mlp_nout;
-    float mlp_umax;
+    float mlp_yunit;              // velocity of one output unit (u_max / 64)
     const BoxDev* boxes;
     const int64_t* tile_prefix;   // [nboxes + 1] first tile of each box for the current block size
     int32_t nboxes;

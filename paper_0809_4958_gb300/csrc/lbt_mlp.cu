@@ -463,7 +463,7 @@ cudaError_t mlp_features_one(const MlpFeatureSet& set, double u_max, int real_f6
 cudaError_t mlp_targets(const void* const smp[4], const void* fine, int E, int K, int first_interval, double u_max,
                         int real_f64, float* T, cudaStream_t s)
 {
-    const float inv = (float)(1.0 / u_max);
+    const float inv = (float)(kMlpOutDiv / u_max);  // targets in the output unit
     const int64_t rows = 6LL * E * E;
     if (real_f64)
         k_mlp_targets<double><<<grid_cap(rows, 256), 256, 0, s>>>(

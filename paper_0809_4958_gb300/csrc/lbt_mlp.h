@@ -10,6 +10,7 @@ namespace lbt {
 constexpr int kMlpIn = 32;       // 24 features, zero padded
 constexpr int kMlpFeat = 24;
 constexpr int kMlpHidden = 128;
+constexpr float kMlpOutDiv = 64.0f;  // network output unit: u_max / kMlpOutDiv
 
 // Byte offsets of the inference parameters and float offsets of the master copy.
 struct MlpLayout {

@@ -71,12 +71,16 @@ def test_features_and_targets_match_oracle(lbt, data):
         X = lbt.mlp_features(d(coarse[max(j - 1, 0)]), d(coarse[j]), d(coarse[j + 1]), d(coarse[j + 2]), E, U_MAX)
         X = X.float().cpu().numpy().astype(np.float64)
         Xref = omlp.features(coarse, j, U_MAX)
-        # bf16 on the GPU: within one bf16 ulp of the rounded oracle value
-        assert np.all(np.abs(X - bf16(Xref)) <= 2.0 ** -8 * np.abs(Xref) + 1e-30)
+        # bf16 on the GPU (rounded from an FP32 difference): within one bf16
+        # ulp (2^-7 of the value at most) of the rounded oracle value
+        assert np.all(np.abs(X - bf16(Xref)) <= 2.0 ** -7 * np.abs(Xref) + 1e-30)
         T = lbt.mlp_targets(d(coarse[max(j - 1, 0)]), d(coarse[j]), d(coarse[j + 1]), d(coarse[j + 2]),
                             d(fine[j * K:j * K + K + 1]), E, K, int(j == 0), U_MAX).cpu().numpy()
         Tref = omlp.targets(fine, coarse, j, K, U_MAX)
-        assert np.abs(T - Tref).max() <= 1e-5 * max(1.0, np.abs(Tref).max())
+        # FP32 samples carry 2^-24 relative rounding of |u| <= u_max, i.e.
+        # 2^-24 OUT_DIV in target units; fine value plus Hermite weights sum
+        # to at most 4 in magnitude, and as much again for the arithmetic
+        assert np.abs(T - Tref).max() <= 8 * 2.0 ** -24 * omlp.OUT_DIV
         assert np.abs(Tref).max() > 1e-4  # a residual worth learning exists
 
 
@@ -119,27 +123,31 @@ def test_gradients_match_oracle(lbt, data):
 
 
 def _dataset(lbt, seeds, E, nint):
+    # intervals 0 .. nint-1 of every seed (interval 0: clamped j-1 sample and
+    # the one-sided Hermite tangent, as the step uses them)
     from paper_0809_4958_gb300 import inputs
     Xs, Ts = [], []
     for sd in seeds:
         modes = inputs.mode_table(sd, 128, 1.0, E / 2.0, E)
         fine = lbt.synth_faces(modes, E, 1, 0, (nint + 2) * K + 1, torch.float32)
         coarse = fine[::K]
-        for j in range(1, nint):
-            Xs.append(lbt.mlp_features(coarse[j - 1], coarse[j], coarse[j + 1], coarse[j + 2], E, U_MAX))
-            Ts.append(lbt.mlp_targets(coarse[j - 1], coarse[j], coarse[j + 1], coarse[j + 2],
-                                      fine[j * K:j * K + K + 1].contiguous(), E, K, 0, U_MAX))
+        for j in range(0, nint):
+            jm = max(j - 1, 0)
+            Xs.append(lbt.mlp_features(coarse[jm], coarse[j], coarse[j + 1], coarse[j + 2], E, U_MAX))
+            Ts.append(lbt.mlp_targets(coarse[jm], coarse[j], coarse[j + 1], coarse[j + 2],
+                                      fine[j * K:j * K + K + 1].contiguous(), E, K, int(j == 0), U_MAX))
     return torch.cat(Xs), torch.cat(Ts)
 
 
 def train(lbt, X, T, steps, lr=2e-3, batch=8192, seed=0):
+    # Adam with a cosine learning-rate decay
     from paper_0809_4958_gb300 import inputs
     up = lbt.Upsampler(K=K, batch_rows=batch, master=inputs.mlp_init(seed, K))
     gen = torch.Generator(device="cuda").manual_seed(seed)
     losses = []
     for it in range(steps):
         idx = torch.randint(0, X.shape[0], (batch,), device="cuda", generator=gen)
-        up.step(X[idx].contiguous(), T[idx].contiguous(), lr)
+        up.step(X[idx].contiguous(), T[idx].contiguous(), lr * 0.5 * (1.0 + np.cos(np.pi * it / steps)))
         if it % 50 == 0 or it == steps - 1:
             losses.append(up.loss.item())
     return up, losses
@@ -170,7 +178,7 @@ def test_mlp_boundary_matches_oracle(lbt):
     # against the oracle step with the FP64 residual of the same weights
     E = 16
     p = omlp.init_params(7, K, scale=0.3)
-    p["b3"] = np.random.default_rng(3).normal(0, 0.02, 3 * K)
+    p["b3"] = np.random.default_rng(3).normal(0, 1.0, 3 * K)
     up = lbt.Upsampler(K=K, batch_rows=256, master=master_vector(p))
     params = up.export()
     c = Case(E, 0.8, 64, M=32, K=K, time_interp=2)
@@ -188,13 +196,19 @@ def test_mlp_boundary_matches_oracle(lbt):
 
 
 def test_learned_boundary_beats_hermite(lbt):
-    # train on boundary data of some boxes, then run held-out boxes with
-    # samples every K = 16 steps: interior velocity error against the run that
-    # sees the boundary every step, Hermite vs Hermite + learned residual
+    # train on boundary data of some boxes, then on held-out boxes with samples
+    # every K = 16 steps: (1) the boundary residual the network leaves, against
+    # the residual of Hermite alone; (2) the interior velocity error against
+    # the run that sees the boundary every step, Hermite vs Hermite + network
     E = 16
-    X, T = _dataset(lbt, [41, 42, 43, 44], E, 8)
-    up, losses = train(lbt, X, T, 600)
+    X, T = _dataset(lbt, list(range(41, 53)), E, 8)
+    up, losses = train(lbt, X, T, 2500)
     params = up.export()
+    Xh, Th = _dataset(lbt, [91, 92], E, 8)
+    Yh = lbt.mlp_forward(params, K, Xh)
+    ratio = float(((Yh - Th) ** 2).mean() / (Th ** 2).mean())
+    print("held-out boundary residual left by the network: %.3f of Hermite's" % ratio)
+    assert ratio < 0.5
     errs = {"hermite": [], "mlp": []}
     for sd in (91, 92):
         ref = Case(E, 0.8, 128, seed=sd, M=128, K=1, time_interp=0)

@@ -82,7 +82,7 @@ def test_residual_layout_from_the_output_bias():
     p["b3"][3 * s + c] = 0.5
     S = np.zeros((6, 6, 3, E, E))
     R = mlp.residual_block(p, S, 1, K, u_max)
-    assert np.allclose(R[:, c, s], 0.5 * u_max) and np.count_nonzero(R) == 6 * E * E
+    assert np.allclose(R[:, c, s], 0.5 * u_max / mlp.OUT_DIV) and np.count_nonzero(R) == 6 * E * E
 
 
 def test_zero_network_reproduces_hermite_boundary(orc):
@@ -103,3 +103,29 @@ def test_zero_network_reproduces_hermite_boundary(orc):
     resid[1, 0, 0, 2] += 1e-3
     mlpr2 = orc.Sim(orc.BoxParams(E=E, tau=0.8, K=K, time_interp=orc.TIME_MLP), u0, S, resid=resid)
     assert mlpr2.run(steps) == 0 and not np.array_equal(herm.f, mlpr2.f)
+
+
+def test_exact_targets_reproduce_the_every_step_boundary(orc):
+    # the targets, used as the residual of the boundary, must give back the
+    # boundary of the run that sees a sample every step: same substep, face,
+    # site and unit on both sides of the definition
+    E, K, steps = 16, 4, 24
+    from paper_0809_4958_gb300 import inputs
+    modes = inputs.mode_table(4, 32, 1, 4, E)
+    fine = orc.face_samples(modes, E, 1, 0, steps + 4 * K + 1)
+    S = fine[::K]
+    u0 = orc.volume_field(modes, E, 0.0)
+    u_max = 0.05
+    resid = np.zeros((steps // K, 6, 3, K, E, E))
+    for j in range(steps // K):
+        T = mlp.targets(fine, S, j, K, u_max)
+        for s in range(K):
+            for c in range(3):
+                resid[j, :, c, s] = T[:, 3 * s + c].reshape(6, E, E) * (u_max / mlp.OUT_DIV)
+    every = orc.Sim(orc.BoxParams(E=E, tau=0.8, K=1, time_interp=orc.TIME_LINEAR), u0, fine)
+    learned = orc.Sim(orc.BoxParams(E=E, tau=0.8, K=K, time_interp=orc.TIME_MLP), u0, S, resid=resid)
+    herm = orc.Sim(orc.BoxParams(E=E, tau=0.8, K=K, time_interp=orc.TIME_HERMITE), u0, S)
+    assert every.run(steps) == 0 and learned.run(steps) == 0 and herm.run(steps) == 0
+    u = every.fields()[1]
+    assert np.max(np.abs(learned.fields()[1] - u)) <= 1e-15
+    assert np.max(np.abs(herm.fields()[1] - u)) > 1e-7  # Hermite alone misses it
