@@ -86,11 +86,17 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = {
+    "k_stream_collide_staged": ("lbt_sc_staged.cuh", "lbt_device.cuh", "lbt_internal.h"),
+    "k_stream_collide": ("lbt_kernels.cuh", "lbt_device.cuh", "lbt_internal.h"),
+}
+
+
+def kernel_source_hash(kernel):
+    """Hash of the sources a stream-collide kernel is compiled from."""
     h = hashlib.sha256()
-    for rel in ("paper_0809_4958_gb300/csrc/lbt_kernels.cuh", "paper_0809_4958_gb300/csrc/lbt_device.cuh",
-                "paper_0809_4958_gb300/csrc/lbt_sc_staged.cuh"):
-        with open(os.path.join(ROOT, rel), "rb") as f:
+    for rel in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_0809_4958_gb300", "csrc", rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -103,7 +109,7 @@ def ncu_traffic(storage, kernel):
         with open(path) as f:
             d = json.load(f)
         ent = d.get("%s/%s" % (storage, kernel))
-        if ent and ent.get("kernel_hash") == kernel_source_hash():
+        if ent and ent.get("kernel_hash") == kernel_source_hash(kernel):
             return float(ent["bytes_per_launch_full_size"])
     except Exception:
         pass

@@ -230,13 +230,15 @@ int32_t lb_status(lb_ctx* ctx, int32_t box, int32_t* status);
 int64_t lb_current_step(const lb_ctx* ctx);
 
 /* stream-collide kernels */
-#define LB_KERNEL_STAGED 0    /* persistent, tiles staged in shared memory by TMA bulk copies, two-stage pipeline */
+#define LB_KERNEL_STAGED 0    /* persistent, tiles staged in shared memory by TMA bulk copies, producer warp + 15 consumer warps */
 #define LB_KERNEL_REGISTER 1  /* one vector load per population into registers, x-neighbours by warp shuffles */
 
 /* lb_set_launch -- choice and launch shape of the stream-collide kernel.
- *   kernel LB_KERNEL_STAGED (default): 512 threads per block, tiles of 4 KB
- *   per population row; threads and sites_per_thread must be 0;
- *   ctas = persistent grid (0 = one block per SM).
+ *   kernel LB_KERNEL_STAGED (default): 512 threads per block (one producer
+ *   warp, 15 consumer warps), tiles of 480 x sites_per_thread sites staged
+ *   in as many pipeline stages as fit in shared memory; threads must be 0;
+ *   sites_per_thread 0 (default: 1 for FP64, 2 otherwise), 1, or 2 (not
+ *   FP64); ctas = persistent grid (0 = one block per SM).
  *   kernel LB_KERNEL_REGISTER: threads per block (multiple of 32, 64 .. 256),
  *   ctas = persistent grid (0 = one block per tile), sites_per_thread
  *   (0 = default: 2 for FP64, 4 for FP32, 8 for 16-bit storage; half or a
@@ -270,16 +272,20 @@ const char* lb_last_error(const lb_ctx* ctx);
  * least lb_synth_workspace_bytes(M, E) bytes for the per-axis phase table.
  * Enqueued on `stream` (cudaStream_t); no synchronisation.
  *
- * lb_synth_faces: samples j0 .. j0+nsamp-1 at t = j K on the six faces,
- *   out [nsamp][6][3][E][E] (device).
- * lb_synth_volume: the field on every site at time t, out [3][E^3] (device).
+ * Points: the coarse grid of a box with zoom z (every z-th site, from site 0
+ * to site E - 1, Ec = (E - 1)/z + 1 per axis; every site for z = 1; E - 1
+ * divisible by z).
+ * lb_synth_faces: samples j0 .. j0+nsamp-1 at t = j K on the coarse points
+ *   of the six faces, out [nsamp][6][3][Ec][Ec] (device).
+ * lb_synth_volume: the field at time t on the coarse grid, out [3][Ec^3]
+ *   (device).
  */
 size_t lb_synth_workspace_bytes(int32_t M, int32_t E);
 int32_t lb_synth_faces(const double* kvec, const double* amp, const double* omega, const double* phi,
-                       int32_t M, int32_t E, int32_t K, int64_t j0, int64_t nsamp, int32_t out_dtype,
+                       int32_t M, int32_t E, int32_t zoom, int32_t K, int64_t j0, int64_t nsamp, int32_t out_dtype,
                        void* out, void* workspace, void* stream);
 int32_t lb_synth_volume(const double* kvec, const double* amp, const double* omega, const double* phi,
-                        int32_t M, int32_t E, double t, int32_t out_dtype, void* out, void* workspace,
+                        int32_t M, int32_t E, int32_t zoom, double t, int32_t out_dtype, void* out, void* workspace,
                         void* stream);
 
 /*

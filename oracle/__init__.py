@@ -58,7 +58,7 @@ class _Box(ctypes.Structure):
         ("time_interp", ctypes.c_int32),
         ("K", ctypes.c_int32),
         ("storage", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("zoom", ctypes.c_int32),
     ]
 
 
@@ -128,6 +128,11 @@ class BoxParams:
     time_interp: int = TIME_LINEAR
     K: int = 1
     storage: int = STORE_F64
+    zoom: int = 1
+
+    def coarse_points(self):
+        """Points per axis of the coarse grid (samples and initial field)."""
+        return coarse_points(self.E, self.zoom)
 
     def c(self):
         b = _Box()
@@ -140,7 +145,14 @@ class BoxParams:
         b.time_interp = int(self.time_interp)
         b.K = int(self.K)
         b.storage = int(self.storage)
+        b.zoom = int(self.zoom)
         return b
+
+
+def coarse_points(E, zoom=1):
+    """Points per axis of the coarse grid: point P at site P zoom, until the
+    grid covers site E - 1 (every site for zoom 1)."""
+    return (E - 1 + zoom - 1) // zoom + 1 if zoom > 1 else E
 
 
 @dataclass
@@ -200,12 +212,13 @@ def round_bf16(x: float) -> float:
     return _load().orc_round_bf16(float(x))
 
 
-def philox4x64_10(ctr, key):
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of a 4-word counter and a 2-word key (uint32 words)."""
     lib = _load()
-    c = np.ascontiguousarray(ctr, dtype=np.uint64)
-    k = np.ascontiguousarray(key, dtype=np.uint64)
-    out = np.zeros(4, np.uint64)
-    lib.orc_philox4x64_10(_ptr(c), _ptr(k), _ptr(out))
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib.orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
     return out
 
 
@@ -220,10 +233,11 @@ def chain_forces(pos, k, R0, eps=1.0, sigma=1.0):
 
 
 def init(box: BoxParams, u0):
-    """Initial condition: equilibrium with rho = 1 and u0 [3][E^3] on every site."""
+    """Initial condition: equilibrium with rho = 1 and the velocity u0 given on
+    the coarse grid [3][Ec^3] (every site when zoom = 1), trilinear in between."""
     lib = _load()
-    E = box.E
-    u0 = np.ascontiguousarray(u0, dtype=np.float64).reshape(3, E, E, E)
+    E, Ec = box.E, box.coarse_points()
+    u0 = np.ascontiguousarray(u0, dtype=np.float64).reshape(3, Ec, Ec, Ec)
     f = np.zeros((Q, E, E, E))
     b = box.c()
     lib.orc_init(ctypes.byref(b), _ptr(u0), _ptr(f))
@@ -362,21 +376,26 @@ def field(modes, E, pts, t):
     return out
 
 
-def face_samples(modes, E, K, j0, nsamp):
-    """Coarse face samples j0..j0+nsamp-1 at t = j K: [nsamp][6][3][E][E]."""
+def face_samples(modes, E, K, j0, nsamp, zoom=1):
+    """Coarse face samples j0..j0+nsamp-1 at t = j K on the coarse face points
+    (site P zoom): [nsamp][6][3][Ec][Ec], Ec = coarse_points(E, zoom)."""
     lib = _load()
-    out = np.zeros((nsamp, 6, 3, E, E))
+    Ec = coarse_points(E, zoom)
+    out = np.zeros((nsamp, 6, 3, Ec, Ec))
     lib.orc_face_samples(_ptr(modes.kvec), _ptr(modes.amp), _ptr(modes.omega), _ptr(modes.phi), ctypes.c_int(modes.M),
-                         ctypes.c_int(E), ctypes.c_int(K), ctypes.c_long(j0), ctypes.c_long(nsamp), _ptr(out))
+                         ctypes.c_int(E), ctypes.c_int(zoom), ctypes.c_int(K), ctypes.c_long(j0),
+                         ctypes.c_long(nsamp), _ptr(out))
     return out
 
 
-def volume_field(modes, E, t=0.0):
-    """Synthetic flow on every site at time t: [3][E][E][E]."""
+def volume_field(modes, E, t=0.0, zoom=1):
+    """Synthetic flow at time t on the coarse grid (every zoom-th site; every
+    site when zoom = 1): [3][Ec][Ec][Ec]."""
     lib = _load()
-    out = np.zeros((3, E, E, E))
+    Ec = coarse_points(E, zoom)
+    out = np.zeros((3, Ec, Ec, Ec))
     lib.orc_volume_field(_ptr(modes.kvec), _ptr(modes.amp), _ptr(modes.omega), _ptr(modes.phi), ctypes.c_int(modes.M),
-                         ctypes.c_int(E), ctypes.c_double(t), _ptr(out))
+                         ctypes.c_int(E), ctypes.c_int(zoom), ctypes.c_double(t), _ptr(out))
     return out
 
 

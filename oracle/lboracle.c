@@ -24,7 +24,7 @@
  *     the chain centre of mass pinned at the box centre (Sec. 2).
  *   - The synthetic coarse flow that stands in for the DNS sub-volume record
  *     (a sum of Fourier modes with a Kolmogorov spectrum).
- *   - Philox4x64-10 (Salmon et al., SC'11) for the bead noise.
+ *   - Philox4x32-10 (Salmon et al., SC'11) for the bead noise.
  *
  * Everything is written for clarity, site by site, with no blocking or fusion.
  * OpenMP only splits the z loop of the lattice sweep; the arithmetic of each
@@ -74,8 +74,15 @@ typedef struct {
     int32_t time_interp; /* ORC_TIME_* */
     int32_t K;           /* LB steps per coarse sample interval */
     int32_t storage;     /* ORC_STORE_*: emulate 16-bit storage of f_i - w_i */
-    int32_t pad;
+    int32_t zoom;        /* z = coarse grid spacing / LB spacing (Sec. 3) */
 } orc_box;
+
+/* points per axis of the coarse grid of a box: coarse point P sits at site
+ * P z, from site 0 until the grid covers site E - 1 (the last coarse cell may
+ * reach past the box when z does not divide E - 1) */
+static int coarse_points_of(int E, int z) { return z > 1 ? (E - 1 + z - 1) / z + 1 : E; }
+static int coarse_points(const orc_box *b) { return coarse_points_of(b->E, b->zoom); }
+static int zoom_of(const orc_box *b) { return b->zoom > 1 ? b->zoom : 1; }
 
 typedef struct {
     int32_t nbeads;
@@ -153,40 +160,36 @@ static double store_round(int storage, double d)
 }
 
 /* ------------------------------------------------------------------ */
-/* Philox4x64-10 counter-based generator (Salmon, Moraes, Dror, Shaw,   */
-/* "Parallel random numbers: as easy as 1, 2, 3", SC'11).               */
+/* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw,   */
+/* "Parallel random numbers: as easy as 1, 2, 3", SC'11): ten rounds of */
+/* two 32x32->64 multiplications with the key bumped by two Weyl        */
+/* constants between rounds.                                            */
 
-static void mul128(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo)
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
 {
-    unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
-    *hi = (uint64_t)(p >> 64);
-    *lo = (uint64_t)p;
-}
-
-void orc_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4])
-{
-    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
-    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
-    uint64_t x0 = ctr_in[0], x1 = ctr_in[1], x2 = ctr_in[2], x3 = ctr_in[3];
-    uint64_t k0 = key_in[0], k1 = key_in[1];
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t x0 = ctr_in[0], x1 = ctr_in[1], x2 = ctr_in[2], x3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
     for (int r = 0; r < 10; r++) {
         if (r > 0) {
             k0 += W0;
             k1 += W1;
         }
-        uint64_t hi0, lo0, hi1, lo1;
-        mul128(M0, x0, &hi0, &lo0);
-        mul128(M1, x2, &hi1, &lo1);
-        uint64_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+        uint64_t p0 = (uint64_t)M0 * x0, p1 = (uint64_t)M1 * x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
         x0 = y0; x1 = y1; x2 = y2; x3 = y3;
     }
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* Unit-variance uniform number on [-sqrt3, sqrt3) from the top 53 bits of a word. */
-static double uniform_unit_variance(uint64_t v)
+/* Unit-variance uniform number on [-sqrt3, sqrt3) from a 32-bit word:
+ * u = v 2^-32 (exact in double), xi = sqrt3 (2u - 1). */
+static double uniform_unit_variance(uint32_t v)
 {
-    double u01 = (double)(v >> 11) * (1.0 / 9007199254740992.0); /* 2^-53 */
+    double u01 = (double)v * (1.0 / 4294967296.0); /* 2^-32 */
     return sqrt(3.0) * (2.0 * u01 - 1.0);
 }
 
@@ -258,16 +261,21 @@ static void moments(const double fi[Q], double *rho, double j[3])
  *   Hermite: cubic Hermite with Catmull-Rom tangents m_j = (U_{j+1}-U_{j-1})/2,
  *            one-sided m_0 = U_1 - U_0 on the first interval
  *   MLP:     Hermite plus a learned residual r[face][comp][s-1][q][p],
- *            s = t - jK in 1..K, supplied by the caller for interval j. */
-static int face_velocity(const orc_box *b, const double *samples, long nsamples,
-                         const double *resid, long n, int f, int p, int q, double u[3])
+ *            s = t - jK in 1..K, supplied by the caller for interval j.
+ * The samples live on the coarse face grid ([6][3][Ec][Ec], point P at site
+ * P z).  With zoom z > 1 the velocity at a
+ * site is the bilinear interpolation, within the face, of the time-interpolated
+ * velocities at the four surrounding coarse points (Sec. 3: bilinear in space
+ * between neighbouring grid points, linear in time). */
+static int coarse_velocity(const orc_box *b, const double *samples, long nsamples, long n, int f, int P, int Qc,
+                           double u[3])
 {
-    int E = b->E, K = b->K;
+    int K = b->K, Ec = coarse_points(b);
     long j = n / K;
     int s = (int)(n + 1 - j * K);
     double th = (double)s / (double)K;
-    long face_stride = 3L * E * E;
-#define U_AT(jj, c) samples[((long)(jj) * 6 + f) * face_stride + (long)(c) * E * E + (long)q * E + p]
+    long face_stride = 3L * Ec * Ec;
+#define U_AT(jj, c) samples[((long)(jj) * 6 + f) * face_stride + (long)(c) * Ec * Ec + (long)Qc * Ec + P]
     if (b->time_interp == ORC_TIME_LINEAR) {
         if (j + 1 >= nsamples) return ORC_ERR_SAMPLES;
         for (int c = 0; c < 3; c++) u[c] = (1.0 - th) * U_AT(j, c) + th * U_AT(j + 1, c);
@@ -283,10 +291,36 @@ static int face_velocity(const orc_box *b, const double *samples, long nsamples,
         double m0 = (j >= 1) ? 0.5 * (u1 - U_AT(j - 1, c)) : (u1 - u0);
         double m1 = 0.5 * (u2 - u0);
         u[c] = h00 * u0 + h10 * m0 + h01 * u1 + h11 * m1;
-        if (b->time_interp == ORC_TIME_MLP && resid)
-            u[c] += resid[(((long)f * 3 + c) * K + (s - 1)) * E * E + (long)q * E + p];
     }
 #undef U_AT
+    return ORC_OK;
+}
+
+static int face_velocity(const orc_box *b, const double *samples, long nsamples,
+                         const double *resid, long n, int f, int p, int q, double u[3])
+{
+    int E = b->E, K = b->K, z = zoom_of(b);
+    if (z == 1) {
+        int e = coarse_velocity(b, samples, nsamples, n, f, p, q, u);
+        if (e) return e;
+    } else {
+        /* coarse cell (P0, Q0) holding the site and the site's fractions in it */
+        int P0 = p / z, Q0 = q / z, Ec = coarse_points(b);
+        int P1 = P0 + 1 < Ec ? P0 + 1 : P0, Q1 = Q0 + 1 < Ec ? Q0 + 1 : Q0;
+        double fp = (double)(p - P0 * z) / z, fq = (double)(q - Q0 * z) / z;
+        double u00[3], u10[3], u01[3], u11[3];
+        int e = coarse_velocity(b, samples, nsamples, n, f, P0, Q0, u00);
+        if (!e) e = coarse_velocity(b, samples, nsamples, n, f, P1, Q0, u10);
+        if (!e) e = coarse_velocity(b, samples, nsamples, n, f, P0, Q1, u01);
+        if (!e) e = coarse_velocity(b, samples, nsamples, n, f, P1, Q1, u11);
+        if (e) return e;
+        for (int c = 0; c < 3; c++)
+            u[c] = (1.0 - fq) * ((1.0 - fp) * u00[c] + fp * u10[c]) + fq * ((1.0 - fp) * u01[c] + fp * u11[c]);
+    }
+    if (b->time_interp == ORC_TIME_MLP && resid && z == 1) {
+        int s = (int)(n + 1 - (n / K) * K);
+        for (int c = 0; c < 3; c++) u[c] += resid[(((long)f * 3 + c) * K + (s - 1)) * E * E + (long)q * E + p];
+    }
     return ORC_OK;
 }
 
@@ -300,15 +334,43 @@ int orc_face_velocity(const orc_box *b, const double *samples, long nsamples, co
 /* ------------------------------------------------------------------ */
 /* initial condition: local equilibrium with rho = 1 and u0 on every site */
 
-void orc_init(const orc_box *b, const double *u0 /* [3][E^3] */, double *f /* [19][E^3] */)
+/* u0: the field on the coarse grid, [3][Ec][Ec][Ec] (the sites themselves when
+ * z = 1); with z > 1 each site takes the trilinear interpolation of the eight
+ * surrounding coarse points (Sec. 2: the initial field interpolated linearly
+ * from the DNS grid). */
+void orc_init(const orc_box *b, const double *u0 /* [3][Ec^3] */, double *f /* [19][E^3] */)
 {
-    int E = b->E;
-    long n3 = (long)E * E * E;
-    for (long s = 0; s < n3; s++) {
-        double u[3] = {u0[s], u0[n3 + s], u0[2 * n3 + s]}, feq[Q];
-        orc_equilibrium(1.0, u, feq);
-        for (int i = 0; i < Q; i++) f[i * n3 + s] = WV[i] + store_round(b->storage, feq[i] - WV[i]);
-    }
+    int E = b->E, z = zoom_of(b), Ec = coarse_points(b);
+    long n3 = (long)E * E * E, c3 = (long)Ec * Ec * Ec;
+    for (int zz = 0; zz < E; zz++)
+        for (int y = 0; y < E; y++)
+            for (int x = 0; x < E; x++) {
+                long s = site_index(E, x, y, zz);
+                double u[3], feq[Q];
+                if (z == 1) {
+                    for (int c = 0; c < 3; c++) u[c] = u0[c * c3 + s];
+                } else {
+                    int i0[3] = {x / z, y / z, zz / z}, i1[3];
+                    double fr[3];
+                    int xyz[3] = {x, y, zz};
+                    for (int a = 0; a < 3; a++) {
+                        i1[a] = i0[a] + 1 < Ec ? i0[a] + 1 : i0[a];
+                        fr[a] = (double)(xyz[a] - i0[a] * z) / z;
+                    }
+                    for (int c = 0; c < 3; c++) {
+                        double acc = 0.0;
+                        for (int k = 0; k < 8; k++) {
+                            int X = (k & 1) ? i1[0] : i0[0], Y = (k & 2) ? i1[1] : i0[1], Z = (k & 4) ? i1[2] : i0[2];
+                            double w = ((k & 1) ? fr[0] : 1.0 - fr[0]) * ((k & 2) ? fr[1] : 1.0 - fr[1]) *
+                                       ((k & 4) ? fr[2] : 1.0 - fr[2]);
+                            acc += w * u0[c * c3 + ((long)Z * Ec + Y) * Ec + X];
+                        }
+                        u[c] = acc;
+                    }
+                }
+                orc_equilibrium(1.0, u, feq);
+                for (int i = 0; i < Q; i++) f[i * n3 + s] = WV[i] + store_round(b->storage, feq[i] - WV[i]);
+            }
 }
 
 /* ------------------------------------------------------------------ */
@@ -435,8 +497,9 @@ int orc_chain_forces(int nbeads, double k, double R0, double eps, double sigma, 
  *   4. the momentum the beads gave to the fluid, -sum (F_fric + F_noise) dt,
  *      spread with the start-of-step trilinear weights into g[3][E^3]
  *      (force density, accumulated in bead order; caller zeroes g).
- * Noise: xi_a from Philox4x64-10, counter (n, substep, bead, box_id),
- * key (seed, 0), word a, mapped to uniform with unit variance. */
+ * Noise: xi_a from Philox4x32-10, counter (n mod 2^32, substep, bead, box_id),
+ * key (low and high 32 bits of seed), word a, mapped to a uniform number with
+ * unit variance. */
 int orc_chain_couple(const orc_box *b, const orc_chain *ch, const double *A, long n,
                      double *pos, double *vel, double *g)
 {
@@ -473,10 +536,10 @@ int orc_chain_couple(const orc_box *b, const orc_chain *ch, const double *A, lon
         for (int bb = 0; bb < N; bb++) {
             double xi[3] = {0.0, 0.0, 0.0};
             if (noise_amp > 0.0) {
-                uint64_t ctr[4] = {(uint64_t)n, (uint64_t)sub, (uint64_t)bb, ch->box_id};
-                uint64_t key[2] = {ch->seed, 0};
-                uint64_t r[4];
-                orc_philox4x64_10(ctr, key, r);
+                uint32_t ctr[4] = {(uint32_t)n, (uint32_t)sub, (uint32_t)bb, (uint32_t)ch->box_id};
+                uint32_t key[2] = {(uint32_t)ch->seed, (uint32_t)(ch->seed >> 32)};
+                uint32_t r[4];
+                orc_philox4x32_10(ctr, key, r);
                 for (int a = 0; a < 3; a++) xi[a] = uniform_unit_variance(r[a]);
             }
             for (int a = 0; a < 3; a++) {
@@ -676,12 +739,13 @@ void orc_field(const double *kvec, const double *amp, const double *omega, const
 }
 
 /* Coarse face samples j0 .. j0+nsamp-1, taken at t = j K, evaluated at the
- * face sites: out[j][face][comp][q][p]. */
+ * coarse face points (site P zoom, Ec points per side): out[j][face][comp][Q][P]. */
 void orc_face_samples(const double *kvec, const double *amp, const double *omega, const double *phi,
-                      int M, int E, int K, long j0, long nsamp, double *out)
+                      int M, int E, int zoom, int K, long j0, long nsamp, double *out)
 {
     double xc[3] = {0.5 * (E - 1), 0.5 * (E - 1), 0.5 * (E - 1)};
-    long ns = (long)E * E;
+    int z = zoom > 1 ? zoom : 1, Ec = coarse_points_of(E, z);
+    long ns = (long)Ec * Ec;
     double *pts = (double *)malloc(sizeof(double) * 3 * ns);
     double *val = (double *)malloc(sizeof(double) * 3 * ns);
     for (long j = 0; j < nsamp; j++) {
@@ -689,12 +753,13 @@ void orc_face_samples(const double *kvec, const double *amp, const double *omega
         for (int f = 0; f < 6; f++) {
             int axis = f / 2;
             int fixed = (f % 2) ? E - 1 : 0;
-            for (int q = 0; q < E; q++)
-                for (int p = 0; p < E; p++) {
-                    double *P = &pts[3 * ((long)q * E + p)];
-                    if (axis == 0) { P[0] = fixed; P[1] = p; P[2] = q; }
-                    else if (axis == 1) { P[0] = p; P[1] = fixed; P[2] = q; }
-                    else { P[0] = p; P[1] = q; P[2] = fixed; }
+            for (int q = 0; q < Ec; q++)
+                for (int p = 0; p < Ec; p++) {
+                    double *P = &pts[3 * ((long)q * Ec + p)];
+                    double pp = (double)p * z, qq = (double)q * z;
+                    if (axis == 0) { P[0] = fixed; P[1] = pp; P[2] = qq; }
+                    else if (axis == 1) { P[0] = pp; P[1] = fixed; P[2] = qq; }
+                    else { P[0] = pp; P[1] = qq; P[2] = fixed; }
                 }
             orc_field(kvec, amp, omega, phi, M, xc, pts, ns, t, val);
             for (int c = 0; c < 3; c++)
@@ -705,19 +770,21 @@ void orc_face_samples(const double *kvec, const double *amp, const double *omega
     free(val);
 }
 
-/* Field on every site at time t: out[comp][z][y][x]. */
+/* Field at time t on the coarse grid (every zoom-th site, Ec points per
+ * axis; every site when zoom = 1): out[comp][Z][Y][X]. */
 void orc_volume_field(const double *kvec, const double *amp, const double *omega, const double *phi,
-                      int M, int E, double t, double *out)
+                      int M, int E, int zoom, double t, double *out)
 {
     double xc[3] = {0.5 * (E - 1), 0.5 * (E - 1), 0.5 * (E - 1)};
-    long n3 = (long)E * E * E;
+    int zm = zoom > 1 ? zoom : 1, Ec = coarse_points_of(E, zm);
+    long n3 = (long)Ec * Ec * Ec;
     double *pts = (double *)malloc(sizeof(double) * 3 * n3);
     double *val = (double *)malloc(sizeof(double) * 3 * n3);
-    for (int z = 0; z < E; z++)
-        for (int y = 0; y < E; y++)
-            for (int x = 0; x < E; x++) {
-                long s = site_index(E, x, y, z);
-                pts[3 * s] = x; pts[3 * s + 1] = y; pts[3 * s + 2] = z;
+    for (int z = 0; z < Ec; z++)
+        for (int y = 0; y < Ec; y++)
+            for (int x = 0; x < Ec; x++) {
+                long s = site_index(Ec, x, y, z);
+                pts[3 * s] = (double)x * zm; pts[3 * s + 1] = (double)y * zm; pts[3 * s + 2] = (double)z * zm;
             }
     orc_field(kvec, amp, omega, phi, M, xc, pts, n3, t, val);
     for (int c = 0; c < 3; c++)

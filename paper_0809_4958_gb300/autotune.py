@@ -21,7 +21,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tune_cache.js
 
 def candidates(storage: int, sms: int):
     dv = {lbt.LB_STORE_F64: 2, lbt.LB_STORE_F32: 4, lbt.LB_STORE_F16DEV: 8, lbt.LB_STORE_BF16DEV: 8}[storage]
-    out = [(lbt.LB_KERNEL_STAGED, 0, 0, 0)]
+    out = [(lbt.LB_KERNEL_STAGED, 0, 0, spt) for spt in ((1,) if storage == lbt.LB_STORE_F64 else (2, 1))]
     for threads in (128, 256):
         for vw in sorted({dv, max(dv // 2, 1), max(dv // 4, 1)}):
             out.append((lbt.LB_KERNEL_REGISTER, threads, 0, vw))

@@ -225,7 +225,7 @@ int default_vw(int storage) { return storage == kF64 ? 2 : (storage == kF32 ? 4 
 int rebuild_tiles(lb_ctx* ctx)
 {
     // sites per tile: fixed by the staged kernel's geometry, threads x sites per thread otherwise
-    const int64_t T = ctx->kernel == LB_KERNEL_STAGED ? lbt_staged_tile_sites(ctx->storage)
+    const int64_t T = ctx->kernel == LB_KERNEL_STAGED ? lbt_staged_tile_sites(ctx->vw)
                                                       : (int64_t)ctx->threads * ctx->vw;
     ctx->tile_prefix.assign(ctx->nboxes + 1, 0);
     for (int b = 0; b < ctx->nboxes; b++)
@@ -346,6 +346,8 @@ int enqueue_step(lb_ctx* ctx, int64_t n)
     fp.step = ctx->at<int64_t>(ctx->L.step);
     fp.tile_counter = ctx->at<int64_t>(ctx->L.tile_counter);
     fp.nchains = nch;
+    fp.splits = (8 * ctx->max_beads + kForcedThreads - 1) / kForcedThreads;
+    if (fp.splits < 1) fp.splits = 1;
     CK(DISPATCH(ctx->storage, forced(fp, ctx->stream)));
     ctx->a_is_pop_a = !ctx->a_is_pop_a;
     return LB_OK;
@@ -446,7 +448,8 @@ int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int
     ctx->arena = reinterpret_cast<char*>(arena);
     ctx->stream = reinterpret_cast<cudaStream_t>(stream);
     ctx->pushed.assign(nboxes, -1);
-    ctx->vw = default_vw(storage);
+    ctx->vw = lbt_staged_default_spt(storage);  // the default kernel is the staged one
+    ctx->threads = 0;
     cudaError_t e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
@@ -810,13 +813,14 @@ int64_t lb_current_step(const lb_ctx* ctx) { return ctx ? ctx->step : -1; }
 int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas, int32_t sites_per_thread)
 {
     if (!ctx) return LB_ERR_ARG;
-    const int dv = default_vw(ctx->storage);
+    const int dv = kernel == LB_KERNEL_STAGED ? lbt_staged_default_spt(ctx->storage) : default_vw(ctx->storage);
     const int vw = sites_per_thread == 0 ? dv : sites_per_thread;
-    if (threads == 0) threads = 256;
     if (kernel == LB_KERNEL_STAGED) {
-        if (threads != 256 || vw != dv || ctas < 0)
-            return ctx->fail(LB_ERR_ARG, "staged kernel: threads and sites_per_thread 0 (fixed tiles), ctas >= 0");
+        if (threads != 0 || ctas < 0 || !lbt_staged_spt_ok(ctx->storage, vw))
+            return ctx->fail(LB_ERR_ARG, "staged kernel: threads 0, ctas >= 0, sites_per_thread 0, 1 or "
+                                         "(not FP64) 2");
     } else if (kernel == LB_KERNEL_REGISTER) {
+        if (threads == 0) threads = 256;
         const int v4 = dv / 4 > 0 ? dv / 4 : 1;
         if (threads < 64 || threads > 256 || threads % 32 || ctas < 0 || (vw != dv && vw != dv / 2 && vw != v4))
             return ctx->fail(LB_ERR_ARG, "register kernel: threads multiple of 32 in [64, 256]; ctas >= 0; "
@@ -871,16 +875,16 @@ const char* lb_last_error(const lb_ctx* ctx) { return ctx ? ctx->err.c_str() : g
 size_t lb_synth_workspace_bytes(int32_t M, int32_t E) { return sizeof(double2) * 3 * (size_t)M * (size_t)E; }
 
 int32_t lb_synth_faces(const double* kvec, const double* amp, const double* omega, const double* phi, int32_t M,
-                       int32_t E, int32_t K, int64_t j0, int64_t nsamp, int32_t out_dtype, void* out, void* workspace,
-                       void* stream)
+                       int32_t E, int32_t zoom, int32_t K, int64_t j0, int64_t nsamp, int32_t out_dtype, void* out,
+                       void* workspace, void* stream)
 {
     if (!kvec || !amp || !omega || !phi || !out || !workspace || M < 1 || E < 2 || K < 1 || nsamp < 0 ||
-        (out_dtype != LB_STORE_F64 && out_dtype != LB_STORE_F32)) {
+        zoom < 1 || (E - 1) % zoom || (out_dtype != LB_STORE_F64 && out_dtype != LB_STORE_F32)) {
         g_last_error = "lb_synth_faces: bad argument";
         return LB_ERR_ARG;
     }
-    cudaError_t e = launch_synth_faces(kvec, amp, omega, phi, M, E, K, j0, nsamp, out_dtype == LB_STORE_F64, out,
-                                       workspace, reinterpret_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_synth_faces(kvec, amp, omega, phi, M, E, zoom, K, j0, nsamp, out_dtype == LB_STORE_F64,
+                                       out, workspace, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         g_last_error = std::string("lb_synth_faces: ") + cudaGetErrorString(e);
         return e == cudaErrorInvalidValue ? LB_ERR_ARG : LB_ERR_CUDA;
@@ -889,15 +893,16 @@ int32_t lb_synth_faces(const double* kvec, const double* amp, const double* omeg
 }
 
 int32_t lb_synth_volume(const double* kvec, const double* amp, const double* omega, const double* phi, int32_t M,
-                        int32_t E, double t, int32_t out_dtype, void* out, void* workspace, void* stream)
+                        int32_t E, int32_t zoom, double t, int32_t out_dtype, void* out, void* workspace,
+                        void* stream)
 {
-    if (!kvec || !amp || !omega || !phi || !out || !workspace || M < 1 || E < 2 ||
+    if (!kvec || !amp || !omega || !phi || !out || !workspace || M < 1 || E < 2 || zoom < 1 || (E - 1) % zoom ||
         (out_dtype != LB_STORE_F64 && out_dtype != LB_STORE_F32)) {
         g_last_error = "lb_synth_volume: bad argument";
         return LB_ERR_ARG;
     }
-    cudaError_t e = launch_synth_volume(kvec, amp, omega, phi, M, E, t, out_dtype == LB_STORE_F64, out, workspace,
-                                        reinterpret_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_synth_volume(kvec, amp, omega, phi, M, E, zoom, t, out_dtype == LB_STORE_F64, out,
+                                        workspace, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
         g_last_error = std::string("lb_synth_volume: ") + cudaGetErrorString(e);
         return e == cudaErrorInvalidValue ? LB_ERR_ARG : LB_ERR_CUDA;

@@ -1,4 +1,4 @@
-// Device helpers: D3Q19 constants, population storage formats, Philox4x64-10.
+// Device helpers: D3Q19 constants, population storage formats, Philox4x32-10.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -117,20 +117,22 @@ __device__ __forceinline__ Raw zero_raw()
     return r;
 }
 
-// ---- Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11) ----------------------
-__device__ __forceinline__ void philox4x64_10(uint64_t x[4], uint64_t k0, uint64_t k1)
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ----------------------
+// 32-bit words throughout: the 32x32 multiplies run at the full integer rate,
+// while 64x64 products (a 64-bit variant) go through a much slower path.
+__device__ __forceinline__ void philox4x32_10(uint32_t x[4], uint32_t k0, uint32_t k1)
 {
-    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
-    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
 #pragma unroll
     for (int r = 0; r < 10; r++) {
         if (r > 0) {
             k0 += W0;
             k1 += W1;
         }
-        uint64_t hi0 = __umul64hi(M0, x[0]), lo0 = M0 * x[0];
-        uint64_t hi1 = __umul64hi(M1, x[2]), lo1 = M1 * x[2];
-        uint64_t y0 = hi1 ^ x[1] ^ k0, y2 = hi0 ^ x[3] ^ k1;
+        const uint32_t hi0 = __umulhi(M0, x[0]), lo0 = M0 * x[0];
+        const uint32_t hi1 = __umulhi(M1, x[2]), lo1 = M1 * x[2];
+        const uint32_t y0 = hi1 ^ x[1] ^ k0, y2 = hi0 ^ x[3] ^ k1;
         x[0] = y0;
         x[1] = lo1;
         x[2] = y2;
@@ -138,23 +140,21 @@ __device__ __forceinline__ void philox4x64_10(uint64_t x[4], uint64_t k0, uint64
     }
 }
 
-// Unit-variance uniform number on [-sqrt3, sqrt3) from the top 53 bits.
-__device__ __forceinline__ double unit_uniform(uint64_t v)
-{
-    double u01 = (double)(v >> 11) * (1.0 / 9007199254740992.0);
-    return sqrt(3.0) * (2.0 * u01 - 1.0);
-}
-
-// The same in the precision of the bead dynamics: FP64 from the top 53 bits,
+// Unit-variance uniform number on [-sqrt3, sqrt3) from a 32-bit word in the
+// precision of the bead dynamics: FP64 from all 32 bits (u = v 2^-32, exact),
 // FP32 from the top 24 bits (exact uniform grid, scaled by sqrt 3).
 template <class T>
-__device__ __forceinline__ T unit_uniform_t(uint64_t v);
+__device__ __forceinline__ T unit_uniform_t(uint32_t v);
 template <>
-__device__ __forceinline__ double unit_uniform_t<double>(uint64_t v) { return unit_uniform(v); }
-template <>
-__device__ __forceinline__ float unit_uniform_t<float>(uint64_t v)
+__device__ __forceinline__ double unit_uniform_t<double>(uint32_t v)
 {
-    const float u01 = (float)(uint32_t)(v >> 40) * (1.0f / 16777216.0f);  // 2^-24
+    const double u01 = (double)v * (1.0 / 4294967296.0);  // 2^-32
+    return sqrt(3.0) * (2.0 * u01 - 1.0);
+}
+template <>
+__device__ __forceinline__ float unit_uniform_t<float>(uint32_t v)
+{
+    const float u01 = (float)(v >> 8) * (1.0f / 16777216.0f);  // 2^-24
     return 1.7320508075688772f * (2.0f * u01 - 1.0f);
 }
 
@@ -207,14 +207,16 @@ __device__ __forceinline__ TimeWeights<R> time_weights(int64_t n, int K, int mod
     return tw;
 }
 
+// Substep s = n + 1 - jK (1 .. K) of the step n -> n + 1 within its coarse interval j.
+__device__ __forceinline__ int mlp_substep(int64_t n, int K) { return (int)(n + 1 - (n / K) * K); }
+
 // Learned residual of the boundary velocity (upsampler boxes): output row of
-// the face site, substep s = n + 1 - jK.
+// the face site, substep s.
 template <class R>
-__device__ __forceinline__ void add_mlp_residual(const SCParams& p, const BoxDev& bd, int64_t n, int f, int pp, int qq,
+__device__ __forceinline__ void add_mlp_residual(const SCParams& p, const BoxDev& bd, int s, int f, int pp, int qq,
                                                  R ub[3])
 {
     if (bd.mlp_row < 0) return;
-    const int s = (int)(n + 1 - (n / bd.K) * bd.K);
     const float* y = p.mlp_y + (bd.mlp_row + ((int64_t)f * bd.E + qq) * bd.E + pp) * p.mlp_nout + 3 * (s - 1);
     for (int c = 0; c < 3; c++) ub[c] += (R)(p.mlp_yunit * y[c]);
 }

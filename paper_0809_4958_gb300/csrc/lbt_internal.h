@@ -13,6 +13,7 @@ namespace lbt {
 constexpr int kQ = 19;
 constexpr int kRingSlots = 4;       // default ring: samples j-1 .. j+2 live in slots j mod ring_slots
 constexpr int kMaxRingSlots = 4096;
+constexpr int kForcedThreads = 128;  // block of the forced re-collision (one force entry per thread)
 constexpr int kMaxBeads = 256;      // beads per chain (one CTA per chain, one thread per bead)
 
 // One box as the kernels see it.
@@ -99,6 +100,9 @@ struct BeadParams {
     ForceEntry* forces;
     const int64_t* step;
     int32_t* status;
+    int32_t max_beads;    // largest chain of the launch (shared-memory strides)
+    int32_t noise_chunk;  // substeps whose noise is drawn at once
+    int32_t lanes;        // threads per bead in the MD substeps (power of two, 2 .. 8)
 };
 
 struct ForcedParams {
@@ -111,6 +115,7 @@ struct ForcedParams {
     int64_t* step;                // incremented once per step by block 0
     int64_t* tile_counter;        // reset to zero once per step by block 0
     int32_t nchains;
+    int32_t splits;               // blocks per chain (set by the launcher)
 };
 
 // Host-side launchers, one instantiation per storage type.
@@ -129,11 +134,13 @@ struct Launch {
 };
 
 // Generator launchers; workspace holds the per-axis phase table (3 M E double2).
+// Points: every zoom-th site, (E - 1)/zoom + 1 per axis.
 cudaError_t launch_synth_faces(const double* kvec, const double* amp, const double* omega, const double* phi,
-                               int M, int E, int K, int64_t j0, int64_t nsamp, int out_f64, void* out,
+                               int M, int E, int zoom, int K, int64_t j0, int64_t nsamp, int out_f64, void* out,
                                void* workspace, cudaStream_t s);
 cudaError_t launch_synth_volume(const double* kvec, const double* amp, const double* omega, const double* phi,
-                                int M, int E, double t, int out_f64, void* out, void* workspace, cudaStream_t s);
+                                int M, int E, int zoom, double t, int out_f64, void* out, void* workspace,
+                                cudaStream_t s);
 
 }  // namespace lbt
 
@@ -141,4 +148,6 @@ cudaError_t launch_synth_volume(const double* kvec, const double* amp, const dou
 void lbt_set_last_error(const char* msg);
 
 // Sites per tile of the staged stream-collide kernel for a storage format.
-int lbt_staged_tile_sites(int storage);
+int lbt_staged_tile_sites(int spt);               // sites per tile of the staged kernel
+bool lbt_staged_spt_ok(int storage, int spt);      // staged sites per consumer thread supported
+int lbt_staged_default_spt(int storage);

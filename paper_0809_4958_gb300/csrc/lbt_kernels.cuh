@@ -134,6 +134,7 @@ __device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, int
     }
     if (bmask) {
         const TimeWeights<R> tw = time_weights<R>(n, bd.K, bd.time_interp, p.ring_slots);
+        const int s_mlp = bd.mlp_row >= 0 ? mlp_substep(n, bd.K) : 0;
         const R* ring = reinterpret_cast<const R*>(p.ring);
 #pragma unroll
         for (int k = 0; k < VW; k++) {
@@ -143,7 +144,7 @@ __device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, int
                 const int f = owning_face(x, y, z, Ei, per, pp, qq);
                 R ub[3];
                 boundary_velocity<R>(ring, p.ring_slot_elems, bd.ring_off, Ei, f, pp, qq, tw, ub);
-                add_mlp_residual<R>(p, bd, n, f, pp, qq, ub);
+                add_mlp_residual<R>(p, bd, s_mlp, f, pp, qq, ub);
                 drho[k] = (A)bd.rho_b - A(1);
                 ux[k] = (A)ub[0];
                 uy[k] = (A)ub[1];
@@ -267,19 +268,32 @@ __device__ __forceinline__ void moments(const A f[kQ], A& drho, A j[3])
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void set_status(int32_t* st, int code) { atomicCAS(st, 0, code); }
 
-constexpr int kMaxNb = 48;              // Verlet neighbours per bead (a quarter per lane)
-constexpr int kNbPerLane = kMaxNb / 4;
+constexpr int kMaxNb = 48;              // Verlet neighbours per bead
 constexpr double kSkin = 0.3;           // Verlet skin (lattice units)
-constexpr int kNoiseChunk = 10;         // substeps whose noise is drawn at once
-constexpr int kBeadThreadsMax = 4 * kMaxBeads;
+constexpr int kNoiseChunk = 25;         // substeps whose noise is drawn at once
+constexpr int kBeadThreadsMax = 2 * kMaxBeads;  // 512: two MD lanes per bead at the largest chain
 
-// Dynamic shared memory of the bead kernel: positions relative to bead 0's
-// start-of-step position, double-buffered over substeps, and the noise of
-// one chunk of substeps.
+// Dynamic shared memory of the bead kernel for chains of at most maxb beads:
+// positions relative to bead 0's start-of-step position, double-buffered over
+// substeps, and the noise of one chunk of substeps.
 template <class MT>
-constexpr size_t bead_dyn_bytes()
+constexpr size_t bead_dyn_bytes(int maxb)
 {
-    return sizeof(MT) * (2 * 3 * kMaxBeads + 3 * kNoiseChunk * kMaxBeads);
+    return sizeof(MT) * (size_t)maxb * (2 * 3 + 3 * kNoiseChunk);
+}
+
+// Barrier over the first nthreads threads (whole warps) of the block with id
+// `id`, returning the OR of `v` over them.
+__device__ __forceinline__ bool bar_or(int id, int nthreads, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbarrier.cta.red.or.pred po, %2, %3, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
 }
 
 template <int ST>
@@ -304,14 +318,12 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     __shared__ MT sU[kMaxBeads][3];          // fluid velocity at each bead
     __shared__ MT sV[kMaxBeads][3];          // velocities
     __shared__ MT sP[kMaxBeads][3];          // momentum given to the fluid
-    __shared__ unsigned char sNb[kMaxBeads][4][kNbPerLane];
-    __shared__ unsigned char sNbN[kMaxBeads][4];
+    __shared__ unsigned char sNb[kMaxBeads][kMaxNb];
     __shared__ double sRc[3];
     __shared__ double sRed[2][kBeadThreadsMax / 32][3];
     __shared__ int sErr;
     extern __shared__ __align__(16) unsigned char bead_dyn[];
-    MT* sXbuf = reinterpret_cast<MT*>(bead_dyn);       // [2][kMaxBeads][3]
-    MT* sXi = sXbuf + 2 * 3 * kMaxBeads;               // [kNoiseChunk][N][3]
+    MT* sXbuf = reinterpret_cast<MT*>(bead_dyn);       // [2][max_beads][3], then the noise
 
     double* pos = p.pos + 3 * ch.bead_off;
     double* vel = p.vel + 3 * ch.bead_off;
@@ -379,140 +391,177 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     __syncthreads();
 
     // 3. MD substeps (symplectic Euler), fluid velocity frozen over the step.
-    //    Four lanes per bead: lane q holds coordinate q of the velocity, of the
-    //    displacement since the start of the step and of the momentum handed to
-    //    the fluid, and a quarter of the bead's WCA neighbours; the force is
-    //    summed over the four lanes by shuffles.  Positions inside the step are
-    //    start + displacement, relative to bead 0's start-of-step position;
-    //    the FP64 position is updated once at the end.  The noise of
-    //    kNoiseChunk substeps is drawn up front by all threads.
-    const int q = tid & 3, bead = tid >> 2;
+    //    L = p.lanes consecutive threads per bead (a power of two, 2 .. 8).
+    //    The force on a bead is a list of tasks -- the bond below, the bond
+    //    above, then its WCA neighbours -- dealt round-robin to its L lanes, so
+    //    the serial part of a substep is about one pair force; the lanes sum
+    //    the force by shuffles and all of them apply the same update (lane 0
+    //    publishes the position).  Velocity, displacement since the start of
+    //    the step and the momentum handed to the fluid stay in registers;
+    //    positions (start + displacement, relative to bead 0's start-of-step
+    //    position) are double-buffered in shared memory.  One named barrier
+    //    over the MD threads per substep publishes the new positions and ORs
+    //    the flags "some bead left half the Verlet skin" and "error".  The
+    //    noise of a chunk of substeps is drawn up front by every thread; the
+    //    FP64 position is updated once at the end.
+    {
+    const int maxb = p.max_beads;
+    const int L = p.lanes;
+    const int nmd = (N * L + 31) & ~31;  // MD threads: whole warps
+    const bool md = tid < nmd;
+    const int bead = tid / L, lane = tid - bead * L;
     const bool own = bead < N;
-    const bool comp = own && q < 3;
+    MT* sXi = sXbuf + 2 * 3 * maxb;  // [chunk][N][3]
     const MT dt = MT(1) / (MT)ch.n_md;
     const MT namp = ch.kT > 0.0 ? (MT)sqrt(2.0 * ch.kT * ch.zeta / (1.0 / ch.n_md)) : MT(0);
     const MT R02 = (MT)(ch.R0 * ch.R0), inv_R02 = MT(1) / R02, kf = (MT)ch.k_fene, zeta = (MT)ch.zeta;
-    const MT dtm = dt / (MT)ch.mass, fext = comp ? (MT)ch.f_ext[q] : MT(0);
+    const MT dtm = dt / (MT)ch.mass;
     const bool wca = ch.eps > 0.0;
     const MT sig2 = (MT)(ch.sigma * ch.sigma), rc2 = (MT)(cbrt(2.0) * ch.sigma * ch.sigma), e24 = (MT)(24.0 * ch.eps);
     const MT rl = (MT)(sqrt(cbrt(2.0)) * ch.sigma + kSkin), rl2 = rl * rl;  // WCA cut-off 2^(1/6) sigma + skin
     const MT half_skin2 = (MT)(0.25 * kSkin * kSkin);
-    const MT X0 = comp ? sXbuf[3 * bead + q] : MT(0);
-    const MT Uq = comp ? sU[bead][q] : MT(0);
-    MT Vq = comp ? sV[bead][q] : MT(0);
-    MT Dq = MT(0), Pq = MT(0), Xref = X0;
-    bool need_build = true;
-    for (int sub = 0; sub < ch.n_md; sub++) {
-        const MT* Xc = sXbuf + (sub & 1) * 3 * kMaxBeads;
-        MT* Xn = sXbuf + ((sub + 1) & 1) * 3 * kMaxBeads;
-        const int cs = sub % kNoiseChunk;
-        if (namp > MT(0) && cs == 0) {
-            const int nc = min(kNoiseChunk, ch.n_md - sub);
+    const int nb_cap = kMaxNb / L;  // neighbour slots of one lane
+    MT X0[3], U[3], V[3], D[3] = {0, 0, 0}, P[3] = {0, 0, 0}, Xref[3], fext[3];
+    for (int a = 0; a < 3; a++) {
+        X0[a] = own ? sXbuf[3 * bead + a] : MT(0);
+        U[a] = own ? sU[bead][a] : MT(0);
+        V[a] = own ? sV[bead][a] : MT(0);
+        fext[a] = lane == 0 ? (MT)ch.f_ext[a] : MT(0);
+        Xref[a] = X0[a];
+    }
+    // errors of substep s go to sErrP[s & 1]: a thread that has passed the
+    // barrier of substep s can write next only to the other word, so every MD
+    // thread reads the same value after that barrier and all stop together
+    __shared__ int sErrP[2];
+    if (tid < 2) sErrP[tid] = 0;
+    __syncthreads();
+    int nb = 0;             // Verlet neighbours held by this lane
+    bool rebuild = true;    // lists out of date
+    const int chunk = namp > MT(0) ? p.noise_chunk : ch.n_md;
+    for (int c0 = 0; c0 < ch.n_md; c0 += chunk) {
+        const int nc = min(chunk, ch.n_md - c0);
+        if (namp > MT(0)) {
+            __syncthreads();  // the previous chunk's noise is consumed
             for (int w = tid; w < nc * N; w += nthr) {
                 const int sb = w / N, bb = w - sb * N;
-                uint64_t x[4] = {(uint64_t)n, (uint64_t)(sub + sb), (uint64_t)bb, (uint64_t)b};
-                philox4x64_10(x, ch.seed, 0);
+                uint32_t x[4] = {(uint32_t)n, (uint32_t)(c0 + sb), (uint32_t)bb, (uint32_t)b};
+                philox4x32_10(x, (uint32_t)ch.seed, (uint32_t)(ch.seed >> 32));
                 for (int a = 0; a < 3; a++) sXi[(sb * N + bb) * 3 + a] = unit_uniform_t<MT>(x[a]);
             }
+            __syncthreads();
         }
-        // has any bead moved more than half the skin since the last list?
-        MT d2 = MT(0);
-        if (comp && !need_build) {
-            const MT d = Xc[3 * bead + q] - Xref;
-            d2 = d * d;
-        }
-        d2 += __shfl_xor_sync(0xffffffffu, d2, 1);
-        d2 += __shfl_xor_sync(0xffffffffu, d2, 2);
-        const bool rebuild = __syncthreads_or(own && d2 > half_skin2) || need_build;  // also orders Xn writes
-        if (sErr) break;
-        if (wca && rebuild) {
-            if (own) {
-                int cnt = 0;
-                for (int b2 = q; b2 < N; b2 += 4) {
-                    if (b2 == bead) continue;
-                    MT e2 = MT(0);
-                    for (int a = 0; a < 3; a++) {
-                        const MT d = Xc[3 * bead + a] - Xc[3 * b2 + a];
-                        e2 += d * d;
+        if (md) {
+            for (int sb = 0; sb < nc; sb++) {
+                const int sub = c0 + sb;
+                const MT* Xc = sXbuf + (sub & 1) * 3 * maxb;
+                MT* Xn = sXbuf + ((sub + 1) & 1) * 3 * maxb;
+                bool flag = false;
+                MT X[3];
+                for (int a = 0; a < 3; a++) X[a] = X0[a] + D[a];  // == Xc[3 bead + a]
+                if (wca && rebuild && own) {  // lane r scans partners r, r + L, ...
+                    nb = 0;
+                    for (int b2 = lane; b2 < N; b2 += L) {
+                        if (b2 == bead) continue;
+                        MT e2 = MT(0);
+                        for (int a = 0; a < 3; a++) {
+                            const MT d = X[a] - Xc[3 * b2 + a];
+                            e2 += d * d;
+                        }
+                        if (e2 < rl2) {
+                            if (nb < nb_cap) sNb[bead][lane * nb_cap + nb] = (unsigned char)b2;
+                            nb++;
+                        }
                     }
-                    if (e2 < rl2) {
-                        if (cnt < kNbPerLane) sNb[bead][q][cnt] = (unsigned char)b2;
-                        cnt++;
+                    if (nb > nb_cap) {  // more neighbours than the list holds
+                        sErrP[sub & 1] = LB_ERR_CHAIN;
+                        flag = true;
+                        nb = nb_cap;
                     }
+                    for (int a = 0; a < 3; a++) Xref[a] = X[a];
                 }
-                if (cnt > kNbPerLane) sErr = LB_ERR_CHAIN;  // more neighbours than the list holds
-                sNbN[bead][q] = (unsigned char)(cnt < kNbPerLane ? cnt : kNbPerLane);
-                if (comp) Xref = Xc[3 * bead + q];
-            }
-            need_build = false;
-        }
-        MT F[3] = {0, 0, 0};
-        if (own) {
-            if (q == 0 && bead > 0) {  // bond (bead-1, bead): force -k r / (1 - r^2/R0^2) on the upper bead
-                MT r[3], r2 = 0;
-                for (int a = 0; a < 3; a++) {
-                    r[a] = Xc[3 * bead + a] - Xc[3 * (bead - 1) + a];
-                    r2 += r[a] * r[a];
-                }
-                if (r2 >= R02) sErr = LB_ERR_FENE;
-                const MT fac = kf * recip(MT(1) - r2 * inv_R02);
-                for (int a = 0; a < 3; a++) F[a] -= fac * r[a];
-            }
-            if (q == 1 && bead + 1 < N) {  // bond (bead, bead+1): opposite force on the lower bead
-                MT r[3], r2 = 0;
-                for (int a = 0; a < 3; a++) {
-                    r[a] = Xc[3 * (bead + 1) + a] - Xc[3 * bead + a];
-                    r2 += r[a] * r[a];
-                }
-                if (r2 >= R02) sErr = LB_ERR_FENE;
-                const MT fac = kf * recip(MT(1) - r2 * inv_R02);
-                for (int a = 0; a < 3; a++) F[a] += fac * r[a];
-            }
-            if (wca) {  // WCA: 24 eps (2 (s/r)^12 - (s/r)^6) / r^2 along R_bead - R_partner
-                const int cnt = sNbN[bead][q];
-                for (int k = 0; k < cnt; k++) {
-                    const int b2 = sNb[bead][q][k];
-                    MT r[3], r2 = 0;
-                    for (int a = 0; a < 3; a++) {
-                        r[a] = Xc[3 * bead + a] - Xc[3 * b2 + a];
-                        r2 += r[a] * r[a];
+                rebuild = false;
+                MT F[3] = {fext[0], fext[1], fext[2]};
+                if (own) {
+                    if (lane == 0 && bead > 0) {  // bond (bead-1, bead): force -k r / (1 - r^2/R0^2) on the upper bead
+                        MT r[3], r2 = 0;
+                        for (int a = 0; a < 3; a++) {
+                            r[a] = X[a] - Xc[3 * (bead - 1) + a];
+                            r2 += r[a] * r[a];
+                        }
+                        if (r2 >= R02) {
+                            sErrP[sub & 1] = LB_ERR_FENE;
+                            flag = true;
+                        }
+                        const MT fac = kf * recip(MT(1) - r2 * inv_R02);
+                        for (int a = 0; a < 3; a++) F[a] -= fac * r[a];
                     }
-                    if (r2 < rc2) {
-                        const MT inv = recip(r2);
-                        const MT s2 = sig2 * inv, s6 = s2 * s2 * s2;
-                        const MT fac = e24 * (MT(2) * s6 * s6 - s6) * inv;
+                    if (lane == 1 % L && bead + 1 < N) {  // bond (bead, bead+1): the opposite force on the lower bead
+                        MT r[3], r2 = 0;
+                        for (int a = 0; a < 3; a++) {
+                            r[a] = Xc[3 * (bead + 1) + a] - X[a];
+                            r2 += r[a] * r[a];
+                        }
+                        if (r2 >= R02) {
+                            sErrP[sub & 1] = LB_ERR_FENE;
+                            flag = true;
+                        }
+                        const MT fac = kf * recip(MT(1) - r2 * inv_R02);
                         for (int a = 0; a < 3; a++) F[a] += fac * r[a];
                     }
+                    for (int k = 0; k < nb; k++) {  // WCA: 24 eps (2 (s/r)^12 - (s/r)^6) / r^2 along R_bead - R_partner
+                        const int b2 = sNb[bead][lane * nb_cap + k];
+                        MT r[3], r2 = 0;
+                        for (int a = 0; a < 3; a++) {
+                            r[a] = X[a] - Xc[3 * b2 + a];
+                            r2 += r[a] * r[a];
+                        }
+                        if (r2 < rc2) {
+                            const MT inv = recip(r2);
+                            const MT s2 = sig2 * inv, s6 = s2 * s2 * s2;
+                            const MT fac = e24 * (MT(2) * s6 * s6 - s6) * inv;
+                            for (int a = 0; a < 3; a++) F[a] += fac * r[a];
+                        }
+                    }
+                }
+                for (int o = 1; o < L; o <<= 1)  // every lane of an MD warp takes part; xor < L stays in the bead
+                    for (int a = 0; a < 3; a++) F[a] += __shfl_xor_sync(0xffffffffu, F[a], o);
+                if (own) {
+                    MT moved = MT(0);
+                    for (int a = 0; a < 3; a++) {
+                        const MT ffric = -zeta * (V[a] - U[a]);
+                        const MT fnoise = namp > MT(0) ? namp * sXi[(sb * N + bead) * 3 + a] : MT(0);
+                        V[a] += dtm * (F[a] + ffric + fnoise);
+                        D[a] += dt * V[a];
+                        P[a] -= (ffric + fnoise) * dt;
+                        const MT xn = X0[a] + D[a];
+                        if (lane == 0) Xn[3 * bead + a] = xn;
+                        const MT d = xn - Xref[a];
+                        moved += d * d;
+                    }
+                    if (wca && moved > half_skin2) flag = true;
+                }
+                // publish Xn; any flag: rebuild the lists, or stop on an error
+                if (bar_or(1, nmd, flag)) {
+                    if (sErrP[sub & 1]) break;
+                    rebuild = true;
                 }
             }
         }
-        for (int a = 0; a < 3; a++) {
-            F[a] += __shfl_xor_sync(0xffffffffu, F[a], 1);
-            F[a] += __shfl_xor_sync(0xffffffffu, F[a], 2);
-        }
-        if (comp) {
-            const MT Fq = q == 0 ? F[0] : (q == 1 ? F[1] : F[2]);
-            const MT ffric = -zeta * (Vq - Uq);
-            const MT fnoise = namp > MT(0) ? namp * sXi[(cs * N + bead) * 3 + q] : MT(0);
-            const MT ftot = Fq + ffric + fnoise + fext;
-            Vq += dtm * ftot;
-            Dq += dt * Vq;
-            Pq -= (ffric + fnoise) * dt;
-            Xn[3 * bead + q] = X0 + Dq;
-        }
-        if (namp > MT(0) && (sub + 1) % kNoiseChunk == 0) __syncthreads();  // noise chunk consumed
+        __syncthreads();
+        if (sErrP[0] || sErrP[1]) break;
     }
-    __syncthreads();
-    if (sErr) {
-        if (tid == 0) set_status(&p.status[b], sErr);
+    if (sErrP[0] || sErrP[1]) {
+        if (tid == 0) set_status(&p.status[b], sErrP[0] ? sErrP[0] : sErrP[1]);
         return;
     }
-    if (comp) {
-        sR[bead][q] += (double)Dq;
-        sV[bead][q] = Vq;
-        sP[bead][q] = Pq;
-    }
+    if (own && lane == 0)
+        for (int a = 0; a < 3; a++) {
+            sR[bead][a] += (double)D[a];
+            sV[bead][a] = V[a];
+            sP[bead][a] = P[a];
+        }
     __syncthreads();
+    }
 
     // 4. centre of mass pinned at the box centre (one thread per bead)
     double R[3] = {0, 0, 0}, V[3] = {0, 0, 0};
@@ -591,12 +640,13 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
 // advances the device step counter once all of its own work is done.
 // ---------------------------------------------------------------------------
 template <int ST>
-__global__ void __launch_bounds__(256) k_forced(ForcedParams p)
+__global__ void __launch_bounds__(kForcedThreads) k_forced(ForcedParams p)
 {
     using S = Stor<ST>;
     using A = typename S::A;
-    if ((int)blockIdx.x < p.nchains) {
-        const ChainDev& ch = p.chains[blockIdx.x];
+    const int chain = (int)blockIdx.x / p.splits, part = (int)blockIdx.x - chain * p.splits;
+    if (chain < p.nchains) {
+        const ChainDev& ch = p.chains[chain];
         const int b = ch.box;
         if (ch.nbeads > 0 && p.status[b] == 0) {
             const BoxDev& bd = p.boxes[b];
@@ -605,7 +655,7 @@ __global__ void __launch_bounds__(256) k_forced(ForcedParams p)
             const typename S::E* Ab = reinterpret_cast<const typename S::E*>(p.A) + bd.f_off;
             typename S::E* Bb = reinterpret_cast<typename S::E*>(p.B) + bd.f_off;
             const ForceEntry* fl = p.forces + ch.force_off;
-            for (int e = threadIdx.x; e < 8 * ch.nbeads; e += blockDim.x) {
+            for (int e = part * blockDim.x + threadIdx.x; e < 8 * ch.nbeads; e += p.splits * blockDim.x) {
                 const ForceEntry fe = fl[e];
                 if (fe.site < 0) continue;
                 const int x = fe.site % Ei, y = (fe.site / Ei) % Ei, z = fe.site / (Ei * Ei);
@@ -764,28 +814,37 @@ inline int grid_for(int64_t n, int threads, int cap = 152 * 16)
     return g < 1 ? 1 : (int)g;
 }
 
+template <int ST, int SPT>
+cudaError_t launch_staged(const SCParams& p, int ctas, cudaStream_t s)
+{
+    using G = Staged<ST, SPT>;
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_stream_collide_staged<ST, SPT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int sms = 0;
+    if (ctas <= 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    int64_t grid = ctas > 0 ? ctas : sms;
+    if (grid > p.total_tiles) grid = p.total_tiles;
+    if (grid < 1) return cudaSuccess;
+    k_stream_collide_staged<ST, SPT><<<(unsigned)grid, kStagedThreads, G::kSmemBytes, s>>>(p);
+    return cudaGetLastError();
+}
+
 template <int ST>
 cudaError_t Launch<ST>::stream_collide(const SCParams& p, int kernel, int threads, int ctas, int vw, cudaStream_t s)
 {
     if (kernel == LB_KERNEL_STAGED) {
-        static bool attr_set = false;  // per storage instantiation
-        if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(k_stream_collide_staged<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 Staged<ST>::kSmemBytes);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
-        int sms = 0;
-        if (ctas <= 0) {
-            int dev = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        }
-        int64_t grid = ctas > 0 ? ctas : sms;
-        if (grid > p.total_tiles) grid = p.total_tiles;
-        if (grid < 1) return cudaSuccess;
-        k_stream_collide_staged<ST><<<(unsigned)grid, kStagedThreads, Staged<ST>::kSmemBytes, s>>>(p);
-        return cudaGetLastError();
+        // vw: sites per consumer thread (1 or 2; FP64 1)
+        if (ST != kF64 && vw == 2) return launch_staged<ST, (ST == kF64 ? 1 : 2)>(p, ctas, s);
+        return launch_staged<ST, 1>(p, ctas, s);
     }
     int64_t grid = (ctas > 0 && ctas < p.total_tiles) ? ctas : p.total_tiles;
     if (grid < 1) return cudaSuccess;
@@ -804,23 +863,30 @@ cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, int max_be
 {
     if (nchains <= 0) return cudaSuccess;
     using MT = typename std::conditional<ST == kF64, double, float>::type;
-    const size_t dyn = bead_dyn_bytes<MT>();
-    static bool attr_set = false;
-    if (!attr_set) {
+    const size_t dyn = bead_dyn_bytes<MT>(max_beads);
+    static size_t attr_set = 0;  // largest dynamic size enabled so far
+    if (dyn > attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_bead_couple<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set = dyn;
     }
-    int threads = (4 * max_beads + 31) / 32 * 32;  // four lanes per bead
+    BeadParams q = p;
+    q.max_beads = max_beads;
+    q.noise_chunk = kNoiseChunk;
+    // lanes per bead in the MD phase: as many as keep the block at 512 threads, 2 .. 8
+    int lanes = 8;
+    while (lanes > 2 && lanes * max_beads > kBeadThreadsMax) lanes >>= 1;
+    q.lanes = lanes;
+    int threads = (lanes * max_beads + 31) / 32 * 32;
     if (threads < 64) threads = 64;
-    k_bead_couple<ST><<<nchains, threads, dyn, s>>>(p);
+    k_bead_couple<ST><<<nchains, threads, dyn, s>>>(q);
     return cudaGetLastError();
 }
 
 template <int ST>
 cudaError_t Launch<ST>::forced(const ForcedParams& p, cudaStream_t s)
 {
-    k_forced<ST><<<p.nchains > 0 ? p.nchains : 1, 256, 0, s>>>(p);
+    k_forced<ST><<<p.nchains > 0 ? p.nchains * p.splits : 1, kForcedThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -1,14 +1,20 @@
 // Stream-collide with the boundary layer, staged through shared memory by
-// TMA bulk copies (cp.async.bulk) in a two-stage pipeline.
+// TMA bulk copies (cp.async.bulk) in a warp-specialised pipeline.
 //
-// A tile is kStageSites consecutive sites of one box (4 KB of one population
-// row).  For population i the sites of a tile pull from one contiguous
-// source range shifted by c_iy E + c_iz E^2 (and by c_ix inside the row), so
-// one bulk copy per population, widened by a 16-byte halo on each side for
-// the x shift, brings everything the tile needs into shared memory; the x
-// shift becomes an offset into that row.  Each persistent block keeps the
-// copies for its next tile in flight while it computes the current one, so
-// DRAM sees a steady stream instead of load-compute-store bursts.
+// A tile is kSites consecutive sites of one box.  For population i the sites
+// of a tile pull from one contiguous source range shifted by c_iy E + c_iz E^2
+// (and by c_ix inside the row), so one bulk copy per population, widened by a
+// 16-byte halo on each side for the x shift, brings everything the tile needs
+// into shared memory; the x shift becomes an offset into that row.
+//
+// One producer warp claims tiles from a global counter and issues their 19
+// copies into a ring of stages; a "full" barrier per stage counts the bytes
+// landing, an "empty" barrier counts the consumer warps done with the stage.
+// Fifteen consumer warps take the stages in order.  A consumer warp loads its
+// sites' populations from the stage into registers and releases the stage at
+// once, then collides and stores straight to global memory, so the copies of
+// a later tile into that stage overlap the arithmetic and the stores of this
+// one.  No block-wide barrier is taken inside the loop.
 //
 // Only sites whose pull source crosses a periodic face (a wrap) read global
 // memory directly.  Copies are clamped to the box's arrays; sites whose
@@ -19,32 +25,35 @@
 
 namespace lbt {
 
-constexpr int kStagedThreads = 512;
-constexpr int kStagedHaloBytes = 16;                           // x-shift halo on each side
+constexpr int kStagedHaloBytes = 16;  // x-shift halo on each side of a row
+constexpr int kStagedConsumerWarps = 15;  // + the producer: four warps per scheduler
+constexpr int kStagedConsumers = kStagedConsumerWarps * 32;
+constexpr int kStagedThreads = kStagedConsumers + 32;  // + the producer warp
+constexpr int kStagedHeaderBytes = 1024;               // barriers and tile headers
+constexpr int kStagedMaxStages = 6;
 
-// Tile geometry: two stages of 4 KB rows.  (Four stages of 2 KB rows measured
-// slower on GB300: the cost per bulk copy and per tile grows faster than the
-// gain from the deeper pipeline.)
-template <int ST>
+// Tile geometry for SPT sites per consumer thread.  As many stages as fit in
+// the 227 KB of shared memory a block may use (at most six).
+template <int ST, int SPT>
 struct Staged {
     using E = typename Stor<ST>::E;
-    static constexpr int kRowBytes = 4096;                                  // one population row of a tile
-    static constexpr int kStages = 2;
+    static constexpr int kSites = kStagedConsumers * SPT;
+    static constexpr int kRowBytes = kSites * (int)sizeof(E);               // one population row of a tile
     static constexpr int kRowStride = kRowBytes + 2 * kStagedHaloBytes;
     static constexpr int kStageBytes = kQ * kRowStride;
-    static constexpr int kSmemBytes = kStages * kStageBytes + 64;          // + mbarriers
-    static constexpr int kSites = kRowBytes / (int)sizeof(E);              // sites per tile
-    static constexpr int kSPT = kSites / kStagedThreads;                   // sites per thread
-    static constexpr int kHalo = kStagedHaloBytes / (int)sizeof(E);        // halo elements
-    static_assert(kSPT >= 1, "tile smaller than the block");
+    static constexpr int kFit = (227 * 1024 - kStagedHeaderBytes) / kStageBytes;
+    static constexpr int kStages = kFit > kStagedMaxStages ? kStagedMaxStages : kFit;
+    static constexpr int kSmemBytes = kStagedHeaderBytes + kStages * kStageBytes;
+    static constexpr int kHalo = kStagedHaloBytes / (int)sizeof(E);         // halo elements
+    static_assert(kStages >= 2, "tile too large for a two-stage pipeline");
+    static_assert(kRowStride % 16 == 0, "bulk copies need 16-byte aligned rows");
 };
 
-// Sites per tile of the staged kernel (host side, for the tile table).
-inline int staged_tile_sites(int storage)
-{
-    return storage == kF64 ? Staged<kF64>::kSites
-                           : (storage == kF32 ? Staged<kF32>::kSites : Staged<kF16>::kSites);
-}
+// Sites per consumer thread the staged kernel supports per storage format
+// (the first is the default): FP64 1; FP32 2 or 1; 16-bit 2 or 1.
+inline bool staged_spt_ok(int storage, int spt) { return spt == 1 || (spt == 2 && storage != kF64); }
+inline int staged_default_spt(int storage) { return storage == kF64 ? 1 : 2; }
+inline int staged_tile_sites(int spt) { return kStagedConsumers * spt; }
 
 // ---- PTX helpers (mbarrier + bulk copy) ----
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -57,6 +66,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
 {
@@ -71,13 +85,16 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  : "memory");
 }
 
+// Test the phase; a thread that finds it incomplete may be suspended in
+// hardware for up to 20 us (or until the phase completes) instead of spinning
+// and taking issue slots from the warps that compute.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase)
 {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(phase)
+        : "r"(smem_u32(bar)), "r"(phase), "r"(20000u)
         : "memory");
     return ok != 0;
 }
@@ -110,16 +127,34 @@ __device__ __forceinline__ int locate_box(const SCParams& p, int64_t tile)
     return lo;
 }
 
+// Shared-memory header: full and empty barriers, then the tile header the
+// producer writes for each stage before it arms the barrier: box, first site,
+// and what the boundary layer of the box needs at this step -- the ring slots
+// and weights of the time interpolation and the upsampler substep -- so that
+// they are worked out (64-bit divisions) once per box, not once per warp.
+struct StagedTile {
+    int64_t s0;
+    int32_t box;
+    int32_t mlp_s;
+    int32_t slot[4];
+    double c[4];
+};
+struct StagedHeader {
+    uint64_t full[8];
+    uint64_t empty[8];
+    StagedTile t[8];
+};
+static_assert(sizeof(StagedHeader) <= kStagedHeaderBytes, "header does not fit");
+static_assert(kStagedMaxStages <= 8, "header holds eight stages");
+
 // Producer (one thread): bulk copies of the 19 source rows of a tile.
-template <int ST>
-__device__ __forceinline__ void issue_tile(const SCParams& p, int64_t tile, unsigned char* stage, uint64_t* bar)
+template <int ST, int SPT>
+__device__ __forceinline__ void issue_tile(const SCParams& p, const BoxDev& bd, int64_t s0, unsigned char* stage,
+                                           uint64_t* bar)
 {
     using E = typename Stor<ST>::E;
-    constexpr int T = Staged<ST>::kSites, H = Staged<ST>::kHalo;
-    const int b = locate_box(p, tile);
-    const BoxDev& bd = p.boxes[b];
+    constexpr int T = Staged<ST, SPT>::kSites, H = Staged<ST, SPT>::kHalo;
     const int64_t n3 = bd.n3, Ei = bd.E;
-    const int64_t s0 = (tile - p.tile_prefix[b]) * T;
     const E* Ab = reinterpret_cast<const E*>(p.A) + bd.f_off;
     int64_t lo[kQ], hi[kQ];
     uint32_t total = 0;
@@ -135,7 +170,7 @@ __device__ __forceinline__ void issue_tile(const SCParams& p, int64_t tile, unsi
     for (int i = 0; i < kQ; i++) {
         if (hi[i] <= lo[i]) continue;
         const int64_t start = s0 - (cvec(i, 1) * Ei + cvec(i, 2) * Ei * Ei) - H;
-        bulk_load(stage + i * Staged<ST>::kRowStride + (lo[i] - start) * sizeof(E), Ab + (int64_t)i * n3 + lo[i],
+        bulk_load(stage + i * Staged<ST, SPT>::kRowStride + (lo[i] - start) * sizeof(E), Ab + (int64_t)i * n3 + lo[i],
                   (uint32_t)((hi[i] - lo[i]) * sizeof(E)), bar);
     }
 }
@@ -144,18 +179,23 @@ __device__ __forceinline__ void issue_tile(const SCParams& p, int64_t tile, unsi
 // q = (s * m) >> 40 with m = ceil(2^40 / E), exact for s < 2^31 and E <= 1024.
 __device__ __forceinline__ int div_e(int64_t s, uint64_t m) { return (int)(((uint64_t)s * m) >> 40); }
 
-// Consumer: thread t collides sites t, t + kStagedThreads, ... of the tile,
-// so the lanes of a warp read consecutive shared-memory words (no bank
-// conflicts) and store consecutive global words.
-template <int ST, bool PER, bool ACCEL>
-__device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd, int64_t s0, int64_t n,
-                                            const unsigned char* stage)
+// Consumer thread c (0 .. 479) of one tile: sites s0 + c + k 480, so the lanes
+// of a warp read consecutive shared-memory words and store consecutive global
+// words.  Populations go to registers, the warp releases the stage, then the
+// collision (BGK with the equilibrium of opposite pairs shared: the even part
+// in c.u is common, the odd part changes sign) and the stores.
+template <int ST, int SPT, bool PER, bool ACCEL>
+__device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd, const StagedTile& th,
+                                            const unsigned char* stage, uint64_t* empty)
 {
     using S = Stor<ST>;
     using E = typename S::E;
     using A = typename S::A;
     using R = typename S::R;
-    constexpr int SPT = Staged<ST>::kSPT, H = Staged<ST>::kHalo;
+    constexpr int H = Staged<ST, SPT>::kHalo;
+    constexpr int C = kStagedConsumers;
+    const int tid = threadIdx.x;
+    const int64_t s0 = th.s0;
 
     const int Ei = bd.E;
     const int64_t n3 = bd.n3;
@@ -170,7 +210,7 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
     bool any_bnd = false;
 #pragma unroll
     for (int k = 0; k < SPT; k++) {
-        const int64_t s = s0 + threadIdx.x + k * kStagedThreads;
+        const int64_t s = s0 + tid + k * C;
         act[k] = s < n3;
         const int64_t sc = act[k] ? s : 0;
         const int row = div_e(sc, mE);
@@ -185,34 +225,39 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
         any_bnd |= bnd[k];
     }
 
-    // f_i pulled into site k: shared memory, or global memory across a periodic wrap
-    auto fval = [&](int i, int k) -> A {
+    // f_i pulled into site k: shared memory, or global memory across a periodic
+    // wrap; zero where it is not used (boundary and inactive sites)
+    A f[kQ][SPT];
+#pragma unroll
+    for (int i = 0; i < kQ; i++) {
         const int cx = cvec(i, 0), cy = cvec(i, 1), cz = cvec(i, 2);
-        if (PER) {
-            const int xs = xs_[k] - cx, ys = ys_[k] - cy, zs = zs_[k] - cz;
-            const bool wrap = (px && (xs < 0 || xs >= Ei)) || (py && (ys < 0 || ys >= Ei)) ||
-                              (pz && (zs < 0 || zs >= Ei));
-            if (wrap)
-                return S::in(Ab[(int64_t)i * n3 +
-                                ((int64_t)wrapi(zs, Ei) * Ei + wrapi(ys, Ei)) * Ei + wrapi(xs, Ei)]);
+        const E* row = reinterpret_cast<const E*>(stage + i * Staged<ST, SPT>::kRowStride);
+#pragma unroll
+        for (int k = 0; k < SPT; k++) {
+            A v = S::in(row[H + tid + k * C - cx]);
+            if (PER) {
+                const int xs = xs_[k] - cx, ys = ys_[k] - cy, zs = zs_[k] - cz;
+                const bool wrap = (px && (xs < 0 || xs >= Ei)) || (py && (ys < 0 || ys >= Ei)) ||
+                                  (pz && (zs < 0 || zs >= Ei));
+                if (wrap && act[k])
+                    v = S::in(Ab[(int64_t)i * n3 + ((int64_t)wrapi(zs, Ei) * Ei + wrapi(ys, Ei)) * Ei + wrapi(xs, Ei)]);
+            }
+            f[i][k] = (act[k] && !bnd[k]) ? v : A(0);
         }
-        const E* row = reinterpret_cast<const E*>(stage + i * Staged<ST>::kRowStride);
-        return S::in(row[H + threadIdx.x + k * kStagedThreads - cx]);
-    };
+    }
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(empty);  // this warp is done with the stage
 
     A drho[SPT], ux[SPT], uy[SPT], uz[SPT];
 #pragma unroll
     for (int k = 0; k < SPT; k++) {
         A r = A(0), jx = A(0), jy = A(0), jz = A(0);
-        if (act[k] && !bnd[k]) {
 #pragma unroll
-            for (int i = 0; i < kQ; i++) {
-                const A f = fval(i, k);
-                r += f;
-                if (cvec(i, 0)) jx += cvec(i, 0) * f;
-                if (cvec(i, 1)) jy += cvec(i, 1) * f;
-                if (cvec(i, 2)) jz += cvec(i, 2) * f;
-            }
+        for (int i = 0; i < kQ; i++) {
+            r += f[i][k];
+            if (cvec(i, 0)) jx += cvec(i, 0) * f[i][k];
+            if (cvec(i, 1)) jy += cvec(i, 1) * f[i][k];
+            if (cvec(i, 2)) jz += cvec(i, 2) * f[i][k];
         }
         const A rho = A(1) + r;
         const A inv = A(1) / rho;
@@ -227,16 +272,21 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
         uz[k] = jz * inv;
     }
     if (any_bnd) {
-        const TimeWeights<R> tw = time_weights<R>(n, bd.K, bd.time_interp, p.ring_slots);
+        TimeWeights<R> tw;
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            tw.slot[a] = th.slot[a];
+            tw.c[a] = (R)th.c[a];
+        }
         const R* ring = reinterpret_cast<const R*>(p.ring);
 #pragma unroll
         for (int k = 0; k < SPT; k++) {
             if (bnd[k]) {
                 int pp, qq;
-                const int f = owning_face(xs_[k], ys_[k], zs_[k], Ei, per, pp, qq);
+                const int fc = owning_face(xs_[k], ys_[k], zs_[k], Ei, per, pp, qq);
                 R ub[3];
-                boundary_velocity<R>(ring, p.ring_slot_elems, bd.ring_off, Ei, f, pp, qq, tw, ub);
-                add_mlp_residual<R>(p, bd, n, f, pp, qq, ub);
+                boundary_velocity<R>(ring, p.ring_slot_elems, bd.ring_off, Ei, fc, pp, qq, tw, ub);
+                add_mlp_residual<R>(p, bd, th.mlp_s, fc, pp, qq, ub);
                 drho[k] = (A)bd.rho_b - A(1);
                 ux[k] = (A)ub[0];
                 uy[k] = (A)ub[1];
@@ -245,104 +295,161 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
         }
     }
     const A om = A(1) / (A)bd.tau;
+    const A om1 = A(1) - om;
     const A srcfac = A(1) - A(0.5) * om;
-    A usq[SPT], ua[SPT];
+    A usq[SPT], rho_[SPT], ua[SPT];
 #pragma unroll
     for (int k = 0; k < SPT; k++) {
         usq[k] = A(1.5) * (ux[k] * ux[k] + uy[k] * uy[k] + uz[k] * uz[k]);
+        rho_[k] = A(1) + drho[k];
         if (ACCEL) ua[k] = ux[k] * (A)bd.accel[0] + uy[k] * (A)bd.accel[1] + uz[k] * (A)bd.accel[2];
     }
+    // post-collision value of population i at site k from its equilibrium deviation
+    auto emit = [&](int i, int k, A deq, A cu) {
+        A val = deq;
+        if (!bnd[k]) {
+            val = om1 * f[i][k] + om * deq;
+            if (ACCEL) {
+                const A w = wgt<A>(i);
+                const A ca = (A)(cvec(i, 0) * bd.accel[0] + cvec(i, 1) * bd.accel[1] + cvec(i, 2) * bd.accel[2]);
+                val += srcfac * w * rho_[k] * (A(3) * (ca - ua[k]) + A(9) * cu * ca);
+            }
+        }
+        if (act[k]) Bb[(int64_t)i * n3 + s0 + tid + k * C] = S::out(val);
+    };
 #pragma unroll
-    for (int i = 0; i < kQ; i++) {
+    for (int k = 0; k < SPT; k++) emit(0, k, wgt<A>(0) * (drho[k] - rho_[k] * usq[k]), A(0));
+    // opposite pairs (1,2), (3,4), ..., (17,18)
+#pragma unroll
+    for (int i = 1; i < kQ; i += 2) {
         const A w = wgt<A>(i);
         const int cx = cvec(i, 0), cy = cvec(i, 1), cz = cvec(i, 2);
 #pragma unroll
         for (int k = 0; k < SPT; k++) {
-            const A rho = A(1) + drho[k];
             A cu = A(0);
             if (cx) cu += cx * ux[k];
             if (cy) cu += cy * uy[k];
             if (cz) cu += cz * uz[k];
-            const A deq = w * (drho[k] + rho * (A(3) * cu + A(4.5) * cu * cu - usq[k]));
-            A val = deq;
-            if (!bnd[k]) {
-                const A f = fval(i, k);
-                val = f + om * (deq - f);
-                if (ACCEL) {
-                    const A ca = (A)(cx * bd.accel[0] + cy * bd.accel[1] + cz * bd.accel[2]);
-                    val += srcfac * w * rho * (A(3) * (ca - ua[k]) + A(9) * cu * ca);
-                }
-            }
-            if (act[k]) Bb[(int64_t)i * n3 + s0 + threadIdx.x + k * kStagedThreads] = S::out(val);
+            const A even = w * (drho[k] + rho_[k] * (A(4.5) * cu * cu - usq[k]));
+            const A odd = (A(3) * w) * rho_[k] * cu;
+            emit(i, k, even + odd, cu);
+            emit(i + 1, k, even - odd, -cu);
         }
     }
 }
 
-// Persistent blocks take tiles from a global counter (reset to zero by the
-// forced re-collision at the end of every step), so a block that starts late
-// -- its SM still busy with the bead kernel -- simply takes fewer tiles.
-template <int ST>
-__global__ void __launch_bounds__(kStagedThreads, 1) k_stream_collide_staged(SCParams p)
+// Consumer warps: take the stages in order until the producer posts the end.
+template <int ST, int SPT>
+__device__ __forceinline__ void staged_consume(const SCParams& p, unsigned char* smem, StagedHeader* hd)
 {
-    constexpr int kStagedStages = Staged<ST>::kStages;
-    constexpr int kStagedStageBytes = Staged<ST>::kStageBytes;
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kStagedStages * kStagedStageBytes);
-    __shared__ int64_t sTile[kStagedStages];
-    constexpr int T = Staged<ST>::kSites;
-    const int64_t n = *p.step;
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < kStagedStages; st++) mbar_init(&bar[st], 1);
-        fence_mbar_init();
-        for (int st = 0; st < kStagedStages; st++) {
-            const int64_t t = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(p.tile_counter), 1ull);
-            sTile[st] = t < p.total_tiles ? t : -1;
-            if (t < p.total_tiles) issue_tile<ST>(p, t, smem + st * kStagedStageBytes, &bar[st]);
-        }
-    }
-    __syncthreads();
+    using G = Staged<ST, SPT>;
+    using E = typename Stor<ST>::E;
     for (int k = 0;; k++) {
-        const int st = k % kStagedStages;
-        const int64_t tile = sTile[st];
-        if (tile < 0) break;  // later fetches are larger: nothing else is in flight
-        const uint32_t phase = (uint32_t)((k / kStagedStages) & 1);
-        const int b = locate_box(p, tile);
-        const BoxDev& bd = p.boxes[b];
-        const bool arrived = mbar_wait_bounded(&bar[st], phase);
-        if (!__syncthreads_and(arrived)) {
-            // the copies did not arrive within a second: flag the box, give the
-            // copies one more bounded wait, and leave (the whole block at once)
-            if (threadIdx.x == 0) atomicCAS(&p.status[b], 0, LB_ERR_TIMEOUT);
-            mbar_wait_bounded(&bar[st], phase);
+        const int st = k % G::kStages;
+        const uint32_t phase = (uint32_t)((k / G::kStages) & 1);
+        const bool arrived = mbar_wait_bounded(&hd->full[st], phase);
+        if (!__all_sync(0xffffffffu, arrived)) {
+            // nothing arrived within a second: flag the box, let copies still in
+            // flight land (one more bounded wait) and leave
+            if ((threadIdx.x & 31) == 0) {
+                const int b = hd->t[st].box;
+                atomicCAS(&p.status[b >= 0 && b < p.nboxes ? b : 0], 0, LB_ERR_TIMEOUT);
+            }
+            mbar_wait_bounded(&hd->full[st], phase);
             return;
         }
-        const int64_t s0 = (tile - p.tile_prefix[b]) * T;
-        const unsigned char* stage = smem + st * kStagedStageBytes;
+        const StagedTile& th = hd->t[st];
+        const int b = th.box;
+        if (b < 0) return;  // end of work
+        const int64_t s0 = th.s0;
+        const BoxDev& bd = p.boxes[b];
+        const unsigned char* stage = smem + kStagedHeaderBytes + st * G::kStageBytes;
         if (p.status[b] != 0) {
-            // frozen box: the state does not change
-            using E = typename Stor<ST>::E;
+            // frozen box: release the stage, the state does not change
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) mbar_arrive(&hd->empty[st]);
             const E* Ab = reinterpret_cast<const E*>(p.A) + bd.f_off;
             E* Bb = reinterpret_cast<E*>(p.B) + bd.f_off;
-            for (int t = threadIdx.x; t < T; t += blockDim.x)
+            for (int t = threadIdx.x; t < G::kSites; t += kStagedConsumers)
                 if (s0 + t < bd.n3)
                     for (int i = 0; i < kQ; i++) Bb[(int64_t)i * bd.n3 + s0 + t] = Ab[(int64_t)i * bd.n3 + s0 + t];
         } else if (bd.per_mask == 0) {
-            if (bd.has_accel) staged_tile<ST, false, true>(p, bd, s0, n, stage);
-            else staged_tile<ST, false, false>(p, bd, s0, n, stage);
+            if (bd.has_accel) staged_tile<ST, SPT, false, true>(p, bd, th, stage, &hd->empty[st]);
+            else staged_tile<ST, SPT, false, false>(p, bd, th, stage, &hd->empty[st]);
         } else {
-            if (bd.has_accel) staged_tile<ST, true, true>(p, bd, s0, n, stage);
-            else staged_tile<ST, true, false>(p, bd, s0, n, stage);
-        }
-        __syncthreads();  // every thread is done with this stage
-        if (threadIdx.x == 0) {
-            const int64_t t = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(p.tile_counter), 1ull);
-            sTile[st] = t < p.total_tiles ? t : -1;
-            if (t < p.total_tiles) {
-                fence_proxy_async_smem();
-                issue_tile<ST>(p, t, smem + st * kStagedStageBytes, &bar[st]);
-            }
+            if (bd.has_accel) staged_tile<ST, SPT, true, true>(p, bd, th, stage, &hd->empty[st]);
+            else staged_tile<ST, SPT, true, false>(p, bd, th, stage, &hd->empty[st]);
         }
     }
+}
+
+// Producer (lane 0 of the last warp): claim tiles from the global counter
+// (reset to zero by the forced re-collision at the end of every step, so a
+// block that starts late -- its SM still busy with the bead kernel -- simply
+// takes fewer tiles) and fill the stages as the consumers free them.
+template <int ST, int SPT>
+__device__ __forceinline__ void staged_produce(const SCParams& p, unsigned char* smem, StagedHeader* hd, int64_t n)
+{
+    using G = Staged<ST, SPT>;
+    using R = typename Stor<ST>::R;
+    unsigned long long* ctr = reinterpret_cast<unsigned long long*>(p.tile_counter);
+    int64_t next = (int64_t)atomicAdd(ctr, 1ull);
+    int last_b = -1;
+    TimeWeights<R> tw{};
+    int mlp_s = 0;
+    for (int k = 0;; k++) {
+        const int st = k % G::kStages;
+        // the stage's previous tile must be released by all consumer warps; if
+        // that does not happen within a second the consumers have left
+        if (k >= G::kStages && !mbar_wait_bounded(&hd->empty[st], (uint32_t)(((k / G::kStages) - 1) & 1))) return;
+        const int64_t t = next;
+        if (t >= p.total_tiles) {
+            hd->t[st].box = -1;
+            mbar_arrive(&hd->full[st]);  // completes the phase with no bytes: end of work
+            return;
+        }
+        next = (int64_t)atomicAdd(ctr, 1ull);  // the next claim overlaps this tile's copies
+        const int b = locate_box(p, t);
+        const BoxDev& bd = p.boxes[b];
+        const int64_t s0 = (t - p.tile_prefix[b]) * G::kSites;
+        if (b != last_b) {  // boundary-layer constants of this box at step n
+            tw = time_weights<R>(n, bd.K, bd.time_interp, p.ring_slots);
+            mlp_s = bd.mlp_row >= 0 ? mlp_substep(n, bd.K) : 0;
+            last_b = b;
+        }
+        StagedTile& th = hd->t[st];
+        th.box = b;
+        th.s0 = s0;
+        th.mlp_s = mlp_s;
+        for (int a = 0; a < 4; a++) {
+            th.slot[a] = tw.slot[a];
+            th.c[a] = (double)tw.c[a];
+        }
+        fence_proxy_async_smem();
+        issue_tile<ST, SPT>(p, bd, s0, smem + kStagedHeaderBytes + st * G::kStageBytes, &hd->full[st]);
+    }
+}
+
+template <int ST, int SPT>
+__global__ void __launch_bounds__(kStagedThreads, 1) k_stream_collide_staged(SCParams p)
+{
+    using G = Staged<ST, SPT>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    StagedHeader* hd = reinterpret_cast<StagedHeader*>(smem);
+    const int64_t n = *p.step;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < G::kStages; st++) {
+            mbar_init(&hd->full[st], 1);
+            mbar_init(&hd->empty[st], kStagedConsumerWarps);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x >= kStagedConsumers) {
+        if (threadIdx.x == kStagedConsumers) staged_produce<ST, SPT>(p, smem, hd, n);
+        return;
+    }
+    staged_consume<ST, SPT>(p, smem, hd);
 }
 
 }  // namespace lbt

@@ -37,12 +37,15 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b)
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// One block per (sample, face, chunk of face sites).  out[j][f][c][q][p].
+// One block per (sample, face, chunk of face points).  The points are the
+// coarse face grid: every z-th site, Ec = (E - 1)/z + 1 per side (every site
+// when z = 1).  out[j][f][c][Q][P].
 template <class R>
 __global__ void __launch_bounds__(kSynthThreads) k_synth_faces(const double2* T, const double* amp, const double* omega,
-                                                              const double* phi, int M, int E, int K, int64_t j0,
+                                                              const double* phi, int M, int E, int z, int K, int64_t j0,
                                                               int chunks_per_face, R* out)
 {
+    const int Ec = (E - 1) / z + 1;
     extern __shared__ double2 sC[];  // exp(i (omega t + phi)) * T[fixed axis][m][fixed coordinate]
     const int chunk = blockIdx.x % chunks_per_face;
     const int f = (blockIdx.x / chunks_per_face) % 6;
@@ -58,12 +61,12 @@ __global__ void __launch_bounds__(kSynthThreads) k_synth_faces(const double2* T,
         sC[m] = cmul(make_double2(c, s), T[((int64_t)fa * M + m) * E + fx]);
     }
     __syncthreads();
-    const int64_t fe = (int64_t)E * E;
+    const int64_t fe = (int64_t)Ec * Ec;
     const int64_t per_chunk = (fe + chunks_per_face - 1) / chunks_per_face;
     const int64_t s0 = chunk * per_chunk;
     const int64_t s1 = min(fe, s0 + per_chunk);
     for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-        const int p = (int)(s % E), q = (int)(s / E);
+        const int p = (int)(s % Ec) * z, q = (int)(s / Ec) * z;
         double u0 = 0, u1 = 0, u2 = 0;
         for (int m = 0; m < M; m++) {
             const double2 zp = T[((int64_t)ap * M + m) * E + p];
@@ -81,11 +84,13 @@ __global__ void __launch_bounds__(kSynthThreads) k_synth_faces(const double2* T,
     }
 }
 
-// Field on every site: out[c][z][y][x].
+// Field on the coarse grid (every zm-th site, Ec = (E - 1)/zm + 1 per axis):
+// out[c][Z][Y][X].
 template <class R>
 __global__ void __launch_bounds__(kSynthThreads) k_synth_volume(const double2* T, const double* amp, const double* omega,
-                                                               const double* phi, int M, int E, double t, R* out)
+                                                               const double* phi, int M, int E, int zm, double t, R* out)
 {
+    const int Ec = (E - 1) / zm + 1;
     extern __shared__ double2 sC[];
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
         double s, c;
@@ -93,9 +98,9 @@ __global__ void __launch_bounds__(kSynthThreads) k_synth_volume(const double2* T
         sC[m] = make_double2(c, s);
     }
     __syncthreads();
-    const int64_t n3 = (int64_t)E * E * E;
+    const int64_t n3 = (int64_t)Ec * Ec * Ec;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n3; s += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(s % E), y = (int)((s / E) % E), z = (int)(s / ((int64_t)E * E));
+        const int x = (int)(s % Ec) * zm, y = (int)((s / Ec) % Ec) * zm, z = (int)(s / ((int64_t)Ec * Ec)) * zm;
         double u0 = 0, u1 = 0, u2 = 0;
         for (int m = 0; m < M; m++) {
             const double2 w = cmul(cmul(sC[m], T[(int64_t)m * E + x]), T[((int64_t)M + m) * E + y]);
@@ -118,24 +123,25 @@ static int grid_for_synth(int64_t n)
 }
 
 cudaError_t launch_synth_faces(const double* kvec, const double* amp, const double* omega, const double* phi,
-                               int M, int E, int K, int64_t j0, int64_t nsamp, int out_f64, void* out,
+                               int M, int E, int zoom, int K, int64_t j0, int64_t nsamp, int out_f64, void* out,
                                void* workspace, cudaStream_t s)
 {
     if (M > kSynthMaxModes) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     double2* T = reinterpret_cast<double2*>(workspace);
     k_synth_axis<<<grid_for_synth(3LL * M * E), 256, 0, s>>>(kvec, M, E, T);
-    const int64_t fe = (int64_t)E * E;
+    const int Ec = (E - 1) / zoom + 1;
+    const int64_t fe = (int64_t)Ec * Ec;
     const int chunks = (int)((fe + 1023) / 1024);
     const size_t smem = sizeof(double2) * M;
     for (int64_t j = 0; j < nsamp; j += 4096) {
         const int64_t nj = min((int64_t)4096, nsamp - j);
         const unsigned grid = (unsigned)(nj * 6 * chunks);
         if (out_f64)
-            k_synth_faces<double><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, K, j0 + j, chunks,
+            k_synth_faces<double><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, zoom, K, j0 + j, chunks,
                                                                    reinterpret_cast<double*>(out) + j * 6 * 3 * fe);
         else
-            k_synth_faces<float><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, K, j0 + j, chunks,
+            k_synth_faces<float><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, zoom, K, j0 + j, chunks,
                                                                   reinterpret_cast<float*>(out) + j * 6 * 3 * fe);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -144,18 +150,22 @@ cudaError_t launch_synth_faces(const double* kvec, const double* amp, const doub
 }
 
 cudaError_t launch_synth_volume(const double* kvec, const double* amp, const double* omega, const double* phi,
-                                int M, int E, double t, int out_f64, void* out, void* workspace, cudaStream_t s)
+                                int M, int E, int zoom, double t, int out_f64, void* out, void* workspace,
+                                cudaStream_t s)
 {
     if (M > kSynthMaxModes) return cudaErrorInvalidValue;
     double2* T = reinterpret_cast<double2*>(workspace);
     k_synth_axis<<<grid_for_synth(3LL * M * E), 256, 0, s>>>(kvec, M, E, T);
-    const int64_t n3 = (int64_t)E * E * E;
+    const int Ec = (E - 1) / zoom + 1;
+    const int64_t n3 = (int64_t)Ec * Ec * Ec;
     const size_t smem = sizeof(double2) * M;
     const int grid = (int)min((int64_t)152 * 8, (n3 + kSynthThreads - 1) / kSynthThreads);
     if (out_f64)
-        k_synth_volume<double><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, t, reinterpret_cast<double*>(out));
+        k_synth_volume<double><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, zoom, t,
+                                                                 reinterpret_cast<double*>(out));
     else
-        k_synth_volume<float><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, t, reinterpret_cast<float*>(out));
+        k_synth_volume<float><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, zoom, t,
+                                                                reinterpret_cast<float*>(out));
     return cudaGetLastError();
 }
 
@@ -190,4 +200,6 @@ __global__ void k_cons_final(const BoxDev* boxes, const ChainDev* chains, int nb
 
 }  // namespace lbt
 
-int lbt_staged_tile_sites(int storage) { return lbt::staged_tile_sites(storage); }
+int lbt_staged_tile_sites(int spt) { return lbt::staged_tile_sites(spt); }
+bool lbt_staged_spt_ok(int storage, int spt) { return lbt::staged_spt_ok(storage, spt); }
+int lbt_staged_default_spt(int storage) { return lbt::staged_default_spt(storage); }

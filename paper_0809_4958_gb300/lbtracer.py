@@ -91,8 +91,8 @@ def load(path: str | None = None, build_if_missing: bool = True):
         "lb_profile_read": (_i32, [_vp, ctypes.POINTER(_f64), ctypes.POINTER(_i64)]),
         "lb_last_error": (ctypes.c_char_p, [_vp]),
         "lb_synth_workspace_bytes": (_sz, [_i32, _i32]),
-        "lb_synth_faces": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _i32, _i64, _i64, _i32, _vp, _vp, _vp]),
-        "lb_synth_volume": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _f64, _i32, _vp, _vp, _vp]),
+        "lb_synth_faces": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _i32, _i32, _i64, _i64, _i32, _vp, _vp, _vp]),
+        "lb_synth_volume": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, _i32, _f64, _i32, _vp, _vp, _vp]),
         "lb_population_sums_noalloc": (_i32, [_vp, _i32, _i32, _vp, _vp]),
         "lb_mlp_param_bytes": (_sz, [_i32]),
         "lb_mlp_bind": (_i32, [_vp, _vp, _f64]),
@@ -373,33 +373,42 @@ def modes_to_device(modes, device="cuda"):
                  for a in (modes.kvec, modes.amp, modes.omega, modes.phi))
 
 
-def synth_faces(modes, E, K, j0, nsamp, dtype, stream=None, out=None):
-    """Coarse face samples [nsamp][6][3][E][E] of the synthetic flow on the GPU."""
+def coarse_points(E, zoom=1):
+    """Points per axis of the coarse grid of a box with this zoom."""
+    return (E - 1) // zoom + 1 if zoom > 1 else E
+
+
+def synth_faces(modes, E, K, j0, nsamp, dtype, stream=None, out=None, zoom=1):
+    """Coarse face samples [nsamp][6][3][Ec][Ec] of the synthetic flow on the
+    GPU (every zoom-th site; Ec = E for zoom 1)."""
     torch = _torch()
     lib = load()
     stream = stream or torch.cuda.current_stream()
     kv, am, om, ph = modes_to_device(modes)
+    Ec = coarse_points(E, zoom)
     if out is None:
-        out = torch.empty((nsamp, 6, 3, E, E), dtype=dtype, device="cuda")
+        out = torch.empty((nsamp, 6, 3, Ec, Ec), dtype=dtype, device="cuda")
     ws = torch.empty(int(lib.lb_synth_workspace_bytes(modes.M, E)), dtype=torch.uint8, device="cuda")
     code = LB_STORE_F64 if dtype == torch.float64 else LB_STORE_F32
     with torch.cuda.stream(stream):
-        _check(lib.lb_synth_faces(kv.data_ptr(), am.data_ptr(), om.data_ptr(), ph.data_ptr(), modes.M, E, K, j0,
-                                  nsamp, code, out.data_ptr(), ws.data_ptr(), stream.cuda_stream))
+        _check(lib.lb_synth_faces(kv.data_ptr(), am.data_ptr(), om.data_ptr(), ph.data_ptr(), modes.M, E, zoom, K,
+                                  j0, nsamp, code, out.data_ptr(), ws.data_ptr(), stream.cuda_stream))
     stream.synchronize()
     return out
 
 
-def synth_volume(modes, E, t, dtype, stream=None):
-    """The synthetic flow on every site at time t: [3][E][E][E] on the GPU."""
+def synth_volume(modes, E, t, dtype, stream=None, zoom=1):
+    """The synthetic flow at time t on the coarse grid: [3][Ec][Ec][Ec] on the
+    GPU (every site for zoom 1)."""
     torch = _torch()
     lib = load()
     stream = stream or torch.cuda.current_stream()
     kv, am, om, ph = modes_to_device(modes)
-    out = torch.empty((3, E, E, E), dtype=dtype, device="cuda")
+    Ec = coarse_points(E, zoom)
+    out = torch.empty((3, Ec, Ec, Ec), dtype=dtype, device="cuda")
     ws = torch.empty(int(lib.lb_synth_workspace_bytes(modes.M, E)), dtype=torch.uint8, device="cuda")
     code = LB_STORE_F64 if dtype == torch.float64 else LB_STORE_F32
-    _check(lib.lb_synth_volume(kv.data_ptr(), am.data_ptr(), om.data_ptr(), ph.data_ptr(), modes.M, E, float(t),
-                               code, out.data_ptr(), ws.data_ptr(), stream.cuda_stream))
+    _check(lib.lb_synth_volume(kv.data_ptr(), am.data_ptr(), om.data_ptr(), ph.data_ptr(), modes.M, E, zoom,
+                               float(t), code, out.data_ptr(), ws.data_ptr(), stream.cuda_stream))
     stream.synchronize()
     return out

@@ -258,7 +258,8 @@ def test_launch_shapes_agree(lbt, storage, periodic):
     # are a few eps absolute; a 16-bit store can flip by one storage ulp
     tol = {ST64: 8 * 2.2e-16, ST32: 8 * 1.2e-7, 2: 2.0 ** -10 * scale, 3: 2.0 ** -7 * scale}[storage]
     S, Rg = lbt.LB_KERNEL_STAGED, lbt.LB_KERNEL_REGISTER
-    for kernel, threads, ctas, vw, exact in [(S, 0, 3, 0, True), (S, 0, 1, 0, True), (Rg, 256, 0, 0, False),
+    for kernel, threads, ctas, vw, exact in [(S, 0, 3, 0, True), (S, 0, 1, 0, True), (S, 0, 5, 1, storage == ST64),
+                                             (Rg, 256, 0, 0, False),
                                              (Rg, 128, 0, dv // 2, False), (Rg, 96, 7, dv, False),
                                              (Rg, 64, 152, max(dv // 4, 1), False)]:
         r = GpuRunner(lbt, torch, [c], storage)

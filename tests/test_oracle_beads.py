@@ -152,8 +152,8 @@ def test_noise_statistics(orc):
     n = 20000
     xs = []
     for i in range(n // 4):
-        r = orc.philox4x64_10([i, 3, 1, 0], [99, 0])
-        xs.extend(np.sqrt(3.0) * (2.0 * (r.astype(np.float64) / 2.0 ** 64) - 1.0))
+        r = orc.philox4x32_10([i, 3, 1, 0], [99, 0])
+        xs.extend(np.sqrt(3.0) * (2.0 * (r.astype(np.float64) / 2.0 ** 32) - 1.0))
     xs = np.array(xs)
     assert abs(xs.mean()) < 3 / np.sqrt(n)
     assert abs(xs.var() - 1) < 3 * np.sqrt(0.8 / n)
