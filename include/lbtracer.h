@@ -94,12 +94,26 @@ extern "C" {
 
 #define LB_ALL_BOXES (-1)
 
+/*
+ * Coarse grid (Sec. 3: the DNS grid spacing is z LB spacings).  Boundary
+ * samples and the initial field are given on a grid of Ec points per axis,
+ * point P at site P z, Ec = ceil((E - 1)/z) + 1 (Ec = E when z <= 1); when z
+ * does not divide E - 1 the last coarse cell reaches past the box.  A face
+ * sample holds the face plane (site 0 or E - 1 along the normal) at the
+ * coarse in-face points.  The boundary velocity of a face site is the
+ * bilinear interpolation, within the face, of the time-interpolated
+ * velocities at the four surrounding coarse points; the initial field is
+ * trilinear between the eight surrounding coarse points.  1 <= z <= E - 1;
+ * boxes with LB_TIME_MLP take z <= 1.
+ */
 typedef struct lb_box_desc {
     int32_t E;             /* sites per axis, multiple of 8 */
     int32_t face_mode[6];  /* LB_FACE_* per face, x-, x+, y-, y+, z-, z+ */
     int32_t time_interp;   /* LB_TIME_* */
     int32_t K;             /* LB steps per coarse sample interval, >= 1 */
     int32_t nbeads;        /* capacity for the chain of this box (0 = no chain), <= 256 */
+    int32_t zoom;          /* z = coarse grid spacing in sites (Sec. 3); 0 or 1: samples on every site */
+    int32_t reserved;      /* 0 */
     double tau;            /* BGK relaxation time, > 1/2 */
     double rho_b;          /* density of the boundary equilibrium (1.0) */
     double body_accel[3];  /* uniform body acceleration a; force density rho a (Guo forcing) */
@@ -153,7 +167,8 @@ int32_t lb_destroy(lb_ctx* ctx);
 /*
  * lb_init -- initial condition (Sec. 2): every site of the box gets the local
  * equilibrium with density 1 and velocity u0.
- *   u0: real [3][E^3], host or device.  A host array is staged through the
+ *   u0: real [3][Ec^3] on the coarse grid of the box ([3][E^3] for zoom <= 1),
+ *   host or device.  A host array is staged through the
  *   box's second population buffer.  A one-box context may be re-initialised
  *   at any time (step counter and boundary ring restart at 0); the boxes of a
  *   multi-box context are initialised before the first lb_step
@@ -165,8 +180,9 @@ int32_t lb_init(lb_ctx* ctx, int32_t box, const void* u0);
  * lb_set_boundary -- push coarse boundary sample j (taken at t = j K) into
  * the ring of the box (Sec. 3: boundary velocities interpolated in
  * time between the samples).
- *   face_u: real [6][3][E][E] for one box, or, with box == LB_ALL_BOXES, the
- *   arrays of all boxes back to back in box order; host or device.
+ *   face_u: real [6][3][Ec][Ec] for one box (the coarse face points; Ec = E
+ *   for zoom <= 1), or, with box == LB_ALL_BOXES, the arrays of all boxes back
+ *   to back in box order; host or device.
  *   Samples must be pushed in order 0, 1, 2, ...; sample j may be pushed
  *   once no step still to be enqueued needs sample j - ring_slots.
  *   The copy is enqueued on the context stream (pinned host memory keeps it
@@ -246,6 +262,14 @@ int64_t lb_current_step(const lb_ctx* ctx);
  *   Used by the autotuner.  Drops a captured graph. */
 int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas, int32_t sites_per_thread);
 
+/* lb_set_bead_launch -- threads per bead in the MD substeps of the bead
+ *   kernel (Sec. 1: the chain dynamics of the hybrid method): 0 = default
+ *   (4, halved until lanes x largest chain <= 512), or 1, 2, 4, 8 with
+ *   lanes x largest chain <= 512.  The lanes of a bead share its bond and
+ *   pair forces and sum them by shuffles.  Used by the autotuner; drops a
+ *   captured graph.  LB_ERR_ARG otherwise. */
+int32_t lb_set_bead_launch(lb_ctx* ctx, int32_t lanes);
+
 /*
  * lb_profile -- time every stream-collide launch with a pair of CUDA events
  * recorded on the context stream around it.  enable = 1 starts a new
@@ -272,11 +296,10 @@ const char* lb_last_error(const lb_ctx* ctx);
  * least lb_synth_workspace_bytes(M, E) bytes for the per-axis phase table.
  * Enqueued on `stream` (cudaStream_t); no synchronisation.
  *
- * Points: the coarse grid of a box with zoom z (every z-th site, from site 0
- * to site E - 1, Ec = (E - 1)/z + 1 per axis; every site for z = 1; E - 1
- * divisible by z).
+ * Points: the coarse grid of a box with zoom z, 1 <= z <= E - 1 (see the
+ * coarse-grid note above lb_box_desc; every site for z = 1).
  * lb_synth_faces: samples j0 .. j0+nsamp-1 at t = j K on the coarse points
- *   of the six faces, out [nsamp][6][3][Ec][Ec] (device).
+ *   of the six face planes, out [nsamp][6][3][Ec][Ec] (device).
  * lb_synth_volume: the field at time t on the coarse grid, out [3][Ec^3]
  *   (device).
  */

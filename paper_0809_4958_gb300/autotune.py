@@ -44,6 +44,34 @@ def _load_cache():
         return {}
 
 
+def tune_bead_lanes(tr, step, nsteps: int = 6):
+    """Lanes per bead of the bead kernel: the whole step is timed with CUDA
+    events on the context stream for every valid choice (the bead kernel runs
+    beside the stream-collide, so only the step shows its cost).  Returns the
+    choice applied to the context (0 when the context has no chain)."""
+    import torch
+    maxb = max(d.nbeads for d in tr.descs)
+    if maxb == 0:
+        return 0
+    best = None
+    for lanes in (1, 2, 4, 8):
+        if lanes * maxb > 512:
+            continue
+        tr.lb_set_bead_launch(lanes)
+        step(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(tr.stream)
+        step(nsteps)
+        e1.record(tr.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / nsteps
+        if best is None or ms < best[1]:
+            best = (lanes, ms)
+    tr.lb_set_bead_launch(best[0])
+    tr.bead_lanes = best[0]
+    return best[0]
+
+
 def tune(tr, step, steps_per_candidate: int = 6, use_cache: bool = True):
     """Pick the fastest stream-collide launch for context `tr`.
 
@@ -57,6 +85,7 @@ def tune(tr, step, steps_per_candidate: int = 6, use_cache: bool = True):
     if key in cache:
         choice = tuple(cache[key]["choice"])
         tr.lb_set_launch(*choice)
+        tr.lb_set_bead_launch(cache[key].get("bead_lanes", 0))
         return choice, cache[key].get("table", [])
     sms = torch.cuda.get_device_properties(tr.stream.device).multi_processor_count
     table = []
@@ -70,7 +99,8 @@ def tune(tr, step, steps_per_candidate: int = 6, use_cache: bool = True):
         table.append((cand, ms / max(n, 1)))
     choice = min(table, key=lambda t: t[1])[0]
     tr.lb_set_launch(*choice)
-    cache[key] = {"choice": list(choice), "table": [[list(c), t] for c, t in table]}
+    lanes = tune_bead_lanes(tr, step, steps_per_candidate)
+    cache[key] = {"choice": list(choice), "table": [[list(c), t] for c, t in table], "bead_lanes": lanes}
     try:
         with open(CACHE, "w") as f:
             json.dump(cache, f, indent=1)

@@ -4,6 +4,7 @@
 // coarse boundary samples, step ordering and launches.  All arithmetic of the
 // method runs in the kernels of lbt_kernels.cuh and lbt_synth.cu.
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -73,6 +74,12 @@ int validate_boxes(const lb_box_desc* boxes, int nboxes, int storage, std::strin
                     return LB_ERR_ARG;
                 }
         }
+        if (d.zoom < 0 || d.zoom > d.E - 1 || (d.zoom > 1 && d.time_interp == LB_TIME_MLP)) {
+            snprintf(buf, sizeof buf, "box %d: zoom %d must be in [0, E-1]; the upsampler needs zoom 0 or 1", b,
+                     d.zoom);
+            why = buf;
+            return LB_ERR_ARG;
+        }
         if (d.K < 1 || d.nbeads < 0 || d.nbeads > kMaxBeads || !(d.rho_b > 0.0)) {
             snprintf(buf, sizeof buf, "box %d: need K >= 1, 0 <= nbeads <= %d, rho_b > 0", b, kMaxBeads);
             why = buf;
@@ -98,7 +105,8 @@ Layout plan_layout(const lb_box_desc* boxes, int nboxes, int storage, int ring_s
     for (int b = 0; b < nboxes; b++) {
         const int64_t E = boxes[b].E, n3 = E * E * E;
         pop = align_up(pop + 19 * n3 * elem_bytes(storage));
-        ring += align_up(6 * 3 * E * E * real_bytes(storage)) / real_bytes(storage);
+        const int64_t Ec = coarse_points(boxes[b].E, boxes[b].zoom);
+        ring += align_up(6 * 3 * Ec * Ec * real_bytes(storage)) / real_bytes(storage);
         beads += boxes[b].nbeads;
         const int64_t c = (n3 + 4095) / 4096;
         if (c > chunks) chunks = c;
@@ -176,6 +184,8 @@ struct lb_ctx {
     std::vector<int64_t> pushed;       // last boundary sample pushed per box (-1 none)
     int kernel = LB_KERNEL_STAGED;
     int max_beads = 0;  // largest chain capacity of the context
+    int sms = 0;        // multiprocessors of the context's device
+    int bead_lanes = 0; // lanes per bead in the MD substeps (0 = default)
     int threads = 256, ctas = 0, vw = 0;  // vw: sites per thread in stream-collide
     std::vector<int64_t> tile_prefix;  // for the current block size
     cudaGraphExec_t graph = nullptr;
@@ -305,7 +315,7 @@ int enqueue_step(lb_ctx* ctx, int64_t n)
         bp.forces = ctx->at<ForceEntry>(ctx->L.forces);
         bp.step = ctx->at<int64_t>(ctx->L.step);
         bp.status = ctx->at<int32_t>(ctx->L.status);
-        CK(DISPATCH(ctx->storage, bead_couple(bp, nch, ctx->max_beads, ctx->side)));
+        CK(DISPATCH(ctx->storage, bead_couple(bp, nch, ctx->max_beads, ctx->bead_lanes, ctx->side)));
         CK(cudaEventRecord(ctx->ev_join, ctx->side));
     }
     SCParams sp;
@@ -319,6 +329,8 @@ int enqueue_step(lb_ctx* ctx, int64_t n)
     sp.mlp_yunit = (float)(ctx->mlp_umax / kMlpOutDiv);
     sp.boxes = ctx->at<BoxDev>(ctx->L.boxes);
     sp.tile_prefix = ctx->at<int64_t>(ctx->L.tile_prefix);
+    sp.general = 0;
+    for (const BoxDev& bd : ctx->boxes) sp.general |= (bd.per_mask != 0 || bd.has_accel) ? 1 : 0;
     sp.nboxes = ctx->nboxes;
     sp.total_tiles = ctx->tile_prefix[ctx->nboxes];
     sp.step = ctx->at<int64_t>(ctx->L.step);
@@ -330,7 +342,14 @@ int enqueue_step(lb_ctx* ctx, int64_t n)
     if (timed) CK(cudaStreamIsCapturing(ctx->stream, &cap));
     const unsigned evflags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (timed) CK(cudaEventRecordWithFlags(ctx->prof_ev[ctx->prof_used], ctx->stream, evflags));
-    CK(DISPATCH(ctx->storage, stream_collide(sp, ctx->kernel, ctx->threads, ctx->ctas, ctx->vw, ctx->stream)));
+    // The persistent stream-collide grid holds every SM (a block fills the
+    // register file), so a bead block launched next to it would wait for the
+    // whole sweep.  With few chains, leave one SM per chain to the bead kernel
+    // so it runs alongside; with many chains the atomic tile counter balances
+    // bead blocks and stream-collide blocks by itself.
+    int ctas = ctx->ctas;
+    if (ctas == 0 && ctx->kernel == LB_KERNEL_STAGED && nch > 0 && nch <= ctx->sms / 8) ctas = ctx->sms - nch;
+    CK(DISPATCH(ctx->storage, stream_collide(sp, ctx->kernel, ctx->threads, ctas, ctx->vw, ctx->stream)));
     if (timed) {
         CK(cudaEventRecordWithFlags(ctx->prof_ev[ctx->prof_used + 1], ctx->stream, evflags));
         ctx->prof_used += 2;
@@ -450,7 +469,10 @@ int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int
     ctx->pushed.assign(nboxes, -1);
     ctx->vw = lbt_staged_default_spt(storage);  // the default kernel is the staged one
     ctx->threads = 0;
-    cudaError_t e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -470,6 +492,8 @@ int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int
         bd.n3 = n3;
         bd.ring_off = (int64_t)ring;
         bd.E = d.E;
+        bd.zoom = d.zoom > 1 ? d.zoom : 1;
+        bd.Ec = coarse_points(d.E, bd.zoom);
         bd.div_magic = ((1ull << 40) + (uint64_t)d.E - 1) / (uint64_t)d.E;
         bd.mlp_row = -1;
         if (d.time_interp == LB_TIME_MLP) {
@@ -505,7 +529,8 @@ int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int
         }
         ctx->boxes.push_back(bd);
         pop = align_up(pop + 19 * n3 * elem_bytes(storage));
-        ring += align_up(6 * 3 * E * E * real_bytes(storage)) / real_bytes(storage);
+        const int64_t Ec = coarse_points(boxes[b].E, boxes[b].zoom);
+        ring += align_up(6 * 3 * Ec * Ec * real_bytes(storage)) / real_bytes(storage);
     }
     // zero the whole arena once (ring, status, step counter, force lists ...)
     e = cudaMemsetAsync(arena, 0, L.total, ctx->stream);
@@ -565,7 +590,7 @@ int32_t lb_init(lb_ctx* ctx, int32_t box, const void* u0)
     const void* src = u0;
     if (!is_device_ptr(u0)) {
         void* stage = reinterpret_cast<char*>(ctx->curB()) + bd.f_off * eb;
-        CK(cudaMemcpyAsync(stage, u0, 3 * bd.n3 * rb, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(stage, u0, 3 * (size_t)bd.Ec * bd.Ec * bd.Ec * rb, cudaMemcpyHostToDevice, ctx->stream));
         src = stage;
     }
     CK(DISPATCH(ctx->storage, init(A, ctx->boxes.data(), box, bd.n3, src, ctx->stream)));
@@ -608,7 +633,7 @@ int32_t lb_set_boundary(lb_ctx* ctx, int32_t box, int64_t j, const void* face_u)
     bool contiguous = true;
     for (int b = b0; b < b1 && contiguous; b++) {
         contiguous = (size_t)ctx->boxes[b].ring_off * rb == (size_t)ctx->boxes[b0].ring_off * rb + packed;
-        packed += 6 * 3 * (size_t)ctx->boxes[b].E * ctx->boxes[b].E * rb;
+        packed += 6 * 3 * (size_t)ctx->boxes[b].Ec * ctx->boxes[b].Ec * rb;
     }
     if (contiguous && b1 - b0 > 1) {
         CK(cudaMemcpyAsync(slot + ctx->boxes[b0].ring_off * rb, src, packed, cudaMemcpyDefault, ctx->stream));
@@ -616,8 +641,8 @@ int32_t lb_set_boundary(lb_ctx* ctx, int32_t box, int64_t j, const void* face_u)
         return LB_OK;
     }
     for (int b = b0; b < b1; b++) {
-        const int64_t E = ctx->boxes[b].E;
-        const size_t bytes = 6 * 3 * E * E * rb;
+        const int64_t Ec = ctx->boxes[b].Ec;
+        const size_t bytes = 6 * 3 * Ec * Ec * rb;
         CK(cudaMemcpyAsync(slot + ctx->boxes[b].ring_off * rb, src, bytes, cudaMemcpyDefault, ctx->stream));
         src += bytes;
         ctx->pushed[b] = j;
@@ -648,6 +673,29 @@ int32_t chain_couple(lb_ctx* ctx, int32_t box, const lb_chain_desc* d, const dou
     ch.sigma = d->sigma;
     for (int a = 0; a < 3; a++) ch.f_ext[a] = d->f_ext[a];
     ch.seed = d->seed;
+    {
+        const double dt = 1.0 / d->n_md, skin = kBeadSkin, rl = std::sqrt(std::cbrt(2.0)) * d->sigma + skin;
+        double* c = ch.md_d;
+        c[kMdDt] = dt;
+        c[kMdDtm] = dt / d->mass;
+        c[kMdNamp] = d->kT > 0.0 ? std::sqrt(2.0 * d->kT * d->zeta / dt) : 0.0;
+        c[kMdR02] = d->R0 * d->R0;
+        c[kMdInvR02] = 1.0 / (d->R0 * d->R0);
+        c[kMdKf] = d->k_fene;
+        c[kMdZeta] = d->zeta;
+        c[kMdSig2] = d->sigma * d->sigma;
+        c[kMdRc2] = std::cbrt(2.0) * d->sigma * d->sigma;
+        c[kMdE24] = 24.0 * d->eps;
+        c[kMdRl2] = rl * rl;
+        c[kMdHalfSkin2] = 0.25 * skin * skin;
+        for (int k = 0; k < kMdConsts; k++) ch.md_f[k] = (float)c[k];
+        // FP32 derived constants rounded from their own FP32 operands, as the
+        // device computed them before
+        ch.md_f[kMdDt] = 1.0f / (float)d->n_md;
+        ch.md_f[kMdDtm] = ch.md_f[kMdDt] / (float)d->mass;
+        ch.md_f[kMdInvR02] = 1.0f / ch.md_f[kMdR02];
+        ch.md_f[kMdRl2] = (float)rl * (float)rl;
+    }
     const size_t bytes = sizeof(double) * 3 * d->nbeads;
     CK(cudaMemcpyAsync(ctx->at<double>(ctx->L.pos) + 3 * ch.bead_off, pos0, bytes, cudaMemcpyDefault, ctx->stream));
     if (vel0)
@@ -839,6 +887,21 @@ int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas
     return rebuild_tiles(ctx);
 }
 
+int32_t lb_set_bead_launch(lb_ctx* ctx, int32_t lanes)
+{
+    if (!ctx) return LB_ERR_ARG;
+    if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
+        return ctx->fail(LB_ERR_ARG, "lb_set_bead_launch: lanes must be 0, 1, 2, 4 or 8");
+    if (lanes * ctx->max_beads > 512)
+        return ctx->fail(LB_ERR_ARG, "lb_set_bead_launch: lanes x largest chain must not exceed 512");
+    ctx->bead_lanes = lanes;
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    return LB_OK;
+}
+
 int32_t lb_profile(lb_ctx* ctx, int32_t enable, int32_t max_launches)
 {
     if (!ctx || max_launches < 0) return LB_ERR_ARG;
@@ -872,14 +935,18 @@ int32_t lb_profile_read(lb_ctx* ctx, double* total_ms, int64_t* launches)
 
 const char* lb_last_error(const lb_ctx* ctx) { return ctx ? ctx->err.c_str() : g_last_error.c_str(); }
 
-size_t lb_synth_workspace_bytes(int32_t M, int32_t E) { return sizeof(double2) * 3 * (size_t)M * (size_t)E; }
+size_t lb_synth_workspace_bytes(int32_t M, int32_t E)
+{
+    // phase table over 2E coordinates per axis: a zoomed coarse grid reaches at most E - 2 sites past the box
+    return sizeof(double2) * 3 * (size_t)M * (size_t)(2 * E);
+}
 
 int32_t lb_synth_faces(const double* kvec, const double* amp, const double* omega, const double* phi, int32_t M,
                        int32_t E, int32_t zoom, int32_t K, int64_t j0, int64_t nsamp, int32_t out_dtype, void* out,
                        void* workspace, void* stream)
 {
     if (!kvec || !amp || !omega || !phi || !out || !workspace || M < 1 || E < 2 || K < 1 || nsamp < 0 ||
-        zoom < 1 || (E - 1) % zoom || (out_dtype != LB_STORE_F64 && out_dtype != LB_STORE_F32)) {
+        zoom < 1 || zoom > E - 1 || (out_dtype != LB_STORE_F64 && out_dtype != LB_STORE_F32)) {
         g_last_error = "lb_synth_faces: bad argument";
         return LB_ERR_ARG;
     }
@@ -896,7 +963,7 @@ int32_t lb_synth_volume(const double* kvec, const double* amp, const double* ome
                         int32_t E, int32_t zoom, double t, int32_t out_dtype, void* out, void* workspace,
                         void* stream)
 {
-    if (!kvec || !amp || !omega || !phi || !out || !workspace || M < 1 || E < 2 || zoom < 1 || (E - 1) % zoom ||
+    if (!kvec || !amp || !omega || !phi || !out || !workspace || M < 1 || E < 2 || zoom < 1 || zoom > E - 1 ||
         (out_dtype != LB_STORE_F64 && out_dtype != LB_STORE_F32)) {
         g_last_error = "lb_synth_volume: bad argument";
         return LB_ERR_ARG;

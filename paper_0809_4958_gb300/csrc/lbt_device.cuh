@@ -158,10 +158,11 @@ __device__ __forceinline__ float unit_uniform_t<float>(uint32_t v)
     return 1.7320508075688772f * (2.0f * u01 - 1.0f);
 }
 
-// Reciprocal: correctly rounded division in FP64, the single-rounding
-// reciprocal instruction sequence in FP32.
+// Reciprocal of the bead pair forces: correctly rounded division in FP64,
+// the fast approximate division intrinsic in FP32 (a couple of ulp, far
+// below the FP32 dynamics' own rounding).
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 
 __device__ __forceinline__ int wrapi(int v, int E) { return v < 0 ? v + E : (v >= E ? v - E : v); }
 
@@ -234,13 +235,13 @@ __device__ __forceinline__ int owning_face(int x, int y, int z, int E, int per, 
     return 5;
 }
 
-// Boundary velocity of a site from the ring of coarse samples.
+// Time-interpolated velocity at coarse face point (P, Q) from the ring.
 template <class R>
-__device__ __forceinline__ void boundary_velocity(const R* ring, int64_t slot_elems, int64_t ring_off, int E,
-                                                  int f, int p, int q, const TimeWeights<R>& tw, R u[3])
+__device__ __forceinline__ void coarse_velocity(const R* ring, int64_t slot_elems, int64_t ring_off, int Ec, int f,
+                                                int P, int Q, const TimeWeights<R>& tw, R u[3])
 {
-    const int64_t fe = (int64_t)E * E;
-    const int64_t site = (int64_t)q * E + p;
+    const int64_t fe = (int64_t)Ec * Ec;
+    const int64_t site = (int64_t)Q * Ec + P;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         R acc = R(0);
@@ -252,6 +253,31 @@ __device__ __forceinline__ void boundary_velocity(const R* ring, int64_t slot_el
         }
         u[c] = acc;
     }
+}
+
+// Boundary velocity of face site (p, q): the ring holds the coarse face grid
+// (point P at site P z, Ec per side); with z > 1 the bilinear interpolation,
+// within the face, of the time-interpolated velocities at the four coarse
+// points around the site (Sec. 3: bilinear in space, interpolated in time).
+template <class R>
+__device__ __forceinline__ void boundary_velocity(const R* ring, int64_t slot_elems, const BoxDev& bd, int f, int p,
+                                                  int q, const TimeWeights<R>& tw, R u[3])
+{
+    const int z = bd.zoom, Ec = bd.Ec;
+    if (z == 1) {
+        coarse_velocity<R>(ring, slot_elems, bd.ring_off, Ec, f, p, q, tw, u);
+        return;
+    }
+    const int P0 = p / z, Q0 = q / z;
+    const int P1 = P0 + 1 < Ec ? P0 + 1 : P0, Q1 = Q0 + 1 < Ec ? Q0 + 1 : Q0;
+    const R fp = (R)(p - P0 * z) / (R)z, fq = (R)(q - Q0 * z) / (R)z;
+    R u00[3], u10[3], u01[3], u11[3];
+    coarse_velocity<R>(ring, slot_elems, bd.ring_off, Ec, f, P0, Q0, tw, u00);
+    coarse_velocity<R>(ring, slot_elems, bd.ring_off, Ec, f, P1, Q0, tw, u10);
+    coarse_velocity<R>(ring, slot_elems, bd.ring_off, Ec, f, P0, Q1, tw, u01);
+    coarse_velocity<R>(ring, slot_elems, bd.ring_off, Ec, f, P1, Q1, tw, u11);
+    for (int c = 0; c < 3; c++)
+        u[c] = (R(1) - fq) * ((R(1) - fp) * u00[c] + fp * u10[c]) + fq * ((R(1) - fp) * u01[c] + fp * u11[c]);
 }
 
 }  // namespace lbt

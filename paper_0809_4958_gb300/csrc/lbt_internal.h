@@ -13,6 +13,10 @@ namespace lbt {
 constexpr int kQ = 19;
 constexpr int kRingSlots = 4;       // default ring: samples j-1 .. j+2 live in slots j mod ring_slots
 constexpr int kMaxRingSlots = 4096;
+// Coarse points per axis of a box with zoom z: point P at site P z, enough
+// points to cover site E - 1 (every site when z = 1).
+__host__ __device__ inline int coarse_points(int E, int z) { return z > 1 ? (E - 1 + z - 1) / z + 1 : E; }
+
 constexpr int kForcedThreads = 128;  // block of the forced re-collision (one force entry per thread)
 constexpr int kMaxBeads = 256;      // beads per chain (one CTA per chain, one thread per bead)
 
@@ -27,11 +31,32 @@ struct BoxDev {
     int32_t K;
     int32_t chain;      // index into the chain table, -1 if none
     int32_t has_accel;
+    int32_t zoom;       // coarse grid spacing z in sites (1: samples on every site)
+    int32_t Ec;         // coarse points per axis: point P at site P z, covering site E - 1
     uint64_t div_magic; // ceil(2^40 / E): site / E = (site * div_magic) >> 40
     int64_t mlp_row;    // first row of the box in the upsampler output, -1 if the box does not use it
     double tau;
     double rho_b;
     double accel[3];
+};
+
+constexpr double kBeadSkin = 0.3;  // Verlet skin of the bead pair lists (lattice units)
+
+// Indices of the per-chain MD constants (ChainDev::md_d / md_f).
+enum MdConst {
+    kMdDt,        // 1 / n_md
+    kMdDtm,       // dt / mass
+    kMdNamp,      // noise amplitude sqrt(2 kT zeta / dt), 0 without noise
+    kMdR02,       // R0^2
+    kMdInvR02,    // 1 / R0^2
+    kMdKf,        // FENE k
+    kMdZeta,      // friction coefficient
+    kMdSig2,      // sigma^2
+    kMdRc2,       // WCA cut-off squared, 2^(1/3) sigma^2
+    kMdE24,       // 24 eps
+    kMdRl2,       // Verlet list radius squared, (2^(1/6) sigma + skin)^2
+    kMdHalfSkin2, // (skin / 2)^2
+    kMdConsts
 };
 
 // One chain (bead-spring polymer) as the bead kernel sees it.
@@ -46,6 +71,10 @@ struct ChainDev {
     double eps, sigma;  // WCA repulsion (eps = 0: FENE only)
     double f_ext[3];
     uint64_t seed;
+    // MD constants worked out once on the host (FP64 arithmetic is slow on
+    // the device), in FP64 and rounded to FP32 for the reduced-precision paths
+    double md_d[kMdConsts];
+    float md_f[kMdConsts];
 };
 
 // Force density at one lattice site, produced by the bead kernel, consumed by
@@ -84,6 +113,7 @@ struct SCParams {
     float mlp_yunit;              // velocity of one output unit (u_max / 64)
     const BoxDev* boxes;
     const int64_t* tile_prefix;   // [nboxes + 1] first tile of each box for the current block size
+    int32_t general;              // some box is periodic or carries a body force
     int32_t nboxes;
     int64_t total_tiles;
     const int64_t* step;          // device step counter n (state holds step n)
@@ -102,7 +132,7 @@ struct BeadParams {
     int32_t* status;
     int32_t max_beads;    // largest chain of the launch (shared-memory strides)
     int32_t noise_chunk;  // substeps whose noise is drawn at once
-    int32_t lanes;        // threads per bead in the MD substeps (power of two, 2 .. 8)
+    int32_t lanes;        // threads per bead in the MD substeps (1, 2, 4 or 8)
 };
 
 struct ForcedParams {
@@ -122,7 +152,7 @@ struct ForcedParams {
 template <int ST>
 struct Launch {
     static cudaError_t stream_collide(const SCParams& p, int kernel, int threads, int ctas, int vw, cudaStream_t s);
-    static cudaError_t bead_couple(const BeadParams& p, int nchains, int max_beads, cudaStream_t s);
+    static cudaError_t bead_couple(const BeadParams& p, int nchains, int max_beads, int lanes, cudaStream_t s);
     static cudaError_t forced(const ForcedParams& p, cudaStream_t s);
     static cudaError_t init(void* A, const BoxDev* boxes, int box, int64_t n3, const void* u0, cudaStream_t s);
     static cudaError_t fields(const void* A, const BoxDev* boxes, int box, int64_t n3, int what, void* dst,

@@ -143,7 +143,7 @@ __device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, int
                 const int x = xg * VW + k;
                 const int f = owning_face(x, y, z, Ei, per, pp, qq);
                 R ub[3];
-                boundary_velocity<R>(ring, p.ring_slot_elems, bd.ring_off, Ei, f, pp, qq, tw, ub);
+                boundary_velocity<R>(ring, p.ring_slot_elems, bd, f, pp, qq, tw, ub);
                 add_mlp_residual<R>(p, bd, s_mlp, f, pp, qq, ub);
                 drho[k] = (A)bd.rho_b - A(1);
                 ux[k] = (A)ub[0];
@@ -268,18 +268,41 @@ __device__ __forceinline__ void moments(const A f[kQ], A& drho, A j[3])
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void set_status(int32_t* st, int code) { atomicCAS(st, 0, code); }
 
-constexpr int kMaxNb = 48;              // Verlet neighbours per bead
-constexpr double kSkin = 0.3;           // Verlet skin (lattice units)
-constexpr int kNoiseChunk = 25;         // substeps whose noise is drawn at once
+constexpr int kMaxTasks = 48;           // pair tasks (bonds + Verlet neighbours) per bead
+constexpr int kNoiseChunk = 25;         // substeps whose noise is drawn at once (at most)
 constexpr int kBeadThreadsMax = 2 * kMaxBeads;  // 512: two MD lanes per bead at the largest chain
+constexpr size_t kBeadDynMax = 160 * 1024;      // dynamic shared memory budget of the bead kernel
 
-// Dynamic shared memory of the bead kernel for chains of at most maxb beads:
-// positions relative to bead 0's start-of-step position, double-buffered over
-// substeps, and the noise of one chunk of substeps.
 template <class MT>
-constexpr size_t bead_dyn_bytes(int maxb)
+struct Vec4;
+template <>
+struct Vec4<float> {
+    using T = float4;
+};
+template <>
+struct Vec4<double> {
+    struct __align__(32) T {
+        double x, y, z, w;
+    };
+};
+
+// Noise chunk of the bead kernel for chains of at most maxb beads: as many
+// substeps (at most kNoiseChunk) as fit the dynamic shared-memory budget next
+// to the two position buffers, all 4-vectors.
+template <class MT>
+inline int bead_noise_chunk(int maxb)
 {
-    return sizeof(MT) * (size_t)maxb * (2 * 3 + 3 * kNoiseChunk);
+    const size_t per = 4 * sizeof(MT) * (size_t)(maxb > 0 ? maxb : 1);
+    const int c = (int)(kBeadDynMax / per) - 2;
+    return c < kNoiseChunk ? (c < 1 ? 1 : c) : kNoiseChunk;
+}
+
+// Dynamic shared memory: positions relative to bead 0's start-of-step
+// position, double-buffered over substeps, and the noise of one chunk.
+template <class MT>
+inline size_t bead_dyn_bytes(int maxb)
+{
+    return 4 * sizeof(MT) * (size_t)maxb * (2 + bead_noise_chunk<MT>(maxb));
 }
 
 // Barrier over the first nthreads threads (whole warps) of the block with id
@@ -318,12 +341,12 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     __shared__ MT sU[kMaxBeads][3];          // fluid velocity at each bead
     __shared__ MT sV[kMaxBeads][3];          // velocities
     __shared__ MT sP[kMaxBeads][3];          // momentum given to the fluid
-    __shared__ unsigned char sNb[kMaxBeads][kMaxNb];
+    __shared__ unsigned char sNb[kMaxBeads][kMaxTasks];
     __shared__ double sRc[3];
     __shared__ double sRed[2][kBeadThreadsMax / 32][3];
     __shared__ int sErr;
-    extern __shared__ __align__(16) unsigned char bead_dyn[];
-    MT* sXbuf = reinterpret_cast<MT*>(bead_dyn);       // [2][max_beads][3], then the noise
+    extern __shared__ __align__(32) unsigned char bead_dyn[];
+    MT* sXbuf = reinterpret_cast<MT*>(bead_dyn);       // [2][max_beads] 4-vectors, then the noise
 
     double* pos = p.pos + 3 * ch.bead_off;
     double* vel = p.vel + 3 * ch.bead_off;
@@ -348,7 +371,7 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
             } else {
                 sBase[bb][a] = (int)(((i0 % Ei) + Ei) % Ei);
             }
-            sXbuf[3 * bb + a] = (MT)(R - sRc[a]);
+            sXbuf[4 * bb + a] = (MT)(R - sRc[a]);  // 4-vector layout of the MD phase
         }
     }
     __syncthreads();
@@ -391,51 +414,78 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     __syncthreads();
 
     // 3. MD substeps (symplectic Euler), fluid velocity frozen over the step.
-    //    L = p.lanes consecutive threads per bead (a power of two, 2 .. 8).
-    //    The force on a bead is a list of tasks -- the bond below, the bond
-    //    above, then its WCA neighbours -- dealt round-robin to its L lanes, so
-    //    the serial part of a substep is about one pair force; the lanes sum
-    //    the force by shuffles and all of them apply the same update (lane 0
-    //    publishes the position).  Velocity, displacement since the start of
-    //    the step and the momentum handed to the fluid stay in registers;
-    //    positions (start + displacement, relative to bead 0's start-of-step
-    //    position) are double-buffered in shared memory.  One named barrier
-    //    over the MD threads per substep publishes the new positions and ORs
-    //    the flags "some bead left half the Verlet skin" and "error".  The
-    //    noise of a chunk of substeps is drawn up front by every thread; the
-    //    FP64 position is updated once at the end.
+    //    L = p.lanes consecutive threads per bead (1, 2, 4 or 8).  Each lane
+    //    owns a list of pair tasks of its bead in shared memory -- lane 0 the
+    //    bond to bead - 1, lane 1 (lane 0 when L = 1) the bond to bead + 1,
+    //    then the WCA neighbours it found -- so the serial part of a substep is
+    //    about one pair force; the lanes sum the force by shuffles and all of
+    //    them apply the same update (lane 0 publishes the position).  Velocity,
+    //    displacement since the start of the step and the momentum handed to
+    //    the fluid stay in registers; positions (start + displacement,
+    //    relative to bead 0's start-of-step position) are double-buffered in
+    //    shared memory as 4-vectors, one 16- or 32-byte load per partner.  One
+    //    named barrier over the MD threads per substep publishes the new
+    //    positions and ORs the flags "some bead left half the Verlet skin" and
+    //    "error".  The noise of a chunk of substeps is drawn up front by every
+    //    thread; the FP64 position is updated once at the end.
     {
+    using V4 = typename Vec4<MT>::T;
     const int maxb = p.max_beads;
-    const int L = p.lanes;
+    const int L = p.lanes, lshift = __ffs(L) - 1;
     const int nmd = (N * L + 31) & ~31;  // MD threads: whole warps
     const bool md = tid < nmd;
-    const int bead = tid / L, lane = tid - bead * L;
+    const int bead = tid >> lshift, lane = tid & (L - 1);
     const bool own = bead < N;
-    MT* sXi = sXbuf + 2 * 3 * maxb;  // [chunk][N][3]
-    const MT dt = MT(1) / (MT)ch.n_md;
-    const MT namp = ch.kT > 0.0 ? (MT)sqrt(2.0 * ch.kT * ch.zeta / (1.0 / ch.n_md)) : MT(0);
-    const MT R02 = (MT)(ch.R0 * ch.R0), inv_R02 = MT(1) / R02, kf = (MT)ch.k_fene, zeta = (MT)ch.zeta;
-    const MT dtm = dt / (MT)ch.mass;
+    V4* sX4 = reinterpret_cast<V4*>(sXbuf);  // [2][maxb] positions
+    V4* sXi = sX4 + 2 * maxb;                // [chunk][N] noise
+    // constants from the chain record (worked out on the host in FP64)
+    const MT* mc;
+    if constexpr (sizeof(MT) == 8) mc = reinterpret_cast<const MT*>(ch.md_d);
+    else mc = reinterpret_cast<const MT*>(ch.md_f);
+    const MT dt = mc[kMdDt], dtm = mc[kMdDtm], namp = mc[kMdNamp];
+    const MT R02 = mc[kMdR02], inv_R02 = mc[kMdInvR02], kf = mc[kMdKf], zeta = mc[kMdZeta];
     const bool wca = ch.eps > 0.0;
-    const MT sig2 = (MT)(ch.sigma * ch.sigma), rc2 = (MT)(cbrt(2.0) * ch.sigma * ch.sigma), e24 = (MT)(24.0 * ch.eps);
-    const MT rl = (MT)(sqrt(cbrt(2.0)) * ch.sigma + kSkin), rl2 = rl * rl;  // WCA cut-off 2^(1/6) sigma + skin
-    const MT half_skin2 = (MT)(0.25 * kSkin * kSkin);
-    const int nb_cap = kMaxNb / L;  // neighbour slots of one lane
+    const MT sig2 = mc[kMdSig2], rc2 = mc[kMdRc2], e24 = mc[kMdE24];
+    const MT rl2 = mc[kMdRl2];  // Verlet radius: WCA cut-off 2^(1/6) sigma + skin
+    const MT half_skin2 = mc[kMdHalfSkin2];
+    const int cap = kMaxTasks / L;  // task slots of one lane
+    unsigned char* tasks = &sNb[bead < kMaxBeads ? bead : 0][lane * cap];
     MT X0[3], U[3], V[3], D[3] = {0, 0, 0}, P[3] = {0, 0, 0}, Xref[3], fext[3];
+    {
+        const V4 x0 = own ? sX4[bead] : V4{};
+        X0[0] = x0.x;
+        X0[1] = x0.y;
+        X0[2] = x0.z;
+    }
     for (int a = 0; a < 3; a++) {
-        X0[a] = own ? sXbuf[3 * bead + a] : MT(0);
         U[a] = own ? sU[bead][a] : MT(0);
         V[a] = own ? sV[bead][a] : MT(0);
         fext[a] = lane == 0 ? (MT)ch.f_ext[a] : MT(0);
         Xref[a] = X0[a];
     }
+    // this lane's bond (FENE) tasks, first in its list: lane 0 the bond to
+    // bead - 1, lane 1 the bond to bead + 1; a single lane holds both
+    int bondA = -1, bondB = -1;
+    if (L == 1) {
+        if (bead > 0) bondA = bead - 1;
+        if (bead + 1 < N) bondB = bead + 1;
+    } else if (lane == 0 && bead > 0) {
+        bondA = bead - 1;
+    } else if (lane == 1 && bead + 1 < N) {
+        bondA = bead + 1;
+    }
+    if (bondA < 0) {
+        bondA = bondB;
+        bondB = -1;
+    }
+    const int nfene = (bondA >= 0 ? 1 : 0) + (bondB >= 0 ? 1 : 0);
     // errors of substep s go to sErrP[s & 1]: a thread that has passed the
     // barrier of substep s can write next only to the other word, so every MD
     // thread reads the same value after that barrier and all stop together
     __shared__ int sErrP[2];
     if (tid < 2) sErrP[tid] = 0;
     __syncthreads();
-    int nb = 0;             // Verlet neighbours held by this lane
+    int ntask = nfene;      // tasks of this lane: its bonds, then its WCA neighbours
     bool rebuild = true;    // lists out of date
     const int chunk = namp > MT(0) ? p.noise_chunk : ch.n_md;
     for (int c0 = 0; c0 < ch.n_md; c0 += chunk) {
@@ -446,97 +496,92 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
                 const int sb = w / N, bb = w - sb * N;
                 uint32_t x[4] = {(uint32_t)n, (uint32_t)(c0 + sb), (uint32_t)bb, (uint32_t)b};
                 philox4x32_10(x, (uint32_t)ch.seed, (uint32_t)(ch.seed >> 32));
-                for (int a = 0; a < 3; a++) sXi[(sb * N + bb) * 3 + a] = unit_uniform_t<MT>(x[a]);
+                V4 xi;
+                xi.x = unit_uniform_t<MT>(x[0]);
+                xi.y = unit_uniform_t<MT>(x[1]);
+                xi.z = unit_uniform_t<MT>(x[2]);
+                xi.w = MT(0);
+                sXi[sb * N + bb] = xi;
             }
             __syncthreads();
         }
         if (md) {
             for (int sb = 0; sb < nc; sb++) {
                 const int sub = c0 + sb;
-                const MT* Xc = sXbuf + (sub & 1) * 3 * maxb;
-                MT* Xn = sXbuf + ((sub + 1) & 1) * 3 * maxb;
+                const V4* Xc = sX4 + (sub & 1) * maxb;
+                V4* Xn = sX4 + ((sub + 1) & 1) * maxb;
                 bool flag = false;
                 MT X[3];
-                for (int a = 0; a < 3; a++) X[a] = X0[a] + D[a];  // == Xc[3 bead + a]
-                if (wca && rebuild && own) {  // lane r scans partners r, r + L, ...
-                    nb = 0;
-                    for (int b2 = lane; b2 < N; b2 += L) {
-                        if (b2 == bead) continue;
-                        MT e2 = MT(0);
-                        for (int a = 0; a < 3; a++) {
-                            const MT d = X[a] - Xc[3 * b2 + a];
-                            e2 += d * d;
+                for (int a = 0; a < 3; a++) X[a] = X0[a] + D[a];  // == Xc[bead]
+                if (rebuild && own) {  // lane r scans partners r, r + L, ... after its bonds
+                    ntask = 0;
+                    if (bondA >= 0) tasks[ntask++] = (unsigned char)bondA;
+                    if (bondB >= 0) tasks[ntask++] = (unsigned char)bondB;
+                    int found = 0;
+                    if (wca)
+                        for (int b2 = lane; b2 < N; b2 += L) {
+                            if (b2 == bead) continue;
+                            const V4 q = Xc[b2];
+                            const MT dx = X[0] - q.x, dy = X[1] - q.y, dz = X[2] - q.z;
+                            if (dx * dx + dy * dy + dz * dz < rl2) {
+                                if (ntask < cap) tasks[ntask++] = (unsigned char)b2;
+                                found++;
+                            }
                         }
-                        if (e2 < rl2) {
-                            if (nb < nb_cap) sNb[bead][lane * nb_cap + nb] = (unsigned char)b2;
-                            nb++;
-                        }
-                    }
-                    if (nb > nb_cap) {  // more neighbours than the list holds
+                    if (nfene + found > cap) {  // more neighbours than the list holds
                         sErrP[sub & 1] = LB_ERR_CHAIN;
                         flag = true;
-                        nb = nb_cap;
                     }
                     for (int a = 0; a < 3; a++) Xref[a] = X[a];
                 }
                 rebuild = false;
+                // pair forces, one code path for both laws, force on this bead
+                // = fac (X - X_partner):
+                //   FENE: fac = -k / (1 - r^2/R0^2)
+                //   WCA:  fac = 24 eps (2 (s/r)^12 - (s/r)^6) / r^2, r < 2^(1/6) s
+                // Both beads of a pair evaluate the same r^2 from exactly
+                // negated differences, so the two forces cancel exactly.
                 MT F[3] = {fext[0], fext[1], fext[2]};
-                if (own) {
-                    if (lane == 0 && bead > 0) {  // bond (bead-1, bead): force -k r / (1 - r^2/R0^2) on the upper bead
-                        MT r[3], r2 = 0;
-                        for (int a = 0; a < 3; a++) {
-                            r[a] = X[a] - Xc[3 * (bead - 1) + a];
-                            r2 += r[a] * r[a];
-                        }
-                        if (r2 >= R02) {
+                if (own)
+                    for (int k = 0; k < ntask; k++) {
+                        const bool fene = k < nfene;
+                        const V4 q = Xc[tasks[k]];
+                        const MT rx = X[0] - q.x, ry = X[1] - q.y, rz = X[2] - q.z;
+                        const MT r2 = rx * rx + ry * ry + rz * rz;
+                        if (fene && r2 >= R02) {
                             sErrP[sub & 1] = LB_ERR_FENE;
                             flag = true;
                         }
-                        const MT fac = kf * recip(MT(1) - r2 * inv_R02);
-                        for (int a = 0; a < 3; a++) F[a] -= fac * r[a];
+                        const MT inv = recip(fene ? MT(1) - r2 * inv_R02 : r2);
+                        const MT s2 = sig2 * inv, s6 = s2 * s2 * s2;
+                        const MT fac = fene ? -kf * inv : (r2 < rc2 ? e24 * (MT(2) * s6 * s6 - s6) * inv : MT(0));
+                        F[0] += fac * rx;
+                        F[1] += fac * ry;
+                        F[2] += fac * rz;
                     }
-                    if (lane == 1 % L && bead + 1 < N) {  // bond (bead, bead+1): the opposite force on the lower bead
-                        MT r[3], r2 = 0;
-                        for (int a = 0; a < 3; a++) {
-                            r[a] = Xc[3 * (bead + 1) + a] - X[a];
-                            r2 += r[a] * r[a];
-                        }
-                        if (r2 >= R02) {
-                            sErrP[sub & 1] = LB_ERR_FENE;
-                            flag = true;
-                        }
-                        const MT fac = kf * recip(MT(1) - r2 * inv_R02);
-                        for (int a = 0; a < 3; a++) F[a] += fac * r[a];
-                    }
-                    for (int k = 0; k < nb; k++) {  // WCA: 24 eps (2 (s/r)^12 - (s/r)^6) / r^2 along R_bead - R_partner
-                        const int b2 = sNb[bead][lane * nb_cap + k];
-                        MT r[3], r2 = 0;
-                        for (int a = 0; a < 3; a++) {
-                            r[a] = X[a] - Xc[3 * b2 + a];
-                            r2 += r[a] * r[a];
-                        }
-                        if (r2 < rc2) {
-                            const MT inv = recip(r2);
-                            const MT s2 = sig2 * inv, s6 = s2 * s2 * s2;
-                            const MT fac = e24 * (MT(2) * s6 * s6 - s6) * inv;
-                            for (int a = 0; a < 3; a++) F[a] += fac * r[a];
-                        }
-                    }
-                }
                 for (int o = 1; o < L; o <<= 1)  // every lane of an MD warp takes part; xor < L stays in the bead
                     for (int a = 0; a < 3; a++) F[a] += __shfl_xor_sync(0xffffffffu, F[a], o);
                 if (own) {
-                    MT moved = MT(0);
+                    const V4 xi = namp > MT(0) ? sXi[sb * N + bead] : V4{};
+                    const MT xin[3] = {xi.x, xi.y, xi.z};
+                    MT moved = MT(0), xn[3];
                     for (int a = 0; a < 3; a++) {
                         const MT ffric = -zeta * (V[a] - U[a]);
-                        const MT fnoise = namp > MT(0) ? namp * sXi[(sb * N + bead) * 3 + a] : MT(0);
+                        const MT fnoise = namp * xin[a];
                         V[a] += dtm * (F[a] + ffric + fnoise);
                         D[a] += dt * V[a];
                         P[a] -= (ffric + fnoise) * dt;
-                        const MT xn = X0[a] + D[a];
-                        if (lane == 0) Xn[3 * bead + a] = xn;
-                        const MT d = xn - Xref[a];
+                        xn[a] = X0[a] + D[a];
+                        const MT d = xn[a] - Xref[a];
                         moved += d * d;
+                    }
+                    if (lane == 0) {
+                        V4 w;
+                        w.x = xn[0];
+                        w.y = xn[1];
+                        w.z = xn[2];
+                        w.w = MT(0);
+                        Xn[bead] = w;
                     }
                     if (wca && moved > half_skin2) flag = true;
                 }
@@ -563,7 +608,8 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     __syncthreads();
     }
 
-    // 4. centre of mass pinned at the box centre (one thread per bead)
+    // 4. centre of mass pinned at the box centre (one thread per bead; only
+    //    the warps holding beads reduce, FP64 being slow on this part)
     double R[3] = {0, 0, 0}, V[3] = {0, 0, 0};
     if (tid < N)
         for (int a = 0; a < 3; a++) {
@@ -571,29 +617,31 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
             V[a] = (double)sV[tid][a];
         }
     if (ch.pin_com >= 1) {
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int pass = 0; pass < 2; pass++) {
-            double s[3];
-            for (int a = 0; a < 3; a++) {
-                s[a] = tid < N ? (pass == 0 ? R[a] : V[a]) : 0.0;
-                for (int o = 16; o > 0; o >>= 1) s[a] += __shfl_xor_sync(0xffffffffu, s[a], o);
+        const int warp = tid >> 5, lane = tid & 31, nbw = (N + 31) >> 5;
+        if (warp < nbw)
+            for (int pass = 0; pass < 2; pass++) {
+                double s[3];
+                for (int a = 0; a < 3; a++) {
+                    s[a] = tid < N ? (pass == 0 ? R[a] : V[a]) : 0.0;
+                    for (int o = 16; o > 0; o >>= 1) s[a] += __shfl_xor_sync(0xffffffffu, s[a], o);
+                }
+                if (lane == 0)
+                    for (int a = 0; a < 3; a++) sRed[pass][warp][a] = s[a];
             }
-            if (lane == 0)
-                for (int a = 0; a < 3; a++) sRed[pass][warp][a] = s[a];
-        }
         __syncthreads();
-        double com[3] = {0, 0, 0}, vcm[3] = {0, 0, 0};
-        for (int w = 0; w < (nthr >> 5); w++)
-            for (int a = 0; a < 3; a++) {
-                com[a] += sRed[0][w][a];
-                vcm[a] += sRed[1][w][a];
-            }
-        const double centre = 0.5 * (Ei - 1);
-        if (tid < N)
+        if (tid < N) {
+            double com[3] = {0, 0, 0}, vcm[3] = {0, 0, 0};
+            for (int w = 0; w < nbw; w++)
+                for (int a = 0; a < 3; a++) {
+                    com[a] += sRed[0][w][a];
+                    vcm[a] += sRed[1][w][a];
+                }
+            const double centre = 0.5 * (Ei - 1);
             for (int a = 0; a < 3; a++) {
                 R[a] += centre - com[a] / N;
                 if (ch.pin_com >= 2) V[a] = (double)(MT)(V[a] - vcm[a] / N);
             }
+        }
     }
     if (tid < N)
         for (int a = 0; a < 3; a++) {
@@ -696,13 +744,41 @@ __global__ void __launch_bounds__(kForcedThreads) k_forced(ForcedParams p)
 // ---------------------------------------------------------------------------
 // Initial condition: equilibrium with rho = 1 and velocity u0 on every site.
 // ---------------------------------------------------------------------------
+// u0 lives on the coarse grid [3][Ec^3] (the sites themselves when z = 1); with
+// z > 1 a site takes the trilinear interpolation of its eight coarse
+// neighbours (Sec. 2: the initial field interpolated linearly).
 template <int ST>
-__global__ void k_init(typename Stor<ST>::E* Ab, int64_t n3, const typename Stor<ST>::R* u0)
+__global__ void k_init(typename Stor<ST>::E* Ab, BoxDev bd, const typename Stor<ST>::R* u0)
 {
     using S = Stor<ST>;
     using A = typename S::A;
+    using R = typename S::R;
+    const int64_t n3 = bd.n3, c3 = (int64_t)bd.Ec * bd.Ec * bd.Ec;
+    const int Ei = bd.E, z = bd.zoom, Ec = bd.Ec;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n3; s += (int64_t)gridDim.x * blockDim.x) {
-        const A u[3] = {(A)u0[s], (A)u0[n3 + s], (A)u0[2 * n3 + s]};
+        A u[3];
+        if (z == 1) {
+            for (int c = 0; c < 3; c++) u[c] = (A)u0[c * c3 + s];
+        } else {
+            const int xyz[3] = {(int)(s % Ei), (int)((s / Ei) % Ei), (int)(s / ((int64_t)Ei * Ei))};
+            int i0[3], i1[3];
+            R fr[3];
+            for (int a = 0; a < 3; a++) {
+                i0[a] = xyz[a] / z;
+                i1[a] = i0[a] + 1 < Ec ? i0[a] + 1 : i0[a];
+                fr[a] = (R)(xyz[a] - i0[a] * z) / (R)z;
+            }
+            for (int c = 0; c < 3; c++) {
+                R acc = R(0);
+                for (int k = 0; k < 8; k++) {
+                    const int X = (k & 1) ? i1[0] : i0[0], Y = (k & 2) ? i1[1] : i0[1], Z = (k & 4) ? i1[2] : i0[2];
+                    const R w = ((k & 1) ? fr[0] : R(1) - fr[0]) * ((k & 2) ? fr[1] : R(1) - fr[1]) *
+                                ((k & 4) ? fr[2] : R(1) - fr[2]);
+                    acc += w * u0[c * c3 + ((int64_t)Z * Ec + Y) * Ec + X];
+                }
+                u[c] = (A)acc;
+            }
+        }
         const A usq = A(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
 #pragma unroll
         for (int i = 0; i < kQ; i++) {
@@ -814,13 +890,13 @@ inline int grid_for(int64_t n, int threads, int cap = 152 * 16)
     return g < 1 ? 1 : (int)g;
 }
 
-template <int ST, int SPT>
+template <int ST, int SPT, bool GENERAL>
 cudaError_t launch_staged(const SCParams& p, int ctas, cudaStream_t s)
 {
     using G = Staged<ST, SPT>;
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_stream_collide_staged<ST, SPT>,
+        cudaError_t e = cudaFuncSetAttribute(k_stream_collide_staged<ST, SPT, GENERAL>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmemBytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -834,7 +910,7 @@ cudaError_t launch_staged(const SCParams& p, int ctas, cudaStream_t s)
     int64_t grid = ctas > 0 ? ctas : sms;
     if (grid > p.total_tiles) grid = p.total_tiles;
     if (grid < 1) return cudaSuccess;
-    k_stream_collide_staged<ST, SPT><<<(unsigned)grid, kStagedThreads, G::kSmemBytes, s>>>(p);
+    k_stream_collide_staged<ST, SPT, GENERAL><<<(unsigned)grid, kStagedThreads, G::kSmemBytes, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -843,8 +919,13 @@ cudaError_t Launch<ST>::stream_collide(const SCParams& p, int kernel, int thread
 {
     if (kernel == LB_KERNEL_STAGED) {
         // vw: sites per consumer thread (1 or 2; FP64 1)
-        if (ST != kF64 && vw == 2) return launch_staged<ST, (ST == kF64 ? 1 : 2)>(p, ctas, s);
-        return launch_staged<ST, 1>(p, ctas, s);
+        constexpr int S2 = ST == kF64 ? 1 : 2;
+        if (p.general) {
+            if (ST != kF64 && vw == 2) return launch_staged<ST, S2, true>(p, ctas, s);
+            return launch_staged<ST, 1, true>(p, ctas, s);
+        }
+        if (ST != kF64 && vw == 2) return launch_staged<ST, S2, false>(p, ctas, s);
+        return launch_staged<ST, 1, false>(p, ctas, s);
     }
     int64_t grid = (ctas > 0 && ctas < p.total_tiles) ? ctas : p.total_tiles;
     if (grid < 1) return cudaSuccess;
@@ -859,7 +940,7 @@ cudaError_t Launch<ST>::stream_collide(const SCParams& p, int kernel, int thread
 }
 
 template <int ST>
-cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, int max_beads, cudaStream_t s)
+cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, int max_beads, int lanes, cudaStream_t s)
 {
     if (nchains <= 0) return cudaSuccess;
     using MT = typename std::conditional<ST == kF64, double, float>::type;
@@ -872,10 +953,13 @@ cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, int max_be
     }
     BeadParams q = p;
     q.max_beads = max_beads;
-    q.noise_chunk = kNoiseChunk;
-    // lanes per bead in the MD phase: as many as keep the block at 512 threads, 2 .. 8
-    int lanes = 8;
-    while (lanes > 2 && lanes * max_beads > kBeadThreadsMax) lanes >>= 1;
+    q.noise_chunk = bead_noise_chunk<MT>(max_beads);
+    // lanes per bead in the MD phase (validated by the caller; 0 = default:
+    // four, halved until the block fits 512 threads)
+    if (lanes <= 0) {
+        lanes = 4;
+        while (lanes > 1 && lanes * max_beads > kBeadThreadsMax) lanes >>= 1;
+    }
     q.lanes = lanes;
     int threads = (lanes * max_beads + 31) / 32 * 32;
     if (threads < 64) threads = 64;
@@ -893,9 +977,7 @@ cudaError_t Launch<ST>::forced(const ForcedParams& p, cudaStream_t s)
 template <int ST>
 cudaError_t Launch<ST>::init(void* A, const BoxDev* boxes, int box, int64_t n3, const void* u0, cudaStream_t s)
 {
-    (void)boxes;
-    (void)box;
-    k_init<ST><<<grid_for(n3, 256), 256, 0, s>>>(reinterpret_cast<typename Stor<ST>::E*>(A), n3,
+    k_init<ST><<<grid_for(n3, 256), 256, 0, s>>>(reinterpret_cast<typename Stor<ST>::E*>(A), boxes[box],
                                                  reinterpret_cast<const typename Stor<ST>::R*>(u0));
     return cudaGetLastError();
 }

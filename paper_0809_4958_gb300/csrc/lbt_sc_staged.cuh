@@ -29,7 +29,7 @@ constexpr int kStagedHaloBytes = 16;  // x-shift halo on each side of a row
 constexpr int kStagedConsumerWarps = 15;  // + the producer: four warps per scheduler
 constexpr int kStagedConsumers = kStagedConsumerWarps * 32;
 constexpr int kStagedThreads = kStagedConsumers + 32;  // + the producer warp
-constexpr int kStagedHeaderBytes = 1024;               // barriers and tile headers
+constexpr int kStagedHeaderBytes = 2048;               // barriers and tile headers
 constexpr int kStagedMaxStages = 6;
 
 // Tile geometry for SPT sites per consumer thread.  As many stages as fit in
@@ -128,24 +128,33 @@ __device__ __forceinline__ int locate_box(const SCParams& p, int64_t tile)
 }
 
 // Shared-memory header: full and empty barriers, then the tile header the
-// producer writes for each stage before it arms the barrier: box, first site,
-// and what the boundary layer of the box needs at this step -- the ring slots
-// and weights of the time interpolation and the upsampler substep -- so that
-// they are worked out (64-bit divisions) once per box, not once per warp.
+// producer writes for each stage before it arms the barrier: the box record,
+// first site, frozen flag, and what the collision and the boundary layer of
+// the box need at this step -- BGK constants in the arithmetic type, the ring
+// slots and weights of the time interpolation, the upsampler substep -- so
+// that they are worked out (64-bit divisions, FP64 conversions, global loads)
+// once per tile by the producer, not once per consumer warp.
+template <int ST>
 struct StagedTile {
+    using A = typename Stor<ST>::A;
+    using R = typename Stor<ST>::R;
+    BoxDev bd;
     int64_t s0;
     int32_t box;
     int32_t mlp_s;
+    int32_t frozen;  // the box carries an error status: its state does not change
     int32_t slot[4];
-    double c[4];
+    R c[4];
+    A om, om1, srcfac, drho_b;  // 1/tau, 1 - 1/tau, 1 - 1/(2 tau), rho_b - 1
 };
+template <int ST>
 struct StagedHeader {
-    uint64_t full[8];
-    uint64_t empty[8];
-    StagedTile t[8];
+    uint64_t full[kStagedMaxStages];
+    uint64_t empty[kStagedMaxStages];
+    StagedTile<ST> t[kStagedMaxStages];
 };
-static_assert(sizeof(StagedHeader) <= kStagedHeaderBytes, "header does not fit");
-static_assert(kStagedMaxStages <= 8, "header holds eight stages");
+static_assert(sizeof(StagedHeader<kF64>) <= kStagedHeaderBytes, "header does not fit");
+static_assert(sizeof(StagedHeader<kF32>) <= kStagedHeaderBytes, "header does not fit");
 
 // Producer (one thread): bulk copies of the 19 source rows of a tile.
 template <int ST, int SPT>
@@ -185,8 +194,8 @@ __device__ __forceinline__ int div_e(int64_t s, uint64_t m) { return (int)(((uin
 // collision (BGK with the equilibrium of opposite pairs shared: the even part
 // in c.u is common, the odd part changes sign) and the stores.
 template <int ST, int SPT, bool PER, bool ACCEL>
-__device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd, const StagedTile& th,
-                                            const unsigned char* stage, uint64_t* empty)
+__device__ __forceinline__ void staged_tile(const SCParams& p, const StagedTile<ST>& th, const unsigned char* stage,
+                                            uint64_t* empty)
 {
     using S = Stor<ST>;
     using E = typename S::E;
@@ -196,6 +205,7 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
     constexpr int C = kStagedConsumers;
     const int tid = threadIdx.x;
     const int64_t s0 = th.s0;
+    const BoxDev& bd = th.bd;
 
     const int Ei = bd.E;
     const int64_t n3 = bd.n3;
@@ -271,12 +281,13 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
         uy[k] = jy * inv;
         uz[k] = jz * inv;
     }
+    // boundary sites: equilibrium of the boundary velocity from the ring
     if (any_bnd) {
         TimeWeights<R> tw;
 #pragma unroll
         for (int a = 0; a < 4; a++) {
             tw.slot[a] = th.slot[a];
-            tw.c[a] = (R)th.c[a];
+            tw.c[a] = th.c[a];
         }
         const R* ring = reinterpret_cast<const R*>(p.ring);
 #pragma unroll
@@ -285,18 +296,16 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
                 int pp, qq;
                 const int fc = owning_face(xs_[k], ys_[k], zs_[k], Ei, per, pp, qq);
                 R ub[3];
-                boundary_velocity<R>(ring, p.ring_slot_elems, bd.ring_off, Ei, fc, pp, qq, tw, ub);
+                boundary_velocity<R>(ring, p.ring_slot_elems, bd, fc, pp, qq, tw, ub);
                 add_mlp_residual<R>(p, bd, th.mlp_s, fc, pp, qq, ub);
-                drho[k] = (A)bd.rho_b - A(1);
+                drho[k] = th.drho_b;
                 ux[k] = (A)ub[0];
                 uy[k] = (A)ub[1];
                 uz[k] = (A)ub[2];
             }
         }
     }
-    const A om = A(1) / (A)bd.tau;
-    const A om1 = A(1) - om;
-    const A srcfac = A(1) - A(0.5) * om;
+    const A om = th.om, om1 = th.om1, srcfac = th.srcfac;
     A usq[SPT], rho_[SPT], ua[SPT];
 #pragma unroll
     for (int k = 0; k < SPT; k++) {
@@ -305,6 +314,9 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
         if (ACCEL) ua[k] = ux[k] * (A)bd.accel[0] + uy[k] * (A)bd.accel[1] + uz[k] * (A)bd.accel[2];
     }
     // post-collision value of population i at site k from its equilibrium deviation
+    // populations are written in order 0, 1, ..., 18 through one running
+    // pointer (row of population i at this thread's first site)
+    E* out = Bb + s0 + tid;
     auto emit = [&](int i, int k, A deq, A cu) {
         A val = deq;
         if (!bnd[k]) {
@@ -315,13 +327,16 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
                 val += srcfac * w * rho_[k] * (A(3) * (ca - ua[k]) + A(9) * cu * ca);
             }
         }
-        if (act[k]) Bb[(int64_t)i * n3 + s0 + tid + k * C] = S::out(val);
+        // population 0 and odd i at `out`, the even partner of a pair one row further
+        const int64_t row = (i > 0 && (i & 1) == 0) ? n3 : 0;
+        if (act[k]) out[row + k * C] = S::out(val);
     };
 #pragma unroll
     for (int k = 0; k < SPT; k++) emit(0, k, wgt<A>(0) * (drho[k] - rho_[k] * usq[k]), A(0));
     // opposite pairs (1,2), (3,4), ..., (17,18)
 #pragma unroll
     for (int i = 1; i < kQ; i += 2) {
+        out += i == 1 ? n3 : 2 * n3;  // row of population i; population i + 1 is one row further
         const A w = wgt<A>(i);
         const int cx = cvec(i, 0), cy = cvec(i, 1), cz = cvec(i, 2);
 #pragma unroll
@@ -339,8 +354,11 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const BoxDev& bd,
 }
 
 // Consumer warps: take the stages in order until the producer posts the end.
-template <int ST, int SPT>
-__device__ __forceinline__ void staged_consume(const SCParams& p, unsigned char* smem, StagedHeader* hd)
+// GENERAL = false: every box of the launch is non-periodic and force-free, so
+// only that tile body is compiled in (fewer registers than the kernel that
+// carries all four bodies).
+template <int ST, int SPT, bool GENERAL>
+__device__ __forceinline__ void staged_consume(const SCParams& p, unsigned char* smem, StagedHeader<ST>* hd)
 {
     using G = Staged<ST, SPT>;
     using E = typename Stor<ST>::E;
@@ -358,13 +376,13 @@ __device__ __forceinline__ void staged_consume(const SCParams& p, unsigned char*
             mbar_wait_bounded(&hd->full[st], phase);
             return;
         }
-        const StagedTile& th = hd->t[st];
+        const StagedTile<ST>& th = hd->t[st];
         const int b = th.box;
         if (b < 0) return;  // end of work
         const int64_t s0 = th.s0;
-        const BoxDev& bd = p.boxes[b];
+        const BoxDev& bd = th.bd;
         const unsigned char* stage = smem + kStagedHeaderBytes + st * G::kStageBytes;
-        if (p.status[b] != 0) {
+        if (th.frozen) {
             // frozen box: release the stage, the state does not change
             __syncwarp();
             if ((threadIdx.x & 31) == 0) mbar_arrive(&hd->empty[st]);
@@ -373,12 +391,14 @@ __device__ __forceinline__ void staged_consume(const SCParams& p, unsigned char*
             for (int t = threadIdx.x; t < G::kSites; t += kStagedConsumers)
                 if (s0 + t < bd.n3)
                     for (int i = 0; i < kQ; i++) Bb[(int64_t)i * bd.n3 + s0 + t] = Ab[(int64_t)i * bd.n3 + s0 + t];
+        } else if (!GENERAL) {
+            staged_tile<ST, SPT, false, false>(p, th, stage, &hd->empty[st]);
         } else if (bd.per_mask == 0) {
-            if (bd.has_accel) staged_tile<ST, SPT, false, true>(p, bd, th, stage, &hd->empty[st]);
-            else staged_tile<ST, SPT, false, false>(p, bd, th, stage, &hd->empty[st]);
+            if (bd.has_accel) staged_tile<ST, SPT, false, true>(p, th, stage, &hd->empty[st]);
+            else staged_tile<ST, SPT, false, false>(p, th, stage, &hd->empty[st]);
         } else {
-            if (bd.has_accel) staged_tile<ST, SPT, true, true>(p, bd, th, stage, &hd->empty[st]);
-            else staged_tile<ST, SPT, true, false>(p, bd, th, stage, &hd->empty[st]);
+            if (bd.has_accel) staged_tile<ST, SPT, true, true>(p, th, stage, &hd->empty[st]);
+            else staged_tile<ST, SPT, true, false>(p, th, stage, &hd->empty[st]);
         }
     }
 }
@@ -388,10 +408,11 @@ __device__ __forceinline__ void staged_consume(const SCParams& p, unsigned char*
 // block that starts late -- its SM still busy with the bead kernel -- simply
 // takes fewer tiles) and fill the stages as the consumers free them.
 template <int ST, int SPT>
-__device__ __forceinline__ void staged_produce(const SCParams& p, unsigned char* smem, StagedHeader* hd, int64_t n)
+__device__ __forceinline__ void staged_produce(const SCParams& p, unsigned char* smem, StagedHeader<ST>* hd, int64_t n)
 {
     using G = Staged<ST, SPT>;
     using R = typename Stor<ST>::R;
+    using A = typename Stor<ST>::A;
     unsigned long long* ctr = reinterpret_cast<unsigned long long*>(p.tile_counter);
     int64_t next = (int64_t)atomicAdd(ctr, 1ull);
     int last_b = -1;
@@ -417,25 +438,33 @@ __device__ __forceinline__ void staged_produce(const SCParams& p, unsigned char*
             mlp_s = bd.mlp_row >= 0 ? mlp_substep(n, bd.K) : 0;
             last_b = b;
         }
-        StagedTile& th = hd->t[st];
+        StagedTile<ST>& th = hd->t[st];
+        static_assert(sizeof(BoxDev) % 8 == 0, "box record copied in 8-byte words");
+        for (int w = 0; w < (int)(sizeof(BoxDev) / 8); w++)  // word by word: few live registers
+            reinterpret_cast<uint64_t*>(&th.bd)[w] = reinterpret_cast<const uint64_t*>(&bd)[w];
         th.box = b;
         th.s0 = s0;
         th.mlp_s = mlp_s;
+        th.frozen = p.status[b] != 0;
         for (int a = 0; a < 4; a++) {
             th.slot[a] = tw.slot[a];
-            th.c[a] = (double)tw.c[a];
+            th.c[a] = tw.c[a];
         }
+        th.om = A(1) / (A)bd.tau;
+        th.om1 = A(1) - th.om;
+        th.srcfac = A(1) - A(0.5) * th.om;
+        th.drho_b = (A)bd.rho_b - A(1);
         fence_proxy_async_smem();
         issue_tile<ST, SPT>(p, bd, s0, smem + kStagedHeaderBytes + st * G::kStageBytes, &hd->full[st]);
     }
 }
 
-template <int ST, int SPT>
+template <int ST, int SPT, bool GENERAL>
 __global__ void __launch_bounds__(kStagedThreads, 1) k_stream_collide_staged(SCParams p)
 {
     using G = Staged<ST, SPT>;
     extern __shared__ __align__(128) unsigned char smem[];
-    StagedHeader* hd = reinterpret_cast<StagedHeader*>(smem);
+    StagedHeader<ST>* hd = reinterpret_cast<StagedHeader<ST>*>(smem);
     const int64_t n = *p.step;
     if (threadIdx.x == 0) {
         for (int st = 0; st < G::kStages; st++) {
@@ -449,7 +478,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_stream_collide_staged(SCP
         if (threadIdx.x == kStagedConsumers) staged_produce<ST, SPT>(p, smem, hd, n);
         return;
     }
-    staged_consume<ST, SPT>(p, smem, hd);
+    staged_consume<ST, SPT, GENERAL>(p, smem, hd);
 }
 
 }  // namespace lbt

@@ -17,15 +17,16 @@ namespace lbt {
 constexpr int kSynthThreads = 256;
 constexpr int kSynthMaxModes = 3072;  // time factors of all modes fit 48 KB of shared memory
 
-// T[a][m][x] = exp(i kvec[m][a] (x - xc)), a = 0..2, x = 0..E-1
-__global__ void k_synth_axis(const double* kvec, int M, int E, double2* T)
+// T[a][m][x] = exp(i kvec[m][a] (x - xc)), a = 0..2, x = 0..X-1 (X >= E: a
+// zoomed coarse grid may reach past the box), xc = (E - 1)/2.
+__global__ void k_synth_axis(const double* kvec, int M, int E, int X, double2* T)
 {
     const double xc = 0.5 * (E - 1);
-    const int64_t total = 3LL * M * E;
+    const int64_t total = 3LL * M * X;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(t % E);
-        const int m = (int)((t / E) % M);
-        const int a = (int)(t / ((int64_t)E * M));
+        const int x = (int)(t % X);
+        const int m = (int)((t / X) % M);
+        const int a = (int)(t / ((int64_t)X * M));
         double s, c;
         sincos(kvec[3 * m + a] * (x - xc), &s, &c);
         T[t] = make_double2(c, s);
@@ -42,10 +43,10 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 // when z = 1).  out[j][f][c][Q][P].
 template <class R>
 __global__ void __launch_bounds__(kSynthThreads) k_synth_faces(const double2* T, const double* amp, const double* omega,
-                                                              const double* phi, int M, int E, int z, int K, int64_t j0,
-                                                              int chunks_per_face, R* out)
+                                                              const double* phi, int M, int E, int X, int z, int K,
+                                                              int64_t j0, int chunks_per_face, R* out)
 {
-    const int Ec = (E - 1) / z + 1;
+    const int Ec = coarse_points(E, z);
     extern __shared__ double2 sC[];  // exp(i (omega t + phi)) * T[fixed axis][m][fixed coordinate]
     const int chunk = blockIdx.x % chunks_per_face;
     const int f = (blockIdx.x / chunks_per_face) % 6;
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(kSynthThreads) k_synth_faces(const double2* T,
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
         double s, c;
         sincos(omega[m] * t + phi[m], &s, &c);
-        sC[m] = cmul(make_double2(c, s), T[((int64_t)fa * M + m) * E + fx]);
+        sC[m] = cmul(make_double2(c, s), T[((int64_t)fa * M + m) * X + fx]);
     }
     __syncthreads();
     const int64_t fe = (int64_t)Ec * Ec;
@@ -69,8 +70,8 @@ __global__ void __launch_bounds__(kSynthThreads) k_synth_faces(const double2* T,
         const int p = (int)(s % Ec) * z, q = (int)(s / Ec) * z;
         double u0 = 0, u1 = 0, u2 = 0;
         for (int m = 0; m < M; m++) {
-            const double2 zp = T[((int64_t)ap * M + m) * E + p];
-            const double2 zq = T[((int64_t)aq * M + m) * E + q];
+            const double2 zp = T[((int64_t)ap * M + m) * X + p];
+            const double2 zq = T[((int64_t)aq * M + m) * X + q];
             const double2 w = cmul(sC[m], zp);
             const double re = w.x * zq.x - w.y * zq.y;
             u0 += amp[3 * m] * re;
@@ -88,9 +89,10 @@ __global__ void __launch_bounds__(kSynthThreads) k_synth_faces(const double2* T,
 // out[c][Z][Y][X].
 template <class R>
 __global__ void __launch_bounds__(kSynthThreads) k_synth_volume(const double2* T, const double* amp, const double* omega,
-                                                               const double* phi, int M, int E, int zm, double t, R* out)
+                                                               const double* phi, int M, int E, int X, int zm, double t,
+                                                               R* out)
 {
-    const int Ec = (E - 1) / zm + 1;
+    const int Ec = coarse_points(E, zm);
     extern __shared__ double2 sC[];
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
         double s, c;
@@ -103,8 +105,8 @@ __global__ void __launch_bounds__(kSynthThreads) k_synth_volume(const double2* T
         const int x = (int)(s % Ec) * zm, y = (int)((s / Ec) % Ec) * zm, z = (int)(s / ((int64_t)Ec * Ec)) * zm;
         double u0 = 0, u1 = 0, u2 = 0;
         for (int m = 0; m < M; m++) {
-            const double2 w = cmul(cmul(sC[m], T[(int64_t)m * E + x]), T[((int64_t)M + m) * E + y]);
-            const double2 zz = T[((int64_t)2 * M + m) * E + z];
+            const double2 w = cmul(cmul(sC[m], T[(int64_t)m * X + x]), T[((int64_t)M + m) * X + y]);
+            const double2 zz = T[((int64_t)2 * M + m) * X + z];
             const double re = w.x * zz.x - w.y * zz.y;
             u0 += amp[3 * m] * re;
             u1 += amp[3 * m + 1] * re;
@@ -129,8 +131,9 @@ cudaError_t launch_synth_faces(const double* kvec, const double* amp, const doub
     if (M > kSynthMaxModes) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     double2* T = reinterpret_cast<double2*>(workspace);
-    k_synth_axis<<<grid_for_synth(3LL * M * E), 256, 0, s>>>(kvec, M, E, T);
-    const int Ec = (E - 1) / zoom + 1;
+    const int Ec = coarse_points(E, zoom);
+    const int X = (Ec - 1) * zoom + 1 > E ? (Ec - 1) * zoom + 1 : E;  // <= 2E - 1: fits the workspace
+    k_synth_axis<<<grid_for_synth(3LL * M * X), 256, 0, s>>>(kvec, M, E, X, T);
     const int64_t fe = (int64_t)Ec * Ec;
     const int chunks = (int)((fe + 1023) / 1024);
     const size_t smem = sizeof(double2) * M;
@@ -138,10 +141,10 @@ cudaError_t launch_synth_faces(const double* kvec, const double* amp, const doub
         const int64_t nj = min((int64_t)4096, nsamp - j);
         const unsigned grid = (unsigned)(nj * 6 * chunks);
         if (out_f64)
-            k_synth_faces<double><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, zoom, K, j0 + j, chunks,
+            k_synth_faces<double><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, X, zoom, K, j0 + j, chunks,
                                                                    reinterpret_cast<double*>(out) + j * 6 * 3 * fe);
         else
-            k_synth_faces<float><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, zoom, K, j0 + j, chunks,
+            k_synth_faces<float><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, X, zoom, K, j0 + j, chunks,
                                                                   reinterpret_cast<float*>(out) + j * 6 * 3 * fe);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -155,16 +158,17 @@ cudaError_t launch_synth_volume(const double* kvec, const double* amp, const dou
 {
     if (M > kSynthMaxModes) return cudaErrorInvalidValue;
     double2* T = reinterpret_cast<double2*>(workspace);
-    k_synth_axis<<<grid_for_synth(3LL * M * E), 256, 0, s>>>(kvec, M, E, T);
-    const int Ec = (E - 1) / zoom + 1;
+    const int Ec = coarse_points(E, zoom);
+    const int X = (Ec - 1) * zoom + 1 > E ? (Ec - 1) * zoom + 1 : E;
+    k_synth_axis<<<grid_for_synth(3LL * M * X), 256, 0, s>>>(kvec, M, E, X, T);
     const int64_t n3 = (int64_t)Ec * Ec * Ec;
     const size_t smem = sizeof(double2) * M;
     const int grid = (int)min((int64_t)152 * 8, (n3 + kSynthThreads - 1) / kSynthThreads);
     if (out_f64)
-        k_synth_volume<double><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, zoom, t,
+        k_synth_volume<double><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, X, zoom, t,
                                                                  reinterpret_cast<double*>(out));
     else
-        k_synth_volume<float><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, zoom, t,
+        k_synth_volume<float><<<grid, kSynthThreads, smem, s>>>(T, amp, omega, phi, M, E, X, zoom, t,
                                                                 reinterpret_cast<float*>(out));
     return cudaGetLastError();
 }

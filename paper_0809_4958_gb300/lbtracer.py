@@ -29,7 +29,7 @@ ERROR_NAMES = {0: "LB_OK", 1: "LB_ERR_ARG", 2: "LB_ERR_CUDA", 3: "LB_ERR_FENE", 
 
 EXPORTS = ["lb_plan", "lb_create", "lb_destroy", "lb_init", "lb_set_boundary", "chain_couple", "lb_step",
            "lb_graph_capture", "lb_graph_launch", "lb_read_fields", "lb_conservation", "lb_sync", "lb_status",
-           "lb_current_step", "lb_set_launch", "lb_profile", "lb_profile_read", "lb_last_error", "lb_synth_workspace_bytes", "lb_synth_faces",
+           "lb_current_step", "lb_set_launch", "lb_set_bead_launch", "lb_profile", "lb_profile_read", "lb_last_error", "lb_synth_workspace_bytes", "lb_synth_faces",
            "lb_synth_volume", "lb_population_sums_noalloc", "lb_mlp_param_bytes", "lb_mlp_bind", "lb_mlp_train_bytes",
            "lb_mlp_train_init", "lb_mlp_features", "lb_mlp_targets", "lb_mlp_forward", "lb_mlp_grad",
            "lb_mlp_train_step", "lb_mlp_export"]
@@ -37,8 +37,9 @@ EXPORTS = ["lb_plan", "lb_create", "lb_destroy", "lb_init", "lb_set_boundary", "
 
 class lb_box_desc(ctypes.Structure):
     _fields_ = [("E", ctypes.c_int32), ("face_mode", ctypes.c_int32 * 6), ("time_interp", ctypes.c_int32),
-                ("K", ctypes.c_int32), ("nbeads", ctypes.c_int32), ("tau", ctypes.c_double),
-                ("rho_b", ctypes.c_double), ("body_accel", ctypes.c_double * 3)]
+                ("K", ctypes.c_int32), ("nbeads", ctypes.c_int32), ("zoom", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("tau", ctypes.c_double), ("rho_b", ctypes.c_double),
+                ("body_accel", ctypes.c_double * 3)]
 
 
 class lb_chain_desc(ctypes.Structure):
@@ -87,6 +88,7 @@ def load(path: str | None = None, build_if_missing: bool = True):
         "lb_status": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
         "lb_current_step": (_i64, [_vp]),
         "lb_set_launch": (_i32, [_vp, _i32, _i32, _i32, _i32]),
+        "lb_set_bead_launch": (_i32, [_vp, _i32]),
         "lb_profile": (_i32, [_vp, _i32, _i32]),
         "lb_profile_read": (_i32, [_vp, ctypes.POINTER(_f64), ctypes.POINTER(_i64)]),
         "lb_last_error": (ctypes.c_char_p, [_vp]),
@@ -140,9 +142,10 @@ def _torch():
 
 
 def box_desc(E, tau, periodic=(False, False, False), time_interp=LB_TIME_LINEAR, K=1, nbeads=0, rho_b=1.0,
-             accel=(0.0, 0.0, 0.0)) -> lb_box_desc:
+             accel=(0.0, 0.0, 0.0), zoom=1) -> lb_box_desc:
     d = lb_box_desc()
     d.E = int(E)
+    d.zoom = int(zoom)
     for a in range(3):
         m = LB_FACE_PERIODIC if periodic[a] else LB_FACE_VELOCITY
         d.face_mode[2 * a] = m
@@ -233,6 +236,9 @@ class Tracers:
 
     def lb_current_step(self):
         return int(self.lib.lb_current_step(self.ctx))
+
+    def lb_set_bead_launch(self, lanes=0):
+        _check(self.lib.lb_set_bead_launch(self.ctx, int(lanes)), self.ctx)
 
     def lb_set_launch(self, kernel=LB_KERNEL_STAGED, threads=0, ctas=0, sites_per_thread=0):
         _check(self.lib.lb_set_launch(self.ctx, int(kernel), int(threads), int(ctas), int(sites_per_thread)),
@@ -374,8 +380,9 @@ def modes_to_device(modes, device="cuda"):
 
 
 def coarse_points(E, zoom=1):
-    """Points per axis of the coarse grid of a box with this zoom."""
-    return (E - 1) // zoom + 1 if zoom > 1 else E
+    """Points per axis of the coarse grid of a box with this zoom: point P at
+    site P zoom, enough points to cover site E - 1 (E for zoom <= 1)."""
+    return (E - 1 + zoom - 1) // zoom + 1 if zoom > 1 else E
 
 
 def synth_faces(modes, E, K, j0, nsamp, dtype, stream=None, out=None, zoom=1):

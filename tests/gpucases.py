@@ -27,20 +27,20 @@ class Case:
     """One box: synthetic Kolmogorov-spectrum boundary, optional chain."""
 
     def __init__(self, E, tau, nsteps, seed=0, M=64, k_max=None, K=1, time_interp=0, periodic=(False, False, False),
-                 accel=(0.0, 0.0, 0.0), nbeads=0, kT=0.0, n_md=50, pin_com=2, chain_seed=7, vel0=None):
-        self.E, self.tau, self.nsteps, self.K = E, tau, nsteps, K
+                 accel=(0.0, 0.0, 0.0), nbeads=0, kT=0.0, n_md=50, pin_com=2, chain_seed=7, vel0=None, zoom=1):
+        self.E, self.tau, self.nsteps, self.K, self.zoom = E, tau, nsteps, K, zoom
         self.time_interp, self.periodic, self.accel = time_interp, tuple(periodic), tuple(accel)
         self.modes = inputs.mode_table(seed, M, 1.0, float(k_max or E // 2), E)
         self.J = nsteps // K + 4
-        self.samples = oracle.face_samples(self.modes, E, K, 0, self.J)
-        self.u0 = oracle.volume_field(self.modes, E, 0.0)
+        self.samples = oracle.face_samples(self.modes, E, K, 0, self.J, zoom)
+        self.u0 = oracle.volume_field(self.modes, E, 0.0, zoom)
         self.nbeads, self.kT, self.n_md, self.pin_com, self.chain_seed = nbeads, kT, n_md, pin_com, chain_seed
         self.pos0 = inputs.chain_start(seed + 100, nbeads, E) if nbeads else None
         self.vel0 = vel0
 
     def oracle_box(self, storage=oracle.STORE_F64):
         return oracle.BoxParams(E=self.E, tau=self.tau, periodic=self.periodic, accel=self.accel,
-                                time_interp=self.time_interp, K=self.K, storage=storage)
+                                time_interp=self.time_interp, K=self.K, storage=storage, zoom=self.zoom)
 
     def oracle_chain(self, box_id=0):
         if not self.nbeads:
@@ -56,7 +56,8 @@ class Case:
 
     # ---- GPU side ----
     def gpu_desc(self, lbt):
-        return lbt.box_desc(self.E, self.tau, self.periodic, self.time_interp, self.K, self.nbeads, 1.0, self.accel)
+        return lbt.box_desc(self.E, self.tau, self.periodic, self.time_interp, self.K, self.nbeads, 1.0, self.accel,
+                            zoom=self.zoom)
 
     def gpu_chain(self, lbt):
         return lbt.chain_desc(self.nbeads, kT=self.kT, seed=self.chain_seed, n_md=self.n_md, pin_com=self.pin_com)

@@ -116,7 +116,30 @@ def test_periodic_conservation_f64(lbt):
     assert np.abs(c1[4:7] - c0[4:7]).max() > 1e-5  # momentum really moved between beads and fluid
     sim = c.run_oracle()
     ref = sim.conservation()
-    assert np.abs(c1 - ref).max() <= 1e-10
+    # the oracle adds the 19 * 16^3 populations one by one in FP64: its mass sum
+    # carries a rounding error of order sqrt(n) eps mass ~ 1e-10 (absolute);
+    # the GPU sums deviations in a tree
+    assert abs(c1[0] - ref[0]) <= 1e-13 * mass
+    assert np.abs(c1[1:] - ref[1:]).max() <= 1e-10
+
+
+@pytest.mark.parametrize("storage", [ST64, ST32])
+def test_bead_lanes_agree(lbt, storage):
+    # the lanes of a bead only split its pair forces: every choice gives the
+    # same chain up to the order of the force sums
+    c = Case(24, 0.8, 20, M=32, nbeads=40, kT=1e-4)
+    runs = []
+    for lanes in (1, 2, 4, 8):
+        r = GpuRunner(lbt, torch, [c], storage)
+        r.tr.lb_set_bead_launch(lanes)
+        r.step(20)
+        runs.append((r.tr.chain(0, c.nbeads), r.tr.deviations(0)))
+    (p0, v0), d0 = runs[0]
+    # FP32: the substep displacements round at 2^-24 of positions ~E/2 and the
+    # differences of summation order grow over 20 steps of 50 substeps
+    tol_p, tol_d = (1e-12, 1e-14) if storage == ST64 else (1e-4, 1e-6)
+    for (p, v), d in runs[1:]:
+        assert np.abs(p - p0).max() <= tol_p and np.abs(d - d0).max() <= tol_d
 
 
 def test_batch_of_uneven_boxes_equals_single_boxes(lbt):
@@ -154,6 +177,7 @@ def test_fullsize_128_sampled_step(lbt):
     for tau in (0.55, 0.8):
         c = Case.__new__(Case)
         c.E, c.tau, c.K, c.time_interp, c.periodic, c.accel = E, tau, 1, 0, (False, False, False), (0.0, 0.0, 0.0)
+        c.zoom = 1
         c.nsteps, c.nbeads, c.kT, c.n_md, c.pin_com, c.chain_seed, c.vel0 = 12, 64, 1e-4, 50, 2, 9, None
         c.modes = inputs.mode_table(11, 1024, 1.0, 64.0, E)
         c.J = 16

@@ -66,6 +66,7 @@ def test_16bit_one_step_sitewise_at_256(lbt, storage):
     E = 256
     c = Case.__new__(Case)
     c.E, c.tau, c.K, c.time_interp, c.periodic, c.accel = E, 0.8, 1, 0, (False, False, False), (0.0, 0.0, 0.0)
+    c.zoom = 1
     c.nsteps, c.nbeads, c.kT, c.n_md, c.pin_com, c.chain_seed, c.vel0 = 6, 0, 0.0, 50, 2, 0, None
     c.modes = inputs.mode_table(3, 2048, 1.0, 128.0, E)
     c.J = 8
