@@ -278,7 +278,7 @@ def main():
     from paper_0809_4958_gb300 import autotune
     modes = inputs.mode_table(seed, w["M"], w["k_min"], w["k_max"], E)
     ncand = 0 if args.no_tune else len(autotune.candidates(storage, torch.cuda.get_device_properties(dev).multi_processor_count))
-    tune_steps = 7 * ncand + 7 * 4  # launch shapes, then the bead kernel's lanes
+    tune_steps = 7 * ncand + 7 * 5  # launch shapes, then the bead kernel's thread layouts
     nsamp = args.warmup + tune_steps + args.steps + 2
     faces = lbt.synth_faces(modes, E, w["K"], 0, nsamp, real)
     u0 = lbt.synth_volume(modes, E, 0.0, real)
@@ -347,7 +347,7 @@ def main():
         # fresh context so the pushed samples line up with the host record
         tr2 = lbt.Tracers([lbt.box_desc(E, w["tau"], nbeads=w["nbeads"], K=w["K"])], storage, stream=stream)
         tr2.lb_set_launch(*choice)
-        tr2.lb_set_bead_launch(getattr(tr, "bead_lanes", 0))
+        tr2.lb_set_bead_launch(*getattr(tr, "bead_lanes", (0, 1)))
         torch.cuda.synchronize()
         tr2.lb_init(0, u0)
         tr2.chain_couple(0, lbt.chain_desc(w["nbeads"], kT=w["kT"], n_md=w["n_md"], seed=seed), pos0)
@@ -395,7 +395,7 @@ def main():
                                "step)" % (E, w["tau"], args.storage, w["kT"]),
                    "boxes_per_gpu": 1, "sites_per_box": E ** 3, "l2": "working set 2 x %.0f MB > L2, no flush"
                    % (Q * E ** 3 * s_elem / 1e6), "launch": {"kernel": ["staged", "register"][choice[0]], "threads": choice[1], "ctas": choice[2],
-                              "sites_per_thread": choice[3], "bead_lanes": getattr(tr, "bead_lanes", 0)},
+                              "sites_per_thread": choice[3], "bead_layout": list(getattr(tr, "bead_lanes", (0, 1)))},
                    "autotune": [[list(c), t] for c, t in table]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(args.storage, sc_kernel),
@@ -444,7 +444,7 @@ def run_batch(args):
     steps = (args.steps + G - 1) // G * G
     warm = (args.warmup + G - 1) // G * G
     ncand = len(autotune.candidates(lbt.LB_STORE_F32, torch.cuda.get_device_properties(dev).multi_processor_count))
-    tune_steps = 7 * ncand + 7 * 4  # launch shapes, then the bead kernel's lanes
+    tune_steps = 7 * ncand + 7 * 5  # launch shapes, then the bead kernel's thread layouts
     nsamp = warm + tune_steps + steps + G + 2
     descs = [lbt.box_desc(int(E), w["tau"], nbeads=int(N), K=w["K"]) for E, N in zip(edges, nbs)]
     stream = torch.cuda.Stream()

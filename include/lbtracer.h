@@ -262,13 +262,15 @@ int64_t lb_current_step(const lb_ctx* ctx);
  *   Used by the autotuner.  Drops a captured graph. */
 int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas, int32_t sites_per_thread);
 
-/* lb_set_bead_launch -- threads per bead in the MD substeps of the bead
- *   kernel (Sec. 1: the chain dynamics of the hybrid method): 0 = default
- *   (4, halved until lanes x largest chain <= 512), or 1, 2, 4, 8 with
- *   lanes x largest chain <= 512.  The lanes of a bead share its bond and
- *   pair forces and sum them by shuffles.  Used by the autotuner; drops a
- *   captured graph.  LB_ERR_ARG otherwise. */
-int32_t lb_set_bead_launch(lb_ctx* ctx, int32_t lanes);
+/* lb_set_bead_launch -- thread layout of the MD substeps of the bead
+ *   kernel (Sec. 1: the chain dynamics of the hybrid method).
+ *   lanes: threads per bead, 0 = default (8, halved until the MD threads
+ *   fit 512), or 1, 2, 4, 8; the lanes of a bead share its bond and pair
+ *   forces and sum them by shuffles.  beads_per_thread: 1, or 2 with
+ *   lanes = 1 (one warp holds up to 64 beads).
+ *   lanes x ceil(largest chain / beads_per_thread) <= 512.  Used by the
+ *   autotuner; drops a captured graph.  LB_ERR_ARG otherwise. */
+int32_t lb_set_bead_launch(lb_ctx* ctx, int32_t lanes, int32_t beads_per_thread);
 
 /*
  * lb_profile -- time every stream-collide launch with a pair of CUDA events

@@ -45,19 +45,20 @@ def _load_cache():
 
 
 def tune_bead_lanes(tr, step, nsteps: int = 6):
-    """Lanes per bead of the bead kernel: the whole step is timed with CUDA
-    events on the context stream for every valid choice (the bead kernel runs
-    beside the stream-collide, so only the step shows its cost).  Returns the
-    choice applied to the context (0 when the context has no chain)."""
+    """MD thread layout of the bead kernel, (lanes per bead, beads per
+    thread): the whole step is timed with CUDA events on the context stream
+    for every valid choice (the bead kernel runs beside the stream-collide, so
+    only the step shows its cost).  Returns the choice applied to the context
+    ((0, 1) when the context has no chain)."""
     import torch
     maxb = max(d.nbeads for d in tr.descs)
     if maxb == 0:
-        return 0
+        return (0, 1)
     best = None
-    for lanes in (1, 2, 4, 8):
-        if lanes * maxb > 512:
+    for lanes, bpt in ((1, 2), (1, 1), (2, 1), (4, 1), (8, 1)):
+        if lanes * ((maxb + bpt - 1) // bpt) > 512:
             continue
-        tr.lb_set_bead_launch(lanes)
+        tr.lb_set_bead_launch(lanes, bpt)
         step(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(tr.stream)
@@ -66,8 +67,8 @@ def tune_bead_lanes(tr, step, nsteps: int = 6):
         e1.synchronize()
         ms = e0.elapsed_time(e1) / nsteps
         if best is None or ms < best[1]:
-            best = (lanes, ms)
-    tr.lb_set_bead_launch(best[0])
+            best = ((lanes, bpt), ms)
+    tr.lb_set_bead_launch(*best[0])
     tr.bead_lanes = best[0]
     return best[0]
 
@@ -85,7 +86,7 @@ def tune(tr, step, steps_per_candidate: int = 6, use_cache: bool = True):
     if key in cache:
         choice = tuple(cache[key]["choice"])
         tr.lb_set_launch(*choice)
-        tr.lb_set_bead_launch(cache[key].get("bead_lanes", 0))
+        tr.lb_set_bead_launch(*cache[key].get("bead_lanes", (0, 1)))
         return choice, cache[key].get("table", [])
     sms = torch.cuda.get_device_properties(tr.stream.device).multi_processor_count
     table = []

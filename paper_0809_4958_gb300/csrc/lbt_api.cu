@@ -186,6 +186,7 @@ struct lb_ctx {
     int max_beads = 0;  // largest chain capacity of the context
     int sms = 0;        // multiprocessors of the context's device
     int bead_lanes = 0; // lanes per bead in the MD substeps (0 = default)
+    int bead_bpt = 1;   // beads per MD thread
     int threads = 256, ctas = 0, vw = 0;  // vw: sites per thread in stream-collide
     std::vector<int64_t> tile_prefix;  // for the current block size
     cudaGraphExec_t graph = nullptr;
@@ -315,7 +316,7 @@ int enqueue_step(lb_ctx* ctx, int64_t n)
         bp.forces = ctx->at<ForceEntry>(ctx->L.forces);
         bp.step = ctx->at<int64_t>(ctx->L.step);
         bp.status = ctx->at<int32_t>(ctx->L.status);
-        CK(DISPATCH(ctx->storage, bead_couple(bp, nch, ctx->max_beads, ctx->bead_lanes, ctx->side)));
+        CK(DISPATCH(ctx->storage, bead_couple(bp, nch, ctx->max_beads, ctx->bead_lanes, ctx->bead_bpt, ctx->side)));
         CK(cudaEventRecord(ctx->ev_join, ctx->side));
     }
     SCParams sp;
@@ -887,14 +888,19 @@ int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas
     return rebuild_tiles(ctx);
 }
 
-int32_t lb_set_bead_launch(lb_ctx* ctx, int32_t lanes)
+int32_t lb_set_bead_launch(lb_ctx* ctx, int32_t lanes, int32_t beads_per_thread)
 {
     if (!ctx) return LB_ERR_ARG;
     if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
         return ctx->fail(LB_ERR_ARG, "lb_set_bead_launch: lanes must be 0, 1, 2, 4 or 8");
-    if (lanes * ctx->max_beads > 512)
-        return ctx->fail(LB_ERR_ARG, "lb_set_bead_launch: lanes x largest chain must not exceed 512");
+    if (beads_per_thread != 1 && beads_per_thread != 2)
+        return ctx->fail(LB_ERR_ARG, "lb_set_bead_launch: beads_per_thread must be 1 or 2");
+    if (beads_per_thread == 2 && lanes > 1)
+        return ctx->fail(LB_ERR_ARG, "lb_set_bead_launch: two beads per thread take one lane per bead");
+    if (lanes * ((ctx->max_beads + beads_per_thread - 1) / beads_per_thread) > 512)
+        return ctx->fail(LB_ERR_ARG, "lb_set_bead_launch: lanes x beads per thread layout exceeds 512 threads");
     ctx->bead_lanes = lanes;
+    ctx->bead_bpt = beads_per_thread;
     if (ctx->graph) {
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;

@@ -133,6 +133,7 @@ struct BeadParams {
     int32_t max_beads;    // largest chain of the launch (shared-memory strides)
     int32_t noise_chunk;  // substeps whose noise is drawn at once
     int32_t lanes;        // threads per bead in the MD substeps (1, 2, 4 or 8)
+    int32_t beads_per_thread;  // beads an MD thread holds (1 or 2)
 };
 
 struct ForcedParams {
@@ -152,7 +153,7 @@ struct ForcedParams {
 template <int ST>
 struct Launch {
     static cudaError_t stream_collide(const SCParams& p, int kernel, int threads, int ctas, int vw, cudaStream_t s);
-    static cudaError_t bead_couple(const BeadParams& p, int nchains, int max_beads, int lanes, cudaStream_t s);
+    static cudaError_t bead_couple(const BeadParams& p, int nchains, int max_beads, int lanes, int bpt, cudaStream_t s);
     static cudaError_t forced(const ForcedParams& p, cudaStream_t s);
     static cudaError_t init(void* A, const BoxDev* boxes, int box, int64_t n3, const void* u0, cudaStream_t s);
     static cudaError_t fields(const void* A, const BoxDev* boxes, int box, int64_t n3, int what, void* dst,

@@ -269,7 +269,7 @@ __device__ __forceinline__ void moments(const A f[kQ], A& drho, A j[3])
 __device__ __forceinline__ void set_status(int32_t* st, int code) { atomicCAS(st, 0, code); }
 
 constexpr int kMaxTasks = 48;           // pair tasks (bonds + Verlet neighbours) per bead
-constexpr int kNoiseChunk = 25;         // substeps whose noise is drawn at once (at most)
+constexpr int kNoiseChunk = 64;         // substeps whose noise is drawn at once (at most)
 constexpr int kBeadThreadsMax = 2 * kMaxBeads;  // 512: two MD lanes per bead at the largest chain
 constexpr size_t kBeadDynMax = 160 * 1024;      // dynamic shared memory budget of the bead kernel
 
@@ -317,6 +317,234 @@ __device__ __forceinline__ bool bar_or(int id, int nthreads, bool v)
         : "r"((uint32_t)v), "r"(id), "r"(nthreads)
         : "memory");
     return r != 0;
+}
+
+// MD substeps of one chain (symplectic Euler), the fluid velocity frozen over
+// the LB step.  Each MD thread holds B beads (bead j at slot + j G); L = p.lanes
+// consecutive threads share one bead slot.  Each lane owns a list of pair
+// tasks of its bead in shared memory -- lane 0 the bond to bead - 1, lane 1
+// (lane 0 when L = 1) the bond to bead + 1, then the WCA neighbours it found --
+// so the serial part of a substep is about one pair force per bead; the lanes
+// sum the force by shuffles and all of them apply the same update (lane 0
+// publishes the position).  Velocity, displacement since the start of the step
+// and the momentum handed to the fluid stay in registers; positions (start +
+// displacement, relative to bead 0's start-of-step position) are
+// double-buffered in shared memory as 4-vectors.  One barrier over the MD
+// threads per substep -- a warp vote when they fit one warp -- publishes the
+// new positions and ORs the flags "some bead left half the Verlet skin" and
+// "error".  The noise of a chunk of substeps is drawn up front by every
+// thread.  Returns an error code (0 = none); all threads return the same.
+template <class MT, int B>
+__device__ __forceinline__ int md_substeps(const BeadParams& p, const ChainDev& ch, int N, int64_t n, int b, MT* sXbuf,
+                                        MT (*sU)[3], MT (*sV)[3], double (*sR)[3], MT (*sP)[3],
+                                        unsigned char (*sNb)[kMaxTasks], int* sErrP)
+{
+    using V4 = typename Vec4<MT>::T;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int maxb = p.max_beads;
+    const int L = p.lanes, lshift = __ffs(L) - 1;
+    const int nslot = (N + B - 1) / B;
+    const int nmd = ((nslot << lshift) + 31) & ~31;  // MD threads: whole warps
+    const bool md = tid < nmd;
+    const int slot = tid >> lshift, lane = tid & (L - 1);
+    const int G = nmd >> lshift;  // slots per bead round
+    V4* sX4 = reinterpret_cast<V4*>(sXbuf);  // [2][maxb] positions
+    V4* sXi = sX4 + 2 * maxb;                // [chunk][N] noise
+    // constants from the chain record (worked out on the host in FP64)
+    const MT* mc;
+    if constexpr (sizeof(MT) == 8) mc = reinterpret_cast<const MT*>(ch.md_d);
+    else mc = reinterpret_cast<const MT*>(ch.md_f);
+    const MT dt = mc[kMdDt], dtm = mc[kMdDtm], namp = mc[kMdNamp];
+    const MT R02 = mc[kMdR02], inv_R02 = mc[kMdInvR02], kf = mc[kMdKf], zeta = mc[kMdZeta];
+    const bool wca = ch.eps > 0.0;
+    const MT sig2 = mc[kMdSig2], rc2 = mc[kMdRc2], e24 = mc[kMdE24];
+    const MT rl2 = mc[kMdRl2];  // Verlet radius: WCA cut-off 2^(1/6) sigma + skin
+    const MT half_skin2 = mc[kMdHalfSkin2];
+    const int cap = kMaxTasks / L;  // task slots of one lane
+    int bead[B];
+    bool own[B];
+    MT X0[B][3], U[B][3], V[B][3], D[B][3], P[B][3], Xref[B][3];
+    int bondA[B], bondB[B], nfene[B], ntask[B];
+#pragma unroll
+    for (int j = 0; j < B; j++) {
+        bead[j] = slot + j * G;
+        own[j] = md && bead[j] < N;
+        const int bj = own[j] ? bead[j] : 0;
+        const V4 x0 = sX4[bj];
+        X0[j][0] = x0.x;
+        X0[j][1] = x0.y;
+        X0[j][2] = x0.z;
+        for (int a = 0; a < 3; a++) {
+            U[j][a] = own[j] ? sU[bj][a] : MT(0);
+            V[j][a] = own[j] ? sV[bj][a] : MT(0);
+            D[j][a] = P[j][a] = MT(0);
+            Xref[j][a] = X0[j][a];
+        }
+        // bond (FENE) tasks first: lane 0 the bond to bead - 1, lane 1 the
+        // bond to bead + 1; a single lane holds both
+        bondA[j] = bondB[j] = -1;
+        if (own[j]) {
+            if (L == 1) {
+                if (bj > 0) bondA[j] = bj - 1;
+                if (bj + 1 < N) bondB[j] = bj + 1;
+            } else if (lane == 0 && bj > 0) {
+                bondA[j] = bj - 1;
+            } else if (lane == 1 && bj + 1 < N) {
+                bondA[j] = bj + 1;
+            }
+            if (bondA[j] < 0) {
+                bondA[j] = bondB[j];
+                bondB[j] = -1;
+            }
+        }
+        nfene[j] = (bondA[j] >= 0 ? 1 : 0) + (bondB[j] >= 0 ? 1 : 0);
+        ntask[j] = nfene[j];
+    }
+    MT fext[3];
+    for (int a = 0; a < 3; a++) fext[a] = lane == 0 ? (MT)ch.f_ext[a] : MT(0);
+    // errors of substep s go to sErrP[s & 1]: a thread that has passed the
+    // barrier of substep s can write next only to the other word, so every MD
+    // thread reads the same value after that barrier and all stop together
+    if (tid < 2) sErrP[tid] = 0;
+    __syncthreads();
+    auto sync_or = [&](bool v) -> bool {
+        if (nmd == 32) {  // one warp: order the shared-memory writes, then vote
+            __syncwarp();
+            return __any_sync(0xffffffffu, v);
+        }
+        return bar_or(1, nmd, v);
+    };
+    bool rebuild = true;  // lists out of date
+    const int chunk = namp > MT(0) ? p.noise_chunk : ch.n_md;
+    for (int c0 = 0; c0 < ch.n_md; c0 += chunk) {
+        const int nc = min(chunk, ch.n_md - c0);
+        if (namp > MT(0)) {
+            __syncthreads();  // the previous chunk's noise is consumed
+            for (int w = tid; w < nc * N; w += nthr) {
+                const int sb = w / N, bb = w - sb * N;
+                uint32_t x[4] = {(uint32_t)n, (uint32_t)(c0 + sb), (uint32_t)bb, (uint32_t)b};
+                philox4x32_10(x, (uint32_t)ch.seed, (uint32_t)(ch.seed >> 32));
+                V4 xi;
+                xi.x = unit_uniform_t<MT>(x[0]);
+                xi.y = unit_uniform_t<MT>(x[1]);
+                xi.z = unit_uniform_t<MT>(x[2]);
+                xi.w = MT(0);
+                sXi[sb * N + bb] = xi;
+            }
+            __syncthreads();
+        }
+        if (md) {
+            for (int sb = 0; sb < nc; sb++) {
+                const int sub = c0 + sb;
+                const V4* Xc = sX4 + (sub & 1) * maxb;
+                V4* Xn = sX4 + ((sub + 1) & 1) * maxb;
+                bool flag = false;
+                MT F[B][3], X[B][3];
+#pragma unroll
+                for (int j = 0; j < B; j++) {
+                    for (int a = 0; a < 3; a++) X[j][a] = X0[j][a] + D[j][a];  // == Xc[bead]
+                    if (rebuild && own[j]) {  // lane r scans partners r, r + L, ... after its bonds
+                        unsigned char* tasks = &sNb[bead[j]][lane * cap];
+                        ntask[j] = 0;
+                        if (bondA[j] >= 0) tasks[ntask[j]++] = (unsigned char)bondA[j];
+                        if (bondB[j] >= 0) tasks[ntask[j]++] = (unsigned char)bondB[j];
+                        int found = 0;
+                        if (wca)
+                            for (int b2 = lane; b2 < N; b2 += L) {
+                                if (b2 == bead[j]) continue;
+                                const V4 q = Xc[b2];
+                                const MT dx = X[j][0] - q.x, dy = X[j][1] - q.y, dz = X[j][2] - q.z;
+                                if (dx * dx + dy * dy + dz * dz < rl2) {
+                                    if (ntask[j] < cap) tasks[ntask[j]++] = (unsigned char)b2;
+                                    found++;
+                                }
+                            }
+                        if (nfene[j] + found > cap) {  // more neighbours than the list holds
+                            sErrP[sub & 1] = LB_ERR_CHAIN;
+                            flag = true;
+                        }
+                        for (int a = 0; a < 3; a++) Xref[j][a] = X[j][a];
+                    }
+                    // pair forces, one code path for both laws, force on this
+                    // bead = fac (X - X_partner):
+                    //   FENE: fac = -k / (1 - r^2/R0^2)
+                    //   WCA:  fac = 24 eps (2 (s/r)^12 - (s/r)^6) / r^2, r < 2^(1/6) s
+                    // Both beads of a pair evaluate the same r^2 from exactly
+                    // negated differences, so the two forces cancel exactly.
+                    for (int a = 0; a < 3; a++) F[j][a] = fext[a];
+                    if (own[j]) {
+                        const unsigned char* tasks = &sNb[bead[j]][lane * cap];
+                        for (int k = 0; k < ntask[j]; k++) {
+                            const bool fene = k < nfene[j];
+                            const V4 q = Xc[tasks[k]];
+                            const MT rx = X[j][0] - q.x, ry = X[j][1] - q.y, rz = X[j][2] - q.z;
+                            const MT r2 = rx * rx + ry * ry + rz * rz;
+                            if (fene && r2 >= R02) {
+                                sErrP[sub & 1] = LB_ERR_FENE;
+                                flag = true;
+                            }
+                            const MT inv = recip(fene ? MT(1) - r2 * inv_R02 : r2);
+                            const MT s2 = sig2 * inv, s6 = s2 * s2 * s2;
+                            const MT fac = fene ? -kf * inv : (r2 < rc2 ? e24 * (MT(2) * s6 * s6 - s6) * inv : MT(0));
+                            F[j][0] += fac * rx;
+                            F[j][1] += fac * ry;
+                            F[j][2] += fac * rz;
+                        }
+                    }
+                }
+                rebuild = false;
+                for (int o = 1; o < L; o <<= 1)  // every lane of an MD warp takes part; xor < L stays in the bead
+#pragma unroll
+                    for (int j = 0; j < B; j++)
+                        for (int a = 0; a < 3; a++) F[j][a] += __shfl_xor_sync(0xffffffffu, F[j][a], o);
+#pragma unroll
+                for (int j = 0; j < B; j++) {
+                    if (!own[j]) continue;
+                    const V4 xi = namp > MT(0) ? sXi[sb * N + bead[j]] : V4{};
+                    const MT xin[3] = {xi.x, xi.y, xi.z};
+                    MT moved = MT(0), xn[3];
+                    for (int a = 0; a < 3; a++) {
+                        const MT ffric = -zeta * (V[j][a] - U[j][a]);
+                        const MT fnoise = namp * xin[a];
+                        V[j][a] += dtm * (F[j][a] + ffric + fnoise);
+                        D[j][a] += dt * V[j][a];
+                        P[j][a] -= (ffric + fnoise) * dt;
+                        xn[a] = X0[j][a] + D[j][a];
+                        const MT d = xn[a] - Xref[j][a];
+                        moved += d * d;
+                    }
+                    if (lane == 0) {
+                        V4 w;
+                        w.x = xn[0];
+                        w.y = xn[1];
+                        w.z = xn[2];
+                        w.w = MT(0);
+                        Xn[bead[j]] = w;
+                    }
+                    if (wca && moved > half_skin2) flag = true;
+                }
+                // publish Xn; any flag: rebuild the lists, or stop on an error
+                if (sync_or(flag)) {
+                    if (sErrP[sub & 1]) break;
+                    rebuild = true;
+                }
+            }
+        }
+        __syncthreads();
+        if (sErrP[0] || sErrP[1]) break;
+    }
+    const int err = sErrP[0] ? sErrP[0] : sErrP[1];
+    if (err) return err;
+#pragma unroll
+    for (int j = 0; j < B; j++)
+        if (own[j] && lane == 0)
+            for (int a = 0; a < 3; a++) {
+                sR[bead[j]][a] += (double)D[j][a];
+                sV[bead[j]][a] = V[j][a];
+                sP[bead[j]][a] = P[j][a];
+            }
+    __syncthreads();
+    return 0;
 }
 
 template <int ST>
@@ -413,199 +641,16 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     }
     __syncthreads();
 
-    // 3. MD substeps (symplectic Euler), fluid velocity frozen over the step.
-    //    L = p.lanes consecutive threads per bead (1, 2, 4 or 8).  Each lane
-    //    owns a list of pair tasks of its bead in shared memory -- lane 0 the
-    //    bond to bead - 1, lane 1 (lane 0 when L = 1) the bond to bead + 1,
-    //    then the WCA neighbours it found -- so the serial part of a substep is
-    //    about one pair force; the lanes sum the force by shuffles and all of
-    //    them apply the same update (lane 0 publishes the position).  Velocity,
-    //    displacement since the start of the step and the momentum handed to
-    //    the fluid stay in registers; positions (start + displacement,
-    //    relative to bead 0's start-of-step position) are double-buffered in
-    //    shared memory as 4-vectors, one 16- or 32-byte load per partner.  One
-    //    named barrier over the MD threads per substep publishes the new
-    //    positions and ORs the flags "some bead left half the Verlet skin" and
-    //    "error".  The noise of a chunk of substeps is drawn up front by every
-    //    thread; the FP64 position is updated once at the end.
+    // 3. MD substeps (md_substeps below)
     {
-    using V4 = typename Vec4<MT>::T;
-    const int maxb = p.max_beads;
-    const int L = p.lanes, lshift = __ffs(L) - 1;
-    const int nmd = (N * L + 31) & ~31;  // MD threads: whole warps
-    const bool md = tid < nmd;
-    const int bead = tid >> lshift, lane = tid & (L - 1);
-    const bool own = bead < N;
-    V4* sX4 = reinterpret_cast<V4*>(sXbuf);  // [2][maxb] positions
-    V4* sXi = sX4 + 2 * maxb;                // [chunk][N] noise
-    // constants from the chain record (worked out on the host in FP64)
-    const MT* mc;
-    if constexpr (sizeof(MT) == 8) mc = reinterpret_cast<const MT*>(ch.md_d);
-    else mc = reinterpret_cast<const MT*>(ch.md_f);
-    const MT dt = mc[kMdDt], dtm = mc[kMdDtm], namp = mc[kMdNamp];
-    const MT R02 = mc[kMdR02], inv_R02 = mc[kMdInvR02], kf = mc[kMdKf], zeta = mc[kMdZeta];
-    const bool wca = ch.eps > 0.0;
-    const MT sig2 = mc[kMdSig2], rc2 = mc[kMdRc2], e24 = mc[kMdE24];
-    const MT rl2 = mc[kMdRl2];  // Verlet radius: WCA cut-off 2^(1/6) sigma + skin
-    const MT half_skin2 = mc[kMdHalfSkin2];
-    const int cap = kMaxTasks / L;  // task slots of one lane
-    unsigned char* tasks = &sNb[bead < kMaxBeads ? bead : 0][lane * cap];
-    MT X0[3], U[3], V[3], D[3] = {0, 0, 0}, P[3] = {0, 0, 0}, Xref[3], fext[3];
-    {
-        const V4 x0 = own ? sX4[bead] : V4{};
-        X0[0] = x0.x;
-        X0[1] = x0.y;
-        X0[2] = x0.z;
-    }
-    for (int a = 0; a < 3; a++) {
-        U[a] = own ? sU[bead][a] : MT(0);
-        V[a] = own ? sV[bead][a] : MT(0);
-        fext[a] = lane == 0 ? (MT)ch.f_ext[a] : MT(0);
-        Xref[a] = X0[a];
-    }
-    // this lane's bond (FENE) tasks, first in its list: lane 0 the bond to
-    // bead - 1, lane 1 the bond to bead + 1; a single lane holds both
-    int bondA = -1, bondB = -1;
-    if (L == 1) {
-        if (bead > 0) bondA = bead - 1;
-        if (bead + 1 < N) bondB = bead + 1;
-    } else if (lane == 0 && bead > 0) {
-        bondA = bead - 1;
-    } else if (lane == 1 && bead + 1 < N) {
-        bondA = bead + 1;
-    }
-    if (bondA < 0) {
-        bondA = bondB;
-        bondB = -1;
-    }
-    const int nfene = (bondA >= 0 ? 1 : 0) + (bondB >= 0 ? 1 : 0);
-    // errors of substep s go to sErrP[s & 1]: a thread that has passed the
-    // barrier of substep s can write next only to the other word, so every MD
-    // thread reads the same value after that barrier and all stop together
-    __shared__ int sErrP[2];
-    if (tid < 2) sErrP[tid] = 0;
-    __syncthreads();
-    int ntask = nfene;      // tasks of this lane: its bonds, then its WCA neighbours
-    bool rebuild = true;    // lists out of date
-    const int chunk = namp > MT(0) ? p.noise_chunk : ch.n_md;
-    for (int c0 = 0; c0 < ch.n_md; c0 += chunk) {
-        const int nc = min(chunk, ch.n_md - c0);
-        if (namp > MT(0)) {
-            __syncthreads();  // the previous chunk's noise is consumed
-            for (int w = tid; w < nc * N; w += nthr) {
-                const int sb = w / N, bb = w - sb * N;
-                uint32_t x[4] = {(uint32_t)n, (uint32_t)(c0 + sb), (uint32_t)bb, (uint32_t)b};
-                philox4x32_10(x, (uint32_t)ch.seed, (uint32_t)(ch.seed >> 32));
-                V4 xi;
-                xi.x = unit_uniform_t<MT>(x[0]);
-                xi.y = unit_uniform_t<MT>(x[1]);
-                xi.z = unit_uniform_t<MT>(x[2]);
-                xi.w = MT(0);
-                sXi[sb * N + bb] = xi;
-            }
-            __syncthreads();
+        __shared__ int sErrP[2];
+        const int err = p.beads_per_thread == 2
+                            ? md_substeps<MT, 2>(p, ch, N, n, b, sXbuf, sU, sV, sR, sP, sNb, sErrP)
+                            : md_substeps<MT, 1>(p, ch, N, n, b, sXbuf, sU, sV, sR, sP, sNb, sErrP);
+        if (err) {
+            if (tid == 0) set_status(&p.status[b], err);
+            return;
         }
-        if (md) {
-            for (int sb = 0; sb < nc; sb++) {
-                const int sub = c0 + sb;
-                const V4* Xc = sX4 + (sub & 1) * maxb;
-                V4* Xn = sX4 + ((sub + 1) & 1) * maxb;
-                bool flag = false;
-                MT X[3];
-                for (int a = 0; a < 3; a++) X[a] = X0[a] + D[a];  // == Xc[bead]
-                if (rebuild && own) {  // lane r scans partners r, r + L, ... after its bonds
-                    ntask = 0;
-                    if (bondA >= 0) tasks[ntask++] = (unsigned char)bondA;
-                    if (bondB >= 0) tasks[ntask++] = (unsigned char)bondB;
-                    int found = 0;
-                    if (wca)
-                        for (int b2 = lane; b2 < N; b2 += L) {
-                            if (b2 == bead) continue;
-                            const V4 q = Xc[b2];
-                            const MT dx = X[0] - q.x, dy = X[1] - q.y, dz = X[2] - q.z;
-                            if (dx * dx + dy * dy + dz * dz < rl2) {
-                                if (ntask < cap) tasks[ntask++] = (unsigned char)b2;
-                                found++;
-                            }
-                        }
-                    if (nfene + found > cap) {  // more neighbours than the list holds
-                        sErrP[sub & 1] = LB_ERR_CHAIN;
-                        flag = true;
-                    }
-                    for (int a = 0; a < 3; a++) Xref[a] = X[a];
-                }
-                rebuild = false;
-                // pair forces, one code path for both laws, force on this bead
-                // = fac (X - X_partner):
-                //   FENE: fac = -k / (1 - r^2/R0^2)
-                //   WCA:  fac = 24 eps (2 (s/r)^12 - (s/r)^6) / r^2, r < 2^(1/6) s
-                // Both beads of a pair evaluate the same r^2 from exactly
-                // negated differences, so the two forces cancel exactly.
-                MT F[3] = {fext[0], fext[1], fext[2]};
-                if (own)
-                    for (int k = 0; k < ntask; k++) {
-                        const bool fene = k < nfene;
-                        const V4 q = Xc[tasks[k]];
-                        const MT rx = X[0] - q.x, ry = X[1] - q.y, rz = X[2] - q.z;
-                        const MT r2 = rx * rx + ry * ry + rz * rz;
-                        if (fene && r2 >= R02) {
-                            sErrP[sub & 1] = LB_ERR_FENE;
-                            flag = true;
-                        }
-                        const MT inv = recip(fene ? MT(1) - r2 * inv_R02 : r2);
-                        const MT s2 = sig2 * inv, s6 = s2 * s2 * s2;
-                        const MT fac = fene ? -kf * inv : (r2 < rc2 ? e24 * (MT(2) * s6 * s6 - s6) * inv : MT(0));
-                        F[0] += fac * rx;
-                        F[1] += fac * ry;
-                        F[2] += fac * rz;
-                    }
-                for (int o = 1; o < L; o <<= 1)  // every lane of an MD warp takes part; xor < L stays in the bead
-                    for (int a = 0; a < 3; a++) F[a] += __shfl_xor_sync(0xffffffffu, F[a], o);
-                if (own) {
-                    const V4 xi = namp > MT(0) ? sXi[sb * N + bead] : V4{};
-                    const MT xin[3] = {xi.x, xi.y, xi.z};
-                    MT moved = MT(0), xn[3];
-                    for (int a = 0; a < 3; a++) {
-                        const MT ffric = -zeta * (V[a] - U[a]);
-                        const MT fnoise = namp * xin[a];
-                        V[a] += dtm * (F[a] + ffric + fnoise);
-                        D[a] += dt * V[a];
-                        P[a] -= (ffric + fnoise) * dt;
-                        xn[a] = X0[a] + D[a];
-                        const MT d = xn[a] - Xref[a];
-                        moved += d * d;
-                    }
-                    if (lane == 0) {
-                        V4 w;
-                        w.x = xn[0];
-                        w.y = xn[1];
-                        w.z = xn[2];
-                        w.w = MT(0);
-                        Xn[bead] = w;
-                    }
-                    if (wca && moved > half_skin2) flag = true;
-                }
-                // publish Xn; any flag: rebuild the lists, or stop on an error
-                if (bar_or(1, nmd, flag)) {
-                    if (sErrP[sub & 1]) break;
-                    rebuild = true;
-                }
-            }
-        }
-        __syncthreads();
-        if (sErrP[0] || sErrP[1]) break;
-    }
-    if (sErrP[0] || sErrP[1]) {
-        if (tid == 0) set_status(&p.status[b], sErrP[0] ? sErrP[0] : sErrP[1]);
-        return;
-    }
-    if (own && lane == 0)
-        for (int a = 0; a < 3; a++) {
-            sR[bead][a] += (double)D[a];
-            sV[bead][a] = V[a];
-            sP[bead][a] = P[a];
-        }
-    __syncthreads();
     }
 
     // 4. centre of mass pinned at the box centre (one thread per bead; only
@@ -940,7 +985,7 @@ cudaError_t Launch<ST>::stream_collide(const SCParams& p, int kernel, int thread
 }
 
 template <int ST>
-cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, int max_beads, int lanes, cudaStream_t s)
+cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, int max_beads, int lanes, int bpt, cudaStream_t s)
 {
     if (nchains <= 0) return cudaSuccess;
     using MT = typename std::conditional<ST == kF64, double, float>::type;
@@ -954,15 +999,20 @@ cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, int max_be
     BeadParams q = p;
     q.max_beads = max_beads;
     q.noise_chunk = bead_noise_chunk<MT>(max_beads);
-    // lanes per bead in the MD phase (validated by the caller; 0 = default:
-    // four, halved until the block fits 512 threads)
+    // MD layout (validated by the caller): lanes per bead and beads per
+    // thread; 0 = default, eight lanes per bead, halved until the MD threads
+    // fit 512 (measured fastest for chains of 16 .. 64 beads)
     if (lanes <= 0) {
-        lanes = 4;
+        lanes = 8;
+        bpt = 1;
         while (lanes > 1 && lanes * max_beads > kBeadThreadsMax) lanes >>= 1;
     }
+    if (bpt != 2) bpt = 1;
     q.lanes = lanes;
-    int threads = (lanes * max_beads + 31) / 32 * 32;
-    if (threads < 64) threads = 64;
+    q.beads_per_thread = bpt;
+    // the MD threads, at least 256 for the gather, the noise and the spreading
+    int threads = (lanes * ((max_beads + bpt - 1) / bpt) + 31) / 32 * 32;
+    if (threads < 256) threads = 256;
     k_bead_couple<ST><<<nchains, threads, dyn, s>>>(q);
     return cudaGetLastError();
 }

@@ -204,29 +204,36 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const StagedTile<
     constexpr int H = Staged<ST, SPT>::kHalo;
     constexpr int C = kStagedConsumers;
     const int tid = threadIdx.x;
-    const int64_t s0 = th.s0;
+    // site indices of a box fit 32 bits (E <= 1024)
+    const int s0 = (int)th.s0;
     const BoxDev& bd = th.bd;
 
     const int Ei = bd.E;
-    const int64_t n3 = bd.n3;
+    const int n3 = (int)bd.n3;
     const uint64_t mE = bd.div_magic;
     const int per = bd.per_mask;
     const bool px = per & 1, py = per & 2, pz = per & 4;
     const E* Ab = reinterpret_cast<const E*>(p.A) + bd.f_off;
     E* Bb = reinterpret_cast<E*>(p.B) + bd.f_off;
 
+    // coordinates of site k (recomputed where needed rather than held in
+    // registers across the population loads)
+    auto coords = [&](int k, int& x, int& y, int& z) {
+        const int s = s0 + tid + k * C;
+        const int sc = s < n3 ? s : 0;
+        const int row = div_e(sc, mE);
+        x = sc - row * Ei;
+        z = div_e(row, mE);
+        y = row - z * Ei;
+    };
     int xs_[SPT], ys_[SPT], zs_[SPT];
     bool act[SPT], bnd[SPT];
     bool any_bnd = false;
 #pragma unroll
     for (int k = 0; k < SPT; k++) {
-        const int64_t s = s0 + tid + k * C;
-        act[k] = s < n3;
-        const int64_t sc = act[k] ? s : 0;
-        const int row = div_e(sc, mE);
-        const int x = (int)(sc - (int64_t)row * Ei);
-        const int z = div_e(row, mE);
-        const int y = row - z * Ei;
+        act[k] = s0 + tid + k * C < n3;
+        int x, y, z;
+        coords(k, x, y, z);
         xs_[k] = x;
         ys_[k] = y;
         zs_[k] = z;
@@ -293,8 +300,15 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const StagedTile<
 #pragma unroll
         for (int k = 0; k < SPT; k++) {
             if (bnd[k]) {
-                int pp, qq;
-                const int fc = owning_face(xs_[k], ys_[k], zs_[k], Ei, per, pp, qq);
+                int pp, qq, x, y, z;
+                if (PER) {
+                    x = xs_[k];
+                    y = ys_[k];
+                    z = zs_[k];
+                } else {
+                    coords(k, x, y, z);
+                }
+                const int fc = owning_face(x, y, z, Ei, per, pp, qq);
                 R ub[3];
                 boundary_velocity<R>(ring, p.ring_slot_elems, bd, fc, pp, qq, tw, ub);
                 add_mlp_residual<R>(p, bd, th.mlp_s, fc, pp, qq, ub);
@@ -328,7 +342,7 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const StagedTile<
             }
         }
         // population 0 and odd i at `out`, the even partner of a pair one row further
-        const int64_t row = (i > 0 && (i & 1) == 0) ? n3 : 0;
+        const int row = (i > 0 && (i & 1) == 0) ? n3 : 0;
         if (act[k]) out[row + k * C] = S::out(val);
     };
 #pragma unroll

@@ -88,7 +88,7 @@ def load(path: str | None = None, build_if_missing: bool = True):
         "lb_status": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
         "lb_current_step": (_i64, [_vp]),
         "lb_set_launch": (_i32, [_vp, _i32, _i32, _i32, _i32]),
-        "lb_set_bead_launch": (_i32, [_vp, _i32]),
+        "lb_set_bead_launch": (_i32, [_vp, _i32, _i32]),
         "lb_profile": (_i32, [_vp, _i32, _i32]),
         "lb_profile_read": (_i32, [_vp, ctypes.POINTER(_f64), ctypes.POINTER(_i64)]),
         "lb_last_error": (ctypes.c_char_p, [_vp]),
@@ -237,8 +237,8 @@ class Tracers:
     def lb_current_step(self):
         return int(self.lib.lb_current_step(self.ctx))
 
-    def lb_set_bead_launch(self, lanes=0):
-        _check(self.lib.lb_set_bead_launch(self.ctx, int(lanes)), self.ctx)
+    def lb_set_bead_launch(self, lanes=0, beads_per_thread=1):
+        _check(self.lib.lb_set_bead_launch(self.ctx, int(lanes), int(beads_per_thread)), self.ctx)
 
     def lb_set_launch(self, kernel=LB_KERNEL_STAGED, threads=0, ctas=0, sites_per_thread=0):
         _check(self.lib.lb_set_launch(self.ctx, int(kernel), int(threads), int(ctas), int(sites_per_thread)),

@@ -129,9 +129,9 @@ def test_bead_lanes_agree(lbt, storage):
     # same chain up to the order of the force sums
     c = Case(24, 0.8, 20, M=32, nbeads=40, kT=1e-4)
     runs = []
-    for lanes in (1, 2, 4, 8):
+    for lanes, bpt in ((1, 1), (1, 2), (2, 1), (4, 1), (8, 1)):
         r = GpuRunner(lbt, torch, [c], storage)
-        r.tr.lb_set_bead_launch(lanes)
+        r.tr.lb_set_bead_launch(lanes, bpt)
         r.step(20)
         runs.append((r.tr.chain(0, c.nbeads), r.tr.deviations(0)))
     (p0, v0), d0 = runs[0]
@@ -199,9 +199,11 @@ def test_fullsize_128_sampled_step(lbt):
         assert st == 0
         dref = Bref - w[:, None, None, None]
         assert np.abs(B - dref).max() < 2e-7
-        # the FP32 path runs the chain MD in FP32 (positions FP64): 50 substeps
-        # of FP32 forces of magnitude ~50 leave ~1e-6 in position
-        assert np.abs(pos1 - pref).max() < 1e-5 and np.abs(vel1 - vref).max() < 1e-4
+        # the FP32 path runs the chain MD in FP32 (positions FP64): FP32 bond
+        # forces of magnitude up to ~50 (2^-24 rounding, a 2-ulp fast
+        # reciprocal) drive 50 stiff substeps; the differences reach ~1e-6 in
+        # position and ~1e-4 in velocity
+        assert np.abs(pos1 - pref).max() < 1e-5 and np.abs(vel1 - vref).max() < 3e-4
 
 
 def test_error_flags_freeze_only_the_failing_box(lbt):
