@@ -29,7 +29,7 @@ constexpr int kStagedHaloBytes = 16;  // x-shift halo on each side of a row
 constexpr int kStagedConsumerWarps = 15;  // + the producer: four warps per scheduler
 constexpr int kStagedConsumers = kStagedConsumerWarps * 32;
 constexpr int kStagedThreads = kStagedConsumers + 32;  // + the producer warp
-constexpr int kStagedHeaderBytes = 2048;               // barriers and tile headers
+constexpr int kStagedHeaderBytes = 4096;               // barriers and tile headers
 constexpr int kStagedMaxStages = 6;
 
 // Tile geometry for SPT sites per consumer thread.  As many stages as fit in
@@ -147,11 +147,16 @@ struct StagedTile {
     R c[4];
     A om, om1, srcfac, drho_b;  // 1/tau, 1 - 1/tau, 1 - 1/(2 tau), rho_b - 1
 };
+// Consumers keep reading a tile's header after they have released its data
+// stage (early release), so headers live in a ring of twice the stages: tile
+// k uses header k mod 2S, which the producer rewrites for tile k + 2S only
+// after every consumer warp has released tile k + S -- that is, after each of
+// them has finished tile k (a warp takes the tiles in order).
 template <int ST>
 struct StagedHeader {
     uint64_t full[kStagedMaxStages];
     uint64_t empty[kStagedMaxStages];
-    StagedTile<ST> t[kStagedMaxStages];
+    StagedTile<ST> t[2 * kStagedMaxStages];
 };
 static_assert(sizeof(StagedHeader<kF64>) <= kStagedHeaderBytes, "header does not fit");
 static_assert(sizeof(StagedHeader<kF32>) <= kStagedHeaderBytes, "header does not fit");
@@ -384,13 +389,13 @@ __device__ __forceinline__ void staged_consume(const SCParams& p, unsigned char*
             // nothing arrived within a second: flag the box, let copies still in
             // flight land (one more bounded wait) and leave
             if ((threadIdx.x & 31) == 0) {
-                const int b = hd->t[st].box;
+                const int b = hd->t[k % (2 * G::kStages)].box;
                 atomicCAS(&p.status[b >= 0 && b < p.nboxes ? b : 0], 0, LB_ERR_TIMEOUT);
             }
             mbar_wait_bounded(&hd->full[st], phase);
             return;
         }
-        const StagedTile<ST>& th = hd->t[st];
+        const StagedTile<ST>& th = hd->t[k % (2 * G::kStages)];
         const int b = th.box;
         if (b < 0) return;  // end of work
         const int64_t s0 = th.s0;
@@ -439,7 +444,7 @@ __device__ __forceinline__ void staged_produce(const SCParams& p, unsigned char*
         if (k >= G::kStages && !mbar_wait_bounded(&hd->empty[st], (uint32_t)(((k / G::kStages) - 1) & 1))) return;
         const int64_t t = next;
         if (t >= p.total_tiles) {
-            hd->t[st].box = -1;
+            hd->t[k % (2 * G::kStages)].box = -1;
             mbar_arrive(&hd->full[st]);  // completes the phase with no bytes: end of work
             return;
         }
@@ -452,7 +457,7 @@ __device__ __forceinline__ void staged_produce(const SCParams& p, unsigned char*
             mlp_s = bd.mlp_row >= 0 ? mlp_substep(n, bd.K) : 0;
             last_b = b;
         }
-        StagedTile<ST>& th = hd->t[st];
+        StagedTile<ST>& th = hd->t[k % (2 * G::kStages)];
         static_assert(sizeof(BoxDev) % 8 == 0, "box record copied in 8-byte words");
         for (int w = 0; w < (int)(sizeof(BoxDev) / 8); w++)  // word by word: few live registers
             reinterpret_cast<uint64_t*>(&th.bd)[w] = reinterpret_cast<const uint64_t*>(&bd)[w];

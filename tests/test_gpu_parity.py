@@ -142,6 +142,24 @@ def test_bead_lanes_agree(lbt, storage):
         assert np.abs(p - p0).max() <= tol_p and np.abs(d - d0).max() <= tol_d
 
 
+@pytest.mark.parametrize("ctas", [0, 7])
+def test_batch_with_many_tiles_per_block_equals_single_boxes(lbt, ctas):
+    # four 64^3 Hermite boxes (K = 16): every persistent block takes tiles of
+    # several boxes in turn, so a tile header must stay valid while the next
+    # tile of another box is already being staged
+    cases = [Case(64, 0.8, 40, seed=s, M=64, K=16, time_interp=1) for s in range(4)]
+    rb = GpuRunner(lbt, torch, cases, ST32)
+    rb.tr.lb_set_launch(lbt.LB_KERNEL_STAGED, 0, ctas, 0)
+    rb.step(40)
+    for b in (0, 3):
+        r1 = GpuRunner(lbt, torch, [cases[b]], ST32)
+        r1.step(40)
+        assert np.array_equal(rb.tr.deviations(b), r1.tr.deviations(0)), b
+    u = rb.tr.fields(0)[1]
+    u_ref = cases[0].run_oracle().fields()[1]
+    assert rel_l2(interior(u), interior(u_ref)) <= 1e-5
+
+
 def test_batch_of_uneven_boxes_equals_single_boxes(lbt):
     cases = [Case(24, 0.8, 30, seed=1, M=32, nbeads=12), Case(16, 0.7, 30, seed=2, M=16),
              Case(32, 0.9, 30, seed=3, M=32, nbeads=20)]
