@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "liblbtracer.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 SOURCES = ["lbt_api.cu", "lbt_synth.cu", "lbt_inst_f64.cu", "lbt_inst_f32.cu", "lbt_inst_f16.cu", "lbt_inst_bf16.cu",
-           "lbt_noalloc.cu", "lbt_mlp.cu"]
+           "lbt_noalloc.cu", "lbt_mlp.cu", "lbt_mlp_tc.cu"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",
          "-Xcompiler", "-fPIC", "-I", CSRC, "-I", os.path.join(ROOT, "include")]
 

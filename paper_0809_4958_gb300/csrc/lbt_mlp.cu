@@ -431,6 +431,7 @@ cudaError_t mlp_forward(const void* X, int64_t rows, const void* params, int K, 
 {
     const MlpLayout L = mlp_layout(K);
     const bool save = H1 != nullptr;
+    if (!save) return mlp_forward_tc(X, rows, params, K, Y, nullptr, s);  // inference: tcgen05
     if (K == 16) return save ? forward_t<48, true>(X, rows, params, L, Y, H1, H2, s) : forward_t<48, false>(X, rows, params, L, Y, H1, H2, s);
     if (K == 8) return save ? forward_t<24, true>(X, rows, params, L, Y, H1, H2, s) : forward_t<24, false>(X, rows, params, L, Y, H1, H2, s);
     return cudaErrorInvalidValue;

@@ -43,6 +43,10 @@ MlpTrain mlp_train_layout(int K, int64_t batch_rows);
 
 cudaError_t mlp_forward(const void* X, int64_t rows, const void* params, int K, float* Y, float* H1, float* H2,
                         cudaStream_t s);
+// Inference forward on the tcgen05 tensor cores (lbt_mlp_tc.cu); err (device,
+// may be null) receives LB_ERR_TIMEOUT if an MMA does not complete.
+cudaError_t mlp_forward_tc(const void* X, int64_t rows, const void* params, int K, float* Y, int32_t* err,
+                           cudaStream_t s);
 cudaError_t mlp_features(const MlpFeatureSet* sets_dev, int nsets, int64_t total_rows, double u_max, int real_f64,
                          void* X, cudaStream_t s);
 // Features of one face set passed by value (6 E^2 rows from row 0).
