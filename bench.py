@@ -67,6 +67,22 @@ def dist_env():
     return rank, world, local
 
 
+def whole_job(units, ms, device=None):
+    """Whole-job totals over the ranks of the process group: the site
+    updates every rank made (summed) and the slowest rank's time (max).  The
+    boxes of different ranks are independent, so this is the only exchange;
+    without a group of more than one rank it returns its arguments."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(units), float(ms)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    m = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(m.item())
+
+
 def alg_bytes_per_launch(E, s_elem, s_real, time_interp=0):
     """Algorithmic bytes of one stream-collide launch over one box with
     velocity faces: interior sites read and write 19 populations, boundary
@@ -338,14 +354,11 @@ def main():
     tr.lb_profile(0)
     sc_ms, sc_n = tr.lb_profile_read()
     tr.lb_sync()
-    ms = ev0.elapsed_time(ev1)
+    units, ms = whole_job(E ** 3 * args.steps, ev0.elapsed_time(ev1), dev)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     ms_per_step = ms / args.steps
-    value = world * E ** 3 * args.steps / (ms * 1e-3) / 1e6
+    value = units / (ms * 1e-3) / 1e6
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
@@ -375,12 +388,8 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        ms2 = max(ev0.elapsed_time(ev1), wall * 1e3)
-        if world > 1:
-            t = torch.tensor([ms2], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms2 = float(t.item())
-        e2e = {"value": world * E ** 3 * e2e_steps / (ms2 * 1e-3) / 1e6, "unit": UNIT,
+        units2, ms2 = whole_job(E ** 3 * e2e_steps, max(ev0.elapsed_time(ev1), wall * 1e3), dev)
+        e2e = {"value": units2 / (ms2 * 1e-3) / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": 6 * 3 * E * E * s_real, "d2h_bytes_per_step": 2 * w["nbeads"] * 3 * 8,
                "steps": e2e_steps}
         tr2.close()
@@ -508,12 +517,8 @@ def run_batch(args):
     clk = clocks.stop()
     sc_ms, sc_n = tr.lb_profile_read()  # the kernels of the last graph replay
     tr.lb_sync()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * sites * steps / (ms * 1e-3) / 1e6
+    units, ms = whole_job(sites * steps, ev0.elapsed_time(ev1), dev)
+    value = units / (ms * 1e-3) / 1e6
     if rank == 0:
         peak, peak_kind = measured_peaks()
         alg = sum(alg_bytes_per_launch(int(E), 4, 4) for E in edges)

@@ -689,6 +689,8 @@ int32_t chain_couple(lb_ctx* ctx, int32_t box, const lb_chain_desc* d, const dou
         c[kMdE24] = 24.0 * d->eps;
         c[kMdRl2] = rl * rl;
         c[kMdHalfSkin2] = 0.25 * skin * skin;
+        c[kMdInvN] = 1.0 / d->nbeads;
+        c[kMdSkinComp2] = c[kMdHalfSkin2] / 3.0;
         for (int k = 0; k < kMdConsts; k++) ch.md_f[k] = (float)c[k];
         // FP32 derived constants rounded from their own FP32 operands, as the
         // device computed them before

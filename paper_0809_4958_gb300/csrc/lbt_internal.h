@@ -56,6 +56,8 @@ enum MdConst {
     kMdE24,       // 24 eps
     kMdRl2,       // Verlet list radius squared, (2^(1/6) sigma + skin)^2
     kMdHalfSkin2, // (skin / 2)^2
+    kMdInvN,      // 1 / nbeads (centre-of-mass averages)
+    kMdSkinComp2, // (skin / 2)^2 / 3: per-component displacement bound
     kMdConsts
 };
 

@@ -269,6 +269,7 @@ __device__ __forceinline__ void moments(const A f[kQ], A& drho, A j[3])
 __device__ __forceinline__ void set_status(int32_t* st, int code) { atomicCAS(st, 0, code); }
 
 constexpr int kMaxTasks = 48;           // pair tasks (bonds + Verlet neighbours) per bead
+constexpr int kMaxStencilNb = 24;       // listed beads with a nearby stencil (more: scan all)
 constexpr int kNoiseChunk = 64;         // substeps whose noise is drawn at once (at most)
 constexpr int kBeadThreadsMax = 2 * kMaxBeads;  // 512: two MD lanes per bead at the largest chain
 constexpr size_t kBeadDynMax = 160 * 1024;      // dynamic shared memory budget of the bead kernel
@@ -303,6 +304,54 @@ template <class MT>
 inline size_t bead_dyn_bytes(int maxb)
 {
     return 4 * sizeof(MT) * (size_t)maxb * (2 + bead_noise_chunk<MT>(maxb));
+}
+
+// Pair-force constants of a chain in the MD precision.
+template <class MT>
+struct PairConsts {
+    MT R02, inv_R02, kf, sig2, rc2, e24;
+};
+
+// Pair force on a bead at X from the partner at q, added to F, in one code
+// path for both laws (force = fac (X - q)):
+//   FENE: fac = -k / (1 - r^2/R0^2)
+//   WCA:  fac = 24 eps (2 (s/r)^12 - (s/r)^6) / r^2, r < 2^(1/6) s
+// Both beads of a pair evaluate the same r^2 from exactly negated
+// differences, so the two forces cancel exactly.  Returns true for a bond
+// stretched to R0 or beyond.
+template <class MT>
+__device__ __forceinline__ bool pair_force(const MT X[3], const typename Vec4<MT>::T& q, bool fene,
+                                           const PairConsts<MT>& c, MT F[3])
+{
+    const MT rx = X[0] - q.x, ry = X[1] - q.y, rz = X[2] - q.z;
+    const MT r2 = rx * rx + ry * ry + rz * rz;
+    const MT inv = recip(fene ? MT(1) - r2 * c.inv_R02 : r2);
+    const MT s2 = c.sig2 * inv, s6 = s2 * s2 * s2;
+    const MT fac = fene ? -c.kf * inv : (r2 < c.rc2 ? c.e24 * (MT(2) * s6 * s6 - s6) * inv : MT(0));
+    F[0] += fac * rx;
+    F[1] += fac * ry;
+    F[2] += fac * rz;
+    return fene && r2 >= c.R02;
+}
+
+// Noise of substeps c0 .. c0 + nc - 1 for all N beads (three unit-variance
+// uniforms per bead and substep, Philox4x32-10 with counter (step, substep,
+// bead, box) and the chain seed as key), spread over the block's threads.
+template <class MT>
+__device__ __forceinline__ void md_noise(typename Vec4<MT>::T* sXi, int64_t n, int c0, int nc, int N, int b, uint64_t seed)
+{
+    using V4 = typename Vec4<MT>::T;
+    for (int w = threadIdx.x; w < nc * N; w += blockDim.x) {
+        const int sb = w / N, bb = w - sb * N;
+        uint32_t x[4] = {(uint32_t)n, (uint32_t)(c0 + sb), (uint32_t)bb, (uint32_t)b};
+        philox4x32_10(x, (uint32_t)seed, (uint32_t)(seed >> 32));
+        V4 xi;
+        xi.x = unit_uniform_t<MT>(x[0]);
+        xi.y = unit_uniform_t<MT>(x[1]);
+        xi.z = unit_uniform_t<MT>(x[2]);
+        xi.w = MT(0);
+        sXi[sb * N + bb] = xi;
+    }
 }
 
 // Barrier over the first nthreads threads (whole warps) of the block with id
@@ -340,7 +389,7 @@ __device__ __forceinline__ int md_substeps(const BeadParams& p, const ChainDev& 
                                         unsigned char (*sNb)[kMaxTasks], int* sErrP)
 {
     using V4 = typename Vec4<MT>::T;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = threadIdx.x;
     const int maxb = p.max_beads;
     const int L = p.lanes, lshift = __ffs(L) - 1;
     const int nslot = (N + B - 1) / B;
@@ -355,9 +404,9 @@ __device__ __forceinline__ int md_substeps(const BeadParams& p, const ChainDev& 
     if constexpr (sizeof(MT) == 8) mc = reinterpret_cast<const MT*>(ch.md_d);
     else mc = reinterpret_cast<const MT*>(ch.md_f);
     const MT dt = mc[kMdDt], dtm = mc[kMdDtm], namp = mc[kMdNamp];
-    const MT R02 = mc[kMdR02], inv_R02 = mc[kMdInvR02], kf = mc[kMdKf], zeta = mc[kMdZeta];
+    const MT zeta = mc[kMdZeta];
+    const PairConsts<MT> pc{mc[kMdR02], mc[kMdInvR02], mc[kMdKf], mc[kMdSig2], mc[kMdRc2], mc[kMdE24]};
     const bool wca = ch.eps > 0.0;
-    const MT sig2 = mc[kMdSig2], rc2 = mc[kMdRc2], e24 = mc[kMdE24];
     const MT rl2 = mc[kMdRl2];  // Verlet radius: WCA cut-off 2^(1/6) sigma + skin
     const MT half_skin2 = mc[kMdHalfSkin2];
     const int cap = kMaxTasks / L;  // task slots of one lane
@@ -420,17 +469,7 @@ __device__ __forceinline__ int md_substeps(const BeadParams& p, const ChainDev& 
         const int nc = min(chunk, ch.n_md - c0);
         if (namp > MT(0)) {
             __syncthreads();  // the previous chunk's noise is consumed
-            for (int w = tid; w < nc * N; w += nthr) {
-                const int sb = w / N, bb = w - sb * N;
-                uint32_t x[4] = {(uint32_t)n, (uint32_t)(c0 + sb), (uint32_t)bb, (uint32_t)b};
-                philox4x32_10(x, (uint32_t)ch.seed, (uint32_t)(ch.seed >> 32));
-                V4 xi;
-                xi.x = unit_uniform_t<MT>(x[0]);
-                xi.y = unit_uniform_t<MT>(x[1]);
-                xi.z = unit_uniform_t<MT>(x[2]);
-                xi.w = MT(0);
-                sXi[sb * N + bb] = xi;
-            }
+            md_noise<MT>(sXi, n, c0, nc, N, b, ch.seed);
             __syncthreads();
         }
         if (md) {
@@ -465,30 +504,16 @@ __device__ __forceinline__ int md_substeps(const BeadParams& p, const ChainDev& 
                         }
                         for (int a = 0; a < 3; a++) Xref[j][a] = X[j][a];
                     }
-                    // pair forces, one code path for both laws, force on this
-                    // bead = fac (X - X_partner):
-                    //   FENE: fac = -k / (1 - r^2/R0^2)
-                    //   WCA:  fac = 24 eps (2 (s/r)^12 - (s/r)^6) / r^2, r < 2^(1/6) s
-                    // Both beads of a pair evaluate the same r^2 from exactly
-                    // negated differences, so the two forces cancel exactly.
+                    // pair forces (pair_force above)
                     for (int a = 0; a < 3; a++) F[j][a] = fext[a];
                     if (own[j]) {
                         const unsigned char* tasks = &sNb[bead[j]][lane * cap];
-                        for (int k = 0; k < ntask[j]; k++) {
-                            const bool fene = k < nfene[j];
-                            const V4 q = Xc[tasks[k]];
-                            const MT rx = X[j][0] - q.x, ry = X[j][1] - q.y, rz = X[j][2] - q.z;
-                            const MT r2 = rx * rx + ry * ry + rz * rz;
-                            if (fene && r2 >= R02) {
-                                sErrP[sub & 1] = LB_ERR_FENE;
-                                flag = true;
-                            }
-                            const MT inv = recip(fene ? MT(1) - r2 * inv_R02 : r2);
-                            const MT s2 = sig2 * inv, s6 = s2 * s2 * s2;
-                            const MT fac = fene ? -kf * inv : (r2 < rc2 ? e24 * (MT(2) * s6 * s6 - s6) * inv : MT(0));
-                            F[j][0] += fac * rx;
-                            F[j][1] += fac * ry;
-                            F[j][2] += fac * rz;
+                        bool bad = false;
+                        for (int k = 0; k < ntask[j]; k++)
+                            bad |= pair_force<MT>(X[j], Xc[tasks[k]], k < nfene[j], pc, F[j]);
+                        if (bad) {
+                            sErrP[sub & 1] = LB_ERR_FENE;
+                            flag = true;
                         }
                     }
                 }
@@ -547,6 +572,147 @@ __device__ __forceinline__ int md_substeps(const BeadParams& p, const ChainDev& 
     return 0;
 }
 
+// The same substeps for L = 4 or 8 lanes per bead (one bead per lane group),
+// with the update split by component: after the shuffle sum, lane a < 3
+// alone advances component a of velocity, displacement and momentum and
+// publishes that component of the position; every lane reads its bead's
+// position back from shared memory for the pair forces.  The arithmetic of
+// each component is that of md_substeps.  The Verlet lists are rebuilt when a
+// component of some bead's displacement since the last build exceeds
+// (skin / 2) / sqrt(3), which bounds the displacement by skin / 2.
+template <class MT, int L>
+__device__ __forceinline__ int md_substeps_split(const BeadParams& p, const ChainDev& ch, int N, int64_t n, int b,
+                                                 MT* sXbuf, MT (*sU)[3], MT (*sV)[3], double (*sR)[3], MT (*sP)[3],
+                                                 unsigned char (*sNb)[kMaxTasks], int* sErrP)
+{
+    static_assert(L == 4 || L == 8, "component split needs at least three lanes per bead");
+    using V4 = typename Vec4<MT>::T;
+    constexpr int lshift = L == 8 ? 3 : 2;
+    constexpr int cap = kMaxTasks / L;  // task slots of one lane
+    const int tid = threadIdx.x;
+    const int maxb = p.max_beads;
+    const int nmd = ((N << lshift) + 31) & ~31;  // MD threads: whole warps
+    const bool md = tid < nmd;
+    const int lane = tid & (L - 1);
+    const bool own = md && (tid >> lshift) < N;
+    const int bead = own ? tid >> lshift : 0;
+    const int ca = lane < 3 ? lane : 0;  // component this lane advances
+    const bool upd = own && lane < 3;
+    V4* sX4 = reinterpret_cast<V4*>(sXbuf);  // [2][maxb] positions, then [chunk][N] noise
+    const V4* sXi = sX4 + 2 * maxb;
+    const MT* mc;
+    if constexpr (sizeof(MT) == 8) mc = reinterpret_cast<const MT*>(ch.md_d);
+    else mc = reinterpret_cast<const MT*>(ch.md_f);
+    const MT dt = mc[kMdDt], dtm = mc[kMdDtm], namp = mc[kMdNamp], zeta = mc[kMdZeta];
+    const PairConsts<MT> pc{mc[kMdR02], mc[kMdInvR02], mc[kMdKf], mc[kMdSig2], mc[kMdRc2], mc[kMdE24]};
+    const bool wca = ch.eps > 0.0;
+    const MT rl2 = mc[kMdRl2], skin_c2 = mc[kMdSkinComp2];
+    // component ca of the bead (lanes >= 3 carry copies they never use)
+    const MT x0 = sXbuf[4 * bead + ca];
+    const MT u = own ? sU[bead][ca] : MT(0);
+    MT v = own ? sV[bead][ca] : MT(0);
+    MT d = MT(0), pm = MT(0), dref = MT(0);
+    // bond tasks: lane 0 the bond to bead - 1, lane 1 the bond to bead + 1
+    int bond = -1;
+    if (own && lane == 0 && bead > 0) bond = bead - 1;
+    if (own && lane == 1 && bead + 1 < N) bond = bead + 1;
+    const int nfene = bond >= 0 ? 1 : 0;
+    int ntask = nfene;
+    unsigned char* tasks = &sNb[bead][lane * cap];
+    MT fext[3];
+    for (int a = 0; a < 3; a++) fext[a] = lane == 0 ? (MT)ch.f_ext[a] : MT(0);
+    if (tid < 2) sErrP[tid] = 0;
+    __syncthreads();
+    auto sync_or = [&](bool v) -> bool {
+        if (nmd == 32) {
+            __syncwarp();
+            return __any_sync(0xffffffffu, v);
+        }
+        return bar_or(1, nmd, v);
+    };
+    bool rebuild = true;
+    const int chunk = namp > MT(0) ? p.noise_chunk : ch.n_md;
+    for (int c0 = 0; c0 < ch.n_md; c0 += chunk) {
+        const int nc = min(chunk, ch.n_md - c0);
+        if (namp > MT(0)) {
+            __syncthreads();  // the previous chunk's noise is consumed
+            md_noise<MT>(sX4 + 2 * maxb, n, c0, nc, N, b, ch.seed);
+            __syncthreads();
+        }
+        if (md) {
+            for (int sb = 0; sb < nc; sb++) {
+                const int sub = c0 + sb;
+                const V4* Xc = sX4 + (sub & 1) * maxb;
+                MT* Xn = sXbuf + 4 * ((sub + 1) & 1) * maxb;
+                bool flag = false;
+                const V4 xs = Xc[bead];
+                const MT X[3] = {xs.x, xs.y, xs.z};
+                if (rebuild && own) {  // lane r scans partners r, r + L, ... after its bond
+                    ntask = 0;
+                    if (bond >= 0) tasks[ntask++] = (unsigned char)bond;
+                    int found = 0;
+                    if (wca)
+                        for (int b2 = lane; b2 < N; b2 += L) {
+                            if (b2 == bead) continue;
+                            const V4 q = Xc[b2];
+                            const MT dx = X[0] - q.x, dy = X[1] - q.y, dz = X[2] - q.z;
+                            if (dx * dx + dy * dy + dz * dz < rl2) {
+                                if (ntask < cap) tasks[ntask++] = (unsigned char)b2;
+                                found++;
+                            }
+                        }
+                    if (nfene + found > cap) {  // more neighbours than the list holds
+                        sErrP[sub & 1] = LB_ERR_CHAIN;
+                        flag = true;
+                    }
+                    dref = d;
+                }
+                rebuild = false;
+                MT F[3] = {fext[0], fext[1], fext[2]};
+                if (own) {
+                    bool bad = false;
+                    for (int k = 0; k < ntask; k++) bad |= pair_force<MT>(X, Xc[tasks[k]], k < nfene, pc, F);
+                    if (bad) {
+                        sErrP[sub & 1] = LB_ERR_FENE;
+                        flag = true;
+                    }
+                }
+#pragma unroll
+                for (int o = 1; o < L; o <<= 1)  // xor < L stays within the bead's lanes
+                    for (int a = 0; a < 3; a++) F[a] += __shfl_xor_sync(0xffffffffu, F[a], o);
+                if (upd) {
+                    const MT Fa = ca == 0 ? F[0] : (ca == 1 ? F[1] : F[2]);
+                    const MT xin = namp > MT(0) ? reinterpret_cast<const MT*>(sXi + sb * N + bead)[ca] : MT(0);
+                    const MT ffric = -zeta * (v - u);
+                    const MT fnoise = namp * xin;
+                    v += dtm * (Fa + ffric + fnoise);
+                    d += dt * v;
+                    pm -= (ffric + fnoise) * dt;
+                    Xn[4 * bead + ca] = x0 + d;
+                    const MT dm = d - dref;
+                    if (wca && dm * dm > skin_c2) flag = true;
+                }
+                // publish Xn; any flag: rebuild the lists, or stop on an error
+                if (sync_or(flag)) {
+                    if (sErrP[sub & 1]) break;
+                    rebuild = true;
+                }
+            }
+        }
+        __syncthreads();
+        if (sErrP[0] || sErrP[1]) break;
+    }
+    const int err = sErrP[0] ? sErrP[0] : sErrP[1];
+    if (err) return err;
+    if (upd) {
+        sR[bead][ca] += (double)d;
+        sV[bead][ca] = v;
+        sP[bead][ca] = pm;
+    }
+    __syncthreads();
+    return 0;
+}
+
 template <int ST>
 __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
 {
@@ -570,8 +736,10 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     __shared__ MT sV[kMaxBeads][3];          // velocities
     __shared__ MT sP[kMaxBeads][3];          // momentum given to the fluid
     __shared__ unsigned char sNb[kMaxBeads][kMaxTasks];
+    __shared__ unsigned char sSt[kMaxBeads][kMaxStencilNb];  // beads whose stencil may share a site
+    __shared__ int sStN[kMaxBeads];
     __shared__ double sRc[3];
-    __shared__ double sRed[2][kBeadThreadsMax / 32][3];
+    __shared__ MT sRed[2][kBeadThreadsMax / 32][3];
     __shared__ int sErr;
     extern __shared__ __align__(32) unsigned char bead_dyn[];
     MT* sXbuf = reinterpret_cast<MT*>(bead_dyn);       // [2][max_beads] 4-vectors, then the noise
@@ -644,9 +812,15 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     // 3. MD substeps (md_substeps below)
     {
         __shared__ int sErrP[2];
-        const int err = p.beads_per_thread == 2
-                            ? md_substeps<MT, 2>(p, ch, N, n, b, sXbuf, sU, sV, sR, sP, sNb, sErrP)
-                            : md_substeps<MT, 1>(p, ch, N, n, b, sXbuf, sU, sV, sR, sP, sNb, sErrP);
+        int err;
+        if (p.beads_per_thread == 1 && p.lanes == 8)
+            err = md_substeps_split<MT, 8>(p, ch, N, n, b, sXbuf, sU, sV, sR, sP, sNb, sErrP);
+        else if (p.beads_per_thread == 1 && p.lanes == 4)
+            err = md_substeps_split<MT, 4>(p, ch, N, n, b, sXbuf, sU, sV, sR, sP, sNb, sErrP);
+        else if (p.beads_per_thread == 2)
+            err = md_substeps<MT, 2>(p, ch, N, n, b, sXbuf, sU, sV, sR, sP, sNb, sErrP);
+        else
+            err = md_substeps<MT, 1>(p, ch, N, n, b, sXbuf, sU, sV, sR, sP, sNb, sErrP);
         if (err) {
             if (tid == 0) set_status(&p.status[b], err);
             return;
@@ -654,20 +828,24 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     }
 
     // 4. centre of mass pinned at the box centre (one thread per bead; only
-    //    the warps holding beads reduce, FP64 being slow on this part)
-    double R[3] = {0, 0, 0}, V[3] = {0, 0, 0};
+    //    the warps holding beads reduce).  The sums run in MT over the offsets
+    //    from bead 0's start-of-step position, which are small: FP64 is slow
+    //    on this part, and the pin is re-applied every step, so the FP32
+    //    rounding of one step's shift does not accumulate.
+    double R[3] = {0, 0, 0};
+    MT V[3] = {0, 0, 0};
     if (tid < N)
         for (int a = 0; a < 3; a++) {
             R[a] = sR[tid][a];
-            V[a] = (double)sV[tid][a];
+            V[a] = sV[tid][a];
         }
     if (ch.pin_com >= 1) {
         const int warp = tid >> 5, lane = tid & 31, nbw = (N + 31) >> 5;
         if (warp < nbw)
             for (int pass = 0; pass < 2; pass++) {
-                double s[3];
+                MT s[3];
                 for (int a = 0; a < 3; a++) {
-                    s[a] = tid < N ? (pass == 0 ? R[a] : V[a]) : 0.0;
+                    s[a] = tid < N ? (pass == 0 ? (MT)(R[a] - sRc[a]) : V[a]) : MT(0);
                     for (int o = 16; o > 0; o >>= 1) s[a] += __shfl_xor_sync(0xffffffffu, s[a], o);
                 }
                 if (lane == 0)
@@ -675,29 +853,72 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
             }
         __syncthreads();
         if (tid < N) {
-            double com[3] = {0, 0, 0}, vcm[3] = {0, 0, 0};
+            MT com[3] = {0, 0, 0}, vcm[3] = {0, 0, 0};
             for (int w = 0; w < nbw; w++)
                 for (int a = 0; a < 3; a++) {
                     com[a] += sRed[0][w][a];
                     vcm[a] += sRed[1][w][a];
                 }
             const double centre = 0.5 * (Ei - 1);
+            const MT inv_n = sizeof(MT) == 8 ? (MT)ch.md_d[kMdInvN] : (MT)ch.md_f[kMdInvN];
             for (int a = 0; a < 3; a++) {
-                R[a] += centre - com[a] / N;
-                if (ch.pin_com >= 2) V[a] = (double)(MT)(V[a] - vcm[a] / N);
+                R[a] += (centre - sRc[a]) - (double)(com[a] * inv_n);
+                if (ch.pin_com >= 2) V[a] = V[a] - vcm[a] * inv_n;
             }
         }
     }
     if (tid < N)
         for (int a = 0; a < 3; a++) {
             pos[3 * tid + a] = R[a];
-            vel[3 * tid + a] = V[a];
+            vel[3 * tid + a] = (double)V[a];
         }
 
     // 5. force density at the stencil sites: every entry sums, in bead order,
     //    the contributions of all beads whose stencil holds its site; entries
     //    whose site an earlier bead already holds are marked duplicates.
+    //    Only beads whose stencil corner lies within one cell of this bead's on
+    //    every axis can share a site: each bead first lists those (in bead
+    //    order, itself included), then each entry scans its bead's list only.
     ForceEntry* fl = p.forces + ch.force_off;
+    //    Eight threads per bead scan consecutive eighths of the chain and
+    //    merge their finds in order by a prefix sum over the eight.
+    {
+        const int part = (N + 7) >> 3;  // <= 32 beads per thread
+        for (int base = 0; base < 8 * N; base += nthr) {
+            const int e = base + tid;
+            const bool act = e < 8 * N;
+            const int bb = act ? e >> 3 : 0, r = e & 7;
+            const int lo = r * part, hi = min(N, lo + part);
+            uint32_t m = 0;
+            if (act)
+                for (int b2 = lo; b2 < hi; b2++) {
+                    bool near = true;
+                    for (int a = 0; a < 3; a++) {
+                        int d = sBase[b2][a] - sBase[bb][a];
+                        if ((per >> a) & 1) {
+                            d = wrapi(d, Ei);
+                            if (d > Ei / 2) d -= Ei;
+                        }
+                        near = near && d >= -1 && d <= 1;
+                    }
+                    if (near) m |= 1u << (b2 - lo);
+                }
+            const int cnt = __popc(m);
+            int incl = cnt;
+            for (int o = 1; o < 8; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o, 8);
+                if (r >= o) incl += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 7, 8);
+            if (act) {
+                int k = incl - cnt;
+                for (uint32_t mm = m; mm; mm &= mm - 1, k++)
+                    if (k < kMaxStencilNb) sSt[bb][k] = (unsigned char)(lo + __ffs(mm) - 1);
+                if (r == 7) sStN[bb] = total <= kMaxStencilNb ? total : -1;  // -1: too many, scan every bead
+            }
+        }
+    }
+    __syncthreads();
     for (int e = tid; e < 8 * N; e += nthr) {
         const int bb = e >> 3, c = e & 7;
         int s[3] = {sBase[bb][0] + (c & 1), sBase[bb][1] + ((c >> 1) & 1), sBase[bb][2] + ((c >> 2) & 1)};
@@ -705,7 +926,10 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
             if ((per >> a) & 1) s[a] = wrapi(s[a], Ei);
         MT g[3] = {0, 0, 0};
         bool dup = false;
-        for (int b2 = 0; b2 < N; b2++) {
+        const int nlist = sStN[bb];
+        const int nscan = nlist >= 0 ? nlist : N;
+        for (int k = 0; k < nscan; k++) {
+            const int b2 = nlist >= 0 ? (int)sSt[bb][k] : k;
             int o[3];
             bool in = true;
             for (int a = 0; a < 3; a++) {
