@@ -719,15 +719,38 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     using S = Stor<ST>;
     using A = typename S::A;
     using MT = typename std::conditional<ST == kF64, double, float>::type;
-    const ChainDev& ch = p.chains[blockIdx.x];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    // The chain and box records, the status and the step number are read once
+    // into shared memory: later phases would otherwise reload them from L2
+    // (the gather evicts L1) while the stream-collide launch keeps the memory
+    // system busy, and one reading of the status serves the whole block
+    // (another launch may set it meanwhile).
+    __shared__ ChainDev sCh;
+    __shared__ BoxDev sBd;
+    __shared__ int sGo;
+    __shared__ int64_t sStep;
+    {
+        const int b0 = p.chains[blockIdx.x].box;
+        static_assert(sizeof(ChainDev) % 8 == 0 && sizeof(BoxDev) % 8 == 0, "records copied in 8-byte words");
+        constexpr int wc = (int)(sizeof(ChainDev) / 8), wb = (int)(sizeof(BoxDev) / 8);
+        for (int w = tid; w < wc + wb; w += nthr) {
+            if (w < wc)
+                reinterpret_cast<uint64_t*>(&sCh)[w] = reinterpret_cast<const uint64_t*>(p.chains + blockIdx.x)[w];
+            else
+                reinterpret_cast<uint64_t*>(&sBd)[w - wc] = reinterpret_cast<const uint64_t*>(p.boxes + b0)[w - wc];
+        }
+        if (tid == nthr - 1) sGo = p.status[b0] == 0;
+        if (tid == nthr - 2) sStep = *p.step;
+    }
+    __syncthreads();
+    const ChainDev& ch = sCh;
+    const BoxDev& bd = sBd;
     const int N = ch.nbeads;
     const int b = ch.box;
-    if (N <= 0 || p.status[b] != 0) return;
-    const BoxDev& bd = p.boxes[b];
+    if (N <= 0 || !sGo) return;
     const int Ei = bd.E, per = bd.per_mask;
     const int64_t n3 = bd.n3;
-    const int64_t n = *p.step;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int64_t n = sStep;
 
     __shared__ double sR[kMaxBeads][3];      // start-of-step, then end-of-step positions
     __shared__ MT sD[kMaxBeads][3];          // start-of-step offsets inside the stencil cell
@@ -739,6 +762,7 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     __shared__ unsigned char sSt[kMaxBeads][kMaxStencilNb];  // beads whose stencil may share a site
     __shared__ int sStN[kMaxBeads];
     __shared__ double sRc[3];
+    __shared__ A sAcc[3];  // body acceleration in the collision type
     __shared__ MT sRed[2][kBeadThreadsMax / 32][3];
     __shared__ int sErr;
     extern __shared__ __align__(32) unsigned char bead_dyn[];
@@ -748,7 +772,10 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     double* vel = p.vel + 3 * ch.bead_off;
     if (tid == 0) {
         sErr = 0;
-        for (int a = 0; a < 3; a++) sRc[a] = pos[a];
+        for (int a = 0; a < 3; a++) {
+            sRc[a] = pos[a];
+            sAcc[a] = (A)bd.accel[a];
+        }
     }
     __syncthreads();
 
@@ -797,7 +824,7 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
             moments<A>(f, dr, j);
             const A rho = A(1) + dr;
             const MT w8 = weight(bb, c);
-            for (int a = 0; a < 3; a++) uc[a] = w8 * (MT)((j[a] + A(0.5) * rho * (A)bd.accel[a]) / rho);
+            for (int a = 0; a < 3; a++) uc[a] = w8 * (MT)((j[a] + A(0.5) * rho * sAcc[a]) / rho);
         }
         for (int a = 0; a < 3; a++) {
             uc[a] += __shfl_xor_sync(0xffffffffu, uc[a], 1);
@@ -964,40 +991,41 @@ __global__ void __launch_bounds__(kForcedThreads) k_forced(ForcedParams p)
     const int chain = (int)blockIdx.x / p.splits, part = (int)blockIdx.x - chain * p.splits;
     if (chain < p.nchains) {
         const ChainDev& ch = p.chains[chain];
-        const int b = ch.box;
-        if (ch.nbeads > 0 && p.status[b] == 0) {
+        const int b = ch.box, nb = ch.nbeads;
+        const ForceEntry* fl = p.forces + ch.force_off;
+        // the entry, the status and the box record are independent loads:
+        // issue them together (e stays inside the chain's entries)
+        for (int e = part * blockDim.x + threadIdx.x; e < 8 * nb; e += p.splits * blockDim.x) {
+            const ForceEntry fe = fl[e];
+            const int st = p.status[b];
             const BoxDev& bd = p.boxes[b];
             const int Ei = bd.E, per = bd.per_mask;
             const int64_t n3 = bd.n3;
             const typename S::E* Ab = reinterpret_cast<const typename S::E*>(p.A) + bd.f_off;
             typename S::E* Bb = reinterpret_cast<typename S::E*>(p.B) + bd.f_off;
-            const ForceEntry* fl = p.forces + ch.force_off;
-            for (int e = part * blockDim.x + threadIdx.x; e < 8 * ch.nbeads; e += p.splits * blockDim.x) {
-                const ForceEntry fe = fl[e];
-                if (fe.site < 0) continue;
-                const int x = fe.site % Ei, y = (fe.site / Ei) % Ei, z = fe.site / (Ei * Ei);
-                A f[kQ], dr, j[3];
-                pull_site<ST>(Ab, n3, Ei, per, x, y, z, f);
-                moments<A>(f, dr, j);
-                const A rho = A(1) + dr;
-                A F[3], u[3];
-                for (int a = 0; a < 3; a++) {
-                    F[a] = rho * (A)bd.accel[a] + (A)fe.g[a];
-                    u[a] = (j[a] + A(0.5) * F[a]) / rho;
-                }
-                const A om = A(1) / (A)bd.tau;
-                const A usq = A(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-                const A uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+            if (fe.site < 0 || st != 0) continue;
+            const int x = fe.site % Ei, y = (fe.site / Ei) % Ei, z = fe.site / (Ei * Ei);
+            A f[kQ], dr, j[3];
+            pull_site<ST>(Ab, n3, Ei, per, x, y, z, f);
+            moments<A>(f, dr, j);
+            const A rho = A(1) + dr;
+            A F[3], u[3];
+            for (int a = 0; a < 3; a++) {
+                F[a] = rho * (A)bd.accel[a] + (A)fe.g[a];
+                u[a] = (j[a] + A(0.5) * F[a]) / rho;
+            }
+            const A om = A(1) / (A)bd.tau;
+            const A usq = A(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            const A uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
 #pragma unroll
-                for (int i = 0; i < kQ; i++) {
-                    const A w = wgt<A>(i);
-                    const A cu = cvec(i, 0) * u[0] + cvec(i, 1) * u[1] + cvec(i, 2) * u[2];
-                    const A cF = cvec(i, 0) * F[0] + cvec(i, 1) * F[1] + cvec(i, 2) * F[2];
-                    const A deq = w * (dr + rho * (A(3) * cu + A(4.5) * cu * cu - usq));
-                    A val = f[i] + om * (deq - f[i]);
-                    val += (A(1) - A(0.5) * om) * w * (A(3) * (cF - uF) + A(9) * cu * cF);
-                    Bb[(int64_t)i * n3 + fe.site] = S::out(val);
-                }
+            for (int i = 0; i < kQ; i++) {
+                const A w = wgt<A>(i);
+                const A cu = cvec(i, 0) * u[0] + cvec(i, 1) * u[1] + cvec(i, 2) * u[2];
+                const A cF = cvec(i, 0) * F[0] + cvec(i, 1) * F[1] + cvec(i, 2) * F[2];
+                const A deq = w * (dr + rho * (A(3) * cu + A(4.5) * cu * cu - usq));
+                A val = f[i] + om * (deq - f[i]);
+                val += (A(1) - A(0.5) * om) * w * (A(3) * (cF - uF) + A(9) * cu * cF);
+                Bb[(int64_t)i * n3 + fe.site] = S::out(val);
             }
         }
     }

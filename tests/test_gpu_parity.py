@@ -224,6 +224,28 @@ def test_fullsize_128_sampled_step(lbt):
         assert np.abs(pos1 - pref).max() < 1e-5 and np.abs(vel1 - vref).max() < 3e-4
 
 
+def test_chain_recoupled_at_an_odd_step(lbt):
+    # The sites that carry a bead force are collided by the bead kernel and
+    # left out of the stream-collide launch; they are marked per step parity.
+    # A chain re-coupled at step 3 (odd) at new positions must have its sites
+    # marked for that step: one step is compared site by site with the oracle.
+    c = Case(16, 0.8, 6, seed=3, M=16, nbeads=6)
+    r = GpuRunner(lbt, torch, [c], ST64)
+    r.step(3)
+    _, w = oracle.lattice()
+    A = r.tr.deviations(0).astype(np.float64) + w[:, None, None, None]
+    pos_new = np.ascontiguousarray(c.pos0 + np.array([1.3, 0.4, -0.7]))
+    r.tr.chain_couple(0, c.gpu_chain(lbt), pos_new, None)
+    r.step(1)
+    B = r.tr.deviations(0).astype(np.float64)
+    pos1, vel1 = r.tr.chain(0, 6)
+    st, Bref, pref, vref, _ = oracle.step_from(c.oracle_box(), A, c.samples, 3, c.oracle_chain(), pos_new,
+                                              np.zeros_like(pos_new))
+    assert st == 0
+    assert np.abs(B - (Bref - w[:, None, None, None])).max() < 1e-13
+    assert np.abs(pos1 - pref).max() < 1e-11 and np.abs(vel1 - vref).max() < 1e-10
+
+
 def test_error_flags_freeze_only_the_failing_box(lbt):
     good = Case(16, 0.8, 5, seed=1, M=16, nbeads=6)
     bad = Case(16, 0.8, 5, seed=2, M=16, nbeads=6)
