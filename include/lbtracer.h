@@ -235,6 +235,22 @@ int32_t lb_read_fields(lb_ctx* ctx, int32_t box, int32_t what, void* dst);
  */
 int32_t lb_conservation(lb_ctx* ctx, int32_t box, double* out);
 
+/*
+ * lb_vorticity -- mean magnitude of the vorticity over a cube of one box
+ * (Sec. 4, Figs. 1 and 2: |omega| averaged over the whole sub-volume around
+ * the tracer and over a small region at its centre, LB against DNS).
+ *   u is the velocity lb_read_fields(LB_FIELD_U) reports; omega = curl u by
+ *   second-order central differences, omega_x = (u_z(y+1) - u_z(y-1))/2 -
+ *   (u_y(z+1) - u_y(z-1))/2 and cyclically, |omega| in FP64.
+ *   lo, hi: the cube holds the sites with lo <= x, y, z <= hi; it must lie
+ *   inside 1 .. E-2 (LB_ERR_ARG otherwise).
+ *   out: host, one double: the mean of |omega| over the (hi - lo + 1)^3 sites.
+ *   Uses the context's free population buffer as scratch (no allocation);
+ *   the sum runs in a fixed order (the same inputs give the same result).
+ *   Synchronising (bounded wait); returns a pending box error.
+ */
+int32_t lb_vorticity(lb_ctx* ctx, int32_t box, int32_t lo, int32_t hi, double* out);
+
 /* lb_sync -- wait for the context stream at most timeout_ms (LB_ERR_TIMEOUT
  * after that, the context stays usable) and return the first box error. */
 int32_t lb_sync(lb_ctx* ctx, int32_t timeout_ms);

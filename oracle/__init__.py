@@ -401,3 +401,27 @@ def volume_field(modes, E, t=0.0, zoom=1):
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def vorticity_mean(u, lo, hi):
+    """Mean magnitude of the vorticity over the cube lo <= x, y, z <= hi of a
+    velocity field u [3][E][E][E] (layout [c][z][y][x]), omega = curl u by
+    second-order central differences (Sec. 4, Figs. 1 and 2: |omega| averaged
+    over the sub-volume around the tracer and over a region at its centre).
+    The cube must lie inside sites 1 .. E-2.  FP64, numpy."""
+    u = np.asarray(u, dtype=np.float64)
+    E = u.shape[1]
+    assert 1 <= lo <= hi <= E - 2
+    c = slice(lo, hi + 1)
+    p, m = slice(lo + 1, hi + 2), slice(lo - 1, hi)
+
+    def d(comp, axis):  # central difference of u[comp] along axis (0 = z, 1 = y, 2 = x) on the cube
+        a = [c, c, c]
+        b = [c, c, c]
+        a[axis], b[axis] = p, m
+        return 0.5 * (u[comp][tuple(a)] - u[comp][tuple(b)])
+
+    wx = d(2, 1) - d(1, 0)  # d u_z / dy - d u_y / dz
+    wy = d(0, 0) - d(2, 2)  # d u_x / dz - d u_z / dx
+    wz = d(1, 2) - d(0, 1)  # d u_y / dx - d u_x / dy
+    return float(np.sqrt(wx * wx + wy * wy + wz * wz).mean())

@@ -840,6 +840,29 @@ int32_t lb_conservation(lb_ctx* ctx, int32_t box, double* out)
     return first_status(ctx, box);
 }
 
+int32_t lb_vorticity(lb_ctx* ctx, int32_t box, int32_t lo, int32_t hi, double* out)
+{
+    if (!ctx || !out) return LB_ERR_ARG;
+    if (box < 0 || box >= ctx->nboxes) return ctx->fail(LB_ERR_ARG, "box index out of range");
+    const BoxDev& bd = ctx->boxes[box];
+    if (lo < 1 || hi > bd.E - 2 || lo > hi) return ctx->fail(LB_ERR_ARG, "the cube must lie inside sites 1 .. E-2");
+    const size_t eb = elem_bytes(ctx->storage), rb = real_bytes(ctx->storage);
+    const void* A = reinterpret_cast<const char*>(ctx->curA()) + bd.f_off * eb;
+    // scratch in the box's region of the free buffer (19 E^3 elements): the
+    // velocity field, then 512 block sums and the result
+    char* stage = reinterpret_cast<char*>(ctx->curB()) + bd.f_off * eb;
+    const size_t ubytes = (3 * (size_t)bd.n3 * rb + 255) / 256 * 256;
+    double* sums = reinterpret_cast<double*>(stage + ubytes);
+    CK(DISPATCH(ctx->storage, fields(A, ctx->boxes.data(), box, bd.n3, 1, stage, ctx->stream)));
+    CK(launch_vorticity(stage, ctx->storage == kF64, bd.E, lo, hi, sums, sums + 512, ctx->stream));
+    double r = 0.0;
+    CK(cudaMemcpyAsync(&r, sums + 512, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    int st = wait_stream(ctx, kDefaultTimeoutMs);
+    if (st) return st;
+    *out = r;
+    return first_status(ctx, box);
+}
+
 int32_t lb_sync(lb_ctx* ctx, int32_t timeout_ms)
 {
     if (!ctx) return LB_ERR_ARG;

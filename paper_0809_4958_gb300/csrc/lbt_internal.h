@@ -151,6 +151,12 @@ struct ForcedParams {
     int32_t splits;               // blocks per chain (set by the launcher)
 };
 
+// Mean |curl u| over the cube [lo, hi]^3 of a velocity field u [3][E^3]
+// (double when u_f64, else float); scratch holds 513 doubles, out one double
+// (both device memory).
+cudaError_t launch_vorticity(const void* u, int u_f64, int E, int lo, int hi, double* scratch, double* out,
+                             cudaStream_t s);
+
 // Host-side launchers, one instantiation per storage type.
 template <int ST>
 struct Launch {

@@ -174,6 +174,69 @@ cudaError_t launch_synth_volume(const double* kvec, const double* amp, const dou
 }
 
 // ---------------------------------------------------------------------------
+// Vorticity diagnostic: |curl u| by central differences over the cube
+// [lo, hi]^3 of a box's velocity field u [3][E^3] (real type R), FP64 sums.
+// Each block writes the sum of its sites (grid-stride order, then a fixed
+// tree); one thread adds the block sums in order and divides by the count.
+constexpr int kVortThreads = 256;
+constexpr int kVortMaxBlocks = 512;
+
+template <class R>
+__global__ void __launch_bounds__(kVortThreads) k_vort_partial(const R* u, int E, int lo, int hi, double* partial)
+{
+    const int m = hi - lo + 1;
+    const int64_t cube = (int64_t)m * m * m, n3 = (int64_t)E * E * E;
+    const int64_t sy = E, sz = (int64_t)E * E;
+    const R* ux = u;
+    const R* uy = u + n3;
+    const R* uz = u + 2 * n3;
+    double acc = 0.0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < cube; s += (int64_t)gridDim.x * blockDim.x) {
+        const int x = lo + (int)(s % m), y = lo + (int)((s / m) % m), z = lo + (int)(s / ((int64_t)m * m));
+        const int64_t c = (int64_t)z * sz + (int64_t)y * sy + x;
+        const double wx = 0.5 * ((double)uz[c + sy] - (double)uz[c - sy]) - 0.5 * ((double)uy[c + sz] - (double)uy[c - sz]);
+        const double wy = 0.5 * ((double)ux[c + sz] - (double)ux[c - sz]) - 0.5 * ((double)uz[c + 1] - (double)uz[c - 1]);
+        const double wz = 0.5 * ((double)uy[c + 1] - (double)uy[c - 1]) - 0.5 * ((double)ux[c + sy] - (double)ux[c - sy]);
+        acc += sqrt(wx * wx + wy * wy + wz * wz);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ double ws[kVortThreads / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += ws[w];
+        partial[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_vort_final(const double* partial, int nblocks, double count, double* out)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double t = 0.0;
+    for (int b = 0; b < nblocks; b++) t += partial[b];
+    out[0] = t / count;
+}
+
+cudaError_t launch_vorticity(const void* u, int u_f64, int E, int lo, int hi, double* scratch, double* out,
+                             cudaStream_t s)
+{
+    const int64_t m = hi - lo + 1, cube = m * m * m;
+    int64_t g = (cube + kVortThreads - 1) / kVortThreads;
+    if (g > kVortMaxBlocks) g = kVortMaxBlocks;
+    if (u_f64)
+        k_vort_partial<double><<<(unsigned)g, kVortThreads, 0, s>>>(reinterpret_cast<const double*>(u), E, lo, hi,
+                                                                    scratch);
+    else
+        k_vort_partial<float><<<(unsigned)g, kVortThreads, 0, s>>>(reinterpret_cast<const float*>(u), E, lo, hi,
+                                                                   scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_vort_final<<<1, 32, 0, s>>>(scratch, (int)g, (double)cube, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 __global__ void k_cons_final(const BoxDev* boxes, const ChainDev* chains, int nboxes, int64_t chunks,
                              const double* partial, const double* vel, double* out, int32_t* status)
 {

@@ -28,7 +28,7 @@ ERROR_NAMES = {0: "LB_OK", 1: "LB_ERR_ARG", 2: "LB_ERR_CUDA", 3: "LB_ERR_FENE", 
                5: "LB_ERR_NONFINITE", 6: "LB_ERR_TIMEOUT", 7: "LB_ERR_STATE", 8: "LB_ERR_SIZE", 9: "LB_ERR_CHAIN"}
 
 EXPORTS = ["lb_plan", "lb_create", "lb_destroy", "lb_init", "lb_set_boundary", "chain_couple", "lb_step",
-           "lb_graph_capture", "lb_graph_launch", "lb_read_fields", "lb_conservation", "lb_sync", "lb_status",
+           "lb_graph_capture", "lb_graph_launch", "lb_read_fields", "lb_conservation", "lb_vorticity", "lb_sync", "lb_status",
            "lb_current_step", "lb_set_launch", "lb_set_bead_launch", "lb_profile", "lb_profile_read", "lb_last_error", "lb_synth_workspace_bytes", "lb_synth_faces",
            "lb_synth_volume", "lb_population_sums_noalloc", "lb_mlp_param_bytes", "lb_mlp_bind", "lb_mlp_train_bytes",
            "lb_mlp_train_init", "lb_mlp_features", "lb_mlp_targets", "lb_mlp_forward", "lb_mlp_grad",
@@ -84,6 +84,7 @@ def load(path: str | None = None, build_if_missing: bool = True):
         "lb_graph_launch": (_i32, [_vp]),
         "lb_read_fields": (_i32, [_vp, _i32, _i32, _vp]),
         "lb_conservation": (_i32, [_vp, _i32, _vp]),
+        "lb_vorticity": (_i32, [_vp, _i32, _i32, _i32, _vp]),
         "lb_sync": (_i32, [_vp, _i32]),
         "lb_status": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
         "lb_current_step": (_i64, [_vp]),
@@ -225,6 +226,12 @@ class Tracers:
         out = np.zeros(7)
         _check(self.lib.lb_conservation(self.ctx, box, out.ctypes.data), self.ctx)
         return out
+
+    def lb_vorticity(self, box, lo, hi):
+        """Mean |curl u| over the sites lo <= x, y, z <= hi of a box."""
+        out = np.zeros(1)
+        _check(self.lib.lb_vorticity(self.ctx, box, int(lo), int(hi), out.ctypes.data), self.ctx)
+        return float(out[0])
 
     def lb_sync(self, timeout_ms=120000):
         _check(self.lib.lb_sync(self.ctx, int(timeout_ms)), self.ctx)
