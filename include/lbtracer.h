@@ -356,7 +356,8 @@ int32_t lb_synth_volume(const double* kvec, const double* amp, const double* ome
  *   At every interval start lb_step first builds the features of those boxes
  *   from the ring and runs the network.
  * lb_mlp_features: feature matrix bf16 [6 E^2][32] of one face set from four
- *   samples [6][3][E][E] (real_dtype LB_STORE_F64 or LB_STORE_F32, device).
+ *   samples [6][3][E][E] (real_dtype LB_STORE_F64 or LB_STORE_F32, device);
+ *   X must be 16-byte aligned (LB_ERR_ARG otherwise).
  * lb_mlp_targets: training targets f32 [6 E^2][3K]: (fine - Hermite) * 64 / u_max
  *   with fine [K + 1][6][3][E][E] the boundary at t = jK .. jK + K;
  *   first_interval = 1 uses the one-sided tangent of interval 0.

@@ -301,8 +301,13 @@ int enqueue_step(lb_ctx* ctx, int64_t n)
                               ctx->at<int64_t>(ctx->L.step), ctx->stream));
         CK(mlp_features(sets, ctx->L.mlp_boxes, ctx->L.mlp_rows, ctx->mlp_umax, ctx->storage == kF64,
                         ctx->arena + ctx->L.mlp_x, ctx->stream));
-        CK(mlp_forward(ctx->arena + ctx->L.mlp_x, ctx->L.mlp_rows, ctx->mlp_params, ctx->L.mlp_K,
-                       ctx->at<float>(ctx->L.mlp_y), nullptr, nullptr, ctx->stream));
+        // residuals column-major (see SCParams::mlp_ystride); a timed-out MMA
+        // flags the first upsampler box
+        int first = 0;
+        while (first < ctx->nboxes && ctx->boxes[first].mlp_row < 0) first++;
+        CK(mlp_forward_tc(ctx->arena + ctx->L.mlp_x, ctx->L.mlp_rows, ctx->mlp_params, ctx->L.mlp_K,
+                          ctx->at<float>(ctx->L.mlp_y), ctx->at<int32_t>(ctx->L.status) + first, ctx->stream,
+                          ctx->L.mlp_rows));
     }
     if (nch > 0) {
         CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
@@ -326,7 +331,7 @@ int enqueue_step(lb_ctx* ctx, int64_t n)
     sp.ring_slot_elems = (int64_t)ctx->L.ring_slot_elems;
     sp.ring_slots = ctx->L.ring_slots;
     sp.mlp_y = ctx->at<float>(ctx->L.mlp_y);
-    sp.mlp_nout = 3 * ctx->L.mlp_K;
+    sp.mlp_ystride = ctx->L.mlp_rows;
     sp.mlp_yunit = (float)(ctx->mlp_umax / kMlpOutDiv);
     sp.boxes = ctx->at<BoxDev>(ctx->L.boxes);
     sp.tile_prefix = ctx->at<int64_t>(ctx->L.tile_prefix);
@@ -1066,6 +1071,10 @@ int32_t lb_mlp_features(const void* s_prev, const void* s0, const void* s1, cons
     if (!s_prev || !s0 || !s1 || !s2 || !X || E < 2 || !(u_max > 0) ||
         (real_dtype != LB_STORE_F64 && real_dtype != LB_STORE_F32)) {
         g_last_error = "lb_mlp_features: bad argument";
+        return LB_ERR_ARG;
+    }
+    if (reinterpret_cast<uintptr_t>(X) % 16 != 0) {  // rows are written as 16-byte vectors
+        g_last_error = "lb_mlp_features: X must be 16-byte aligned";
         return LB_ERR_ARG;
     }
     MlpFeatureSet fs{};

@@ -212,14 +212,20 @@ __device__ __forceinline__ TimeWeights<R> time_weights(int64_t n, int K, int mod
 __device__ __forceinline__ int mlp_substep(int64_t n, int K) { return (int)(n + 1 - (n / K) * K); }
 
 // Learned residual of the boundary velocity (upsampler boxes): output row of
-// the face site, substep s.
-template <class R>
-__device__ __forceinline__ void add_mlp_residual(const SCParams& p, const BoxDev& bd, int s, int f, int pp, int qq,
-                                                 R ub[3])
+// the face site, substep s.  Loaded before the time interpolation of the ring
+// samples (the two loads overlap), added after it.
+__device__ __forceinline__ void load_mlp_residual(const SCParams& p, const BoxDev& bd, int s, int f, int pp, int qq,
+                                                  float r[3])
 {
     if (bd.mlp_row < 0) return;
-    const float* y = p.mlp_y + (bd.mlp_row + ((int64_t)f * bd.E + qq) * bd.E + pp) * p.mlp_nout + 3 * (s - 1);
-    for (int c = 0; c < 3; c++) ub[c] += (R)(p.mlp_yunit * y[c]);
+    const float* y = p.mlp_y + (int64_t)(3 * (s - 1)) * p.mlp_ystride + bd.mlp_row + ((int64_t)f * bd.E + qq) * bd.E + pp;
+    for (int c = 0; c < 3; c++) r[c] = y[c * p.mlp_ystride];
+}
+template <class R>
+__device__ __forceinline__ void add_mlp_residual(const SCParams& p, const BoxDev& bd, const float r[3], R ub[3])
+{
+    if (bd.mlp_row < 0) return;
+    for (int c = 0; c < 3; c++) ub[c] += (R)(p.mlp_yunit * r[c]);
 }
 
 // Owning face of a boundary site (first velocity face containing it in the

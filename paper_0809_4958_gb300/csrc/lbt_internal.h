@@ -110,8 +110,8 @@ struct SCParams {
     const void* ring;             // real elements
     int64_t ring_slot_elems;
     int32_t ring_slots;
-    const float* mlp_y;           // upsampler output [rows][mlp_nout] of the current interval
-    int32_t mlp_nout;
+    const float* mlp_y;           // upsampler output of the current interval, column-major:
+    int64_t mlp_ystride;          //   output c of face row r at mlp_y[c * mlp_ystride + r]
     float mlp_yunit;              // velocity of one output unit (u_max / 64)
     const BoxDev* boxes;
     const int64_t* tile_prefix;   // [nboxes + 1] first tile of each box for the current block size

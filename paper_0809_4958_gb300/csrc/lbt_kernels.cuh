@@ -142,9 +142,11 @@ __device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, int
                 int pp, qq;
                 const int x = xg * VW + k;
                 const int f = owning_face(x, y, z, Ei, per, pp, qq);
+                float res[3];
+                load_mlp_residual(p, bd, s_mlp, f, pp, qq, res);
                 R ub[3];
                 boundary_velocity<R>(ring, p.ring_slot_elems, bd, f, pp, qq, tw, ub);
-                add_mlp_residual<R>(p, bd, s_mlp, f, pp, qq, ub);
+                add_mlp_residual<R>(p, bd, res, ub);
                 drho[k] = (A)bd.rho_b - A(1);
                 ux[k] = (A)ub[0];
                 uy[k] = (A)ub[1];

@@ -224,7 +224,18 @@ __device__ void features_row(const R* const smp[4], int E, float inv_umax, int64
         for (int c = 0; c < 3; c++) v[k++] = (face_val(smp[a], E, f, c, qp, p) - face_val(smp[a], E, f, c, qm, p)) * sq * inv_umax;
     }
     for (; k < kMlpIn; k++) v[k] = 0.f;
-    for (int i = 0; i < kMlpIn; i++) out[i] = __float2bfloat16_rn(v[i]);
+    // the row's 64 bytes as four 16-byte stores (rows are 64-byte aligned)
+    uint4* o = reinterpret_cast<uint4*>(out);
+#pragma unroll
+    for (int q4 = 0; q4 < kMlpIn / 8; q4++) {
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * q4 + 2 * h], v[8 * q4 + 2 * h + 1]);
+            w[h] = *reinterpret_cast<const uint32_t*>(&b2);
+        }
+        o[q4] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
 }
 
 // One launch for several face sets: set b has rows [row_off[b], row_off[b] +

@@ -44,9 +44,12 @@ MlpTrain mlp_train_layout(int K, int64_t batch_rows);
 cudaError_t mlp_forward(const void* X, int64_t rows, const void* params, int K, float* Y, float* H1, float* H2,
                         cudaStream_t s);
 // Inference forward on the tcgen05 tensor cores (lbt_mlp_tc.cu); err (device,
-// may be null) receives LB_ERR_TIMEOUT if an MMA does not complete.
+// may be null) receives LB_ERR_TIMEOUT if an MMA does not complete.  Y is
+// row-major [rows][3K] when col_stride is 0, else column-major: output c of
+// row r at Y[c * col_stride + r] (the step's layout: a boundary site's
+// residual at one substep is then read from consecutive rows).
 cudaError_t mlp_forward_tc(const void* X, int64_t rows, const void* params, int K, float* Y, int32_t* err,
-                           cudaStream_t s);
+                           cudaStream_t s, int64_t col_stride = 0);
 cudaError_t mlp_features(const MlpFeatureSet* sets_dev, int nsets, int64_t total_rows, double u_max, int real_f64,
                          void* X, cudaStream_t s);
 // Features of one face set passed by value (6 E^2 rows from row 0).

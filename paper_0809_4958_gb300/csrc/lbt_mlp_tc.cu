@@ -145,7 +145,7 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float* 
 template <int NOUT>
 __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(const __nv_bfloat16* __restrict__ X, int64_t rows,
                                                                const unsigned char* __restrict__ params, MlpLayout L,
-                                                               float* __restrict__ Y, int32_t* err)
+                                                               float* __restrict__ Y, int64_t col_stride, int32_t* err)
 {
     using Sm = TcSmem<NOUT>;
     constexpr int NP = Sm::kNP;
@@ -244,18 +244,24 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(const __nv_bfloat
                 // every lane takes part in the (warp-collective) TMEM loads;
                 // rows past the end store nothing
                 const bool in = r0 + m < rows;
-                float* y = Y + (r0 + m) * NOUT;
 #pragma unroll
                 for (int c0 = 0; c0 < NP; c0 += 16) {
                     float v[16];
                     tc_ld16(tmem_row + 128 + c0, v);
+                    if (col_stride == 0) {  // row-major [rows][NOUT]: four 16-byte stores per lane
+                        float* y = Y + (r0 + m) * NOUT;
 #pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        if (in && c0 + j < NOUT) {
-                            const float4 bb = *reinterpret_cast<const float4*>(sm.b3 + c0 + j);
-                            *reinterpret_cast<float4*>(y + c0 + j) =
-                                make_float4(v[j] + bb.x, v[j + 1] + bb.y, v[j + 2] + bb.z, v[j + 3] + bb.w);
-                        }
+                        for (int j = 0; j < 16; j += 4)
+                            if (in && c0 + j < NOUT) {
+                                const float4 bb = *reinterpret_cast<const float4*>(sm.b3 + c0 + j);
+                                *reinterpret_cast<float4*>(y + c0 + j) =
+                                    make_float4(v[j] + bb.x, v[j + 1] + bb.y, v[j + 2] + bb.z, v[j + 3] + bb.w);
+                            }
+                    } else {  // column-major Y[col * col_stride + row]: the warp's 32 rows in one line per column
+#pragma unroll
+                        for (int j = 0; j < 16; j++)
+                            if (in && c0 + j < NOUT) Y[(int64_t)(c0 + j) * col_stride + r0 + m] = v[j] + sm.b3[c0 + j];
+                    }
                 }
             }
         }
@@ -272,8 +278,8 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(const __nv_bfloat
 }
 
 template <int NOUT>
-cudaError_t forward_tc(const void* X, int64_t rows, const void* params, const MlpLayout& L, float* Y, int32_t* err,
-                       cudaStream_t s)
+cudaError_t forward_tc(const void* X, int64_t rows, const void* params, const MlpLayout& L, float* Y,
+                       int64_t col_stride, int32_t* err, cudaStream_t s)
 {
     static bool attr = false;
     const int smem = (int)sizeof(TcSmem<NOUT>);
@@ -290,18 +296,19 @@ cudaError_t forward_tc(const void* X, int64_t rows, const void* params, const Ml
     if (blocks > tiles) blocks = tiles;
     if (blocks < 1) return cudaSuccess;
     k_mlp_forward_tc<NOUT><<<(unsigned)blocks, kTcThreads, smem, s>>>(
-        reinterpret_cast<const __nv_bfloat16*>(X), rows, reinterpret_cast<const unsigned char*>(params), L, Y, err);
+        reinterpret_cast<const __nv_bfloat16*>(X), rows, reinterpret_cast<const unsigned char*>(params), L, Y, col_stride,
+        err);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t mlp_forward_tc(const void* X, int64_t rows, const void* params, int K, float* Y, int32_t* err,
-                           cudaStream_t s)
+                           cudaStream_t s, int64_t col_stride)
 {
     const MlpLayout L = mlp_layout(K);
-    if (K == 16) return forward_tc<48>(X, rows, params, L, Y, err, s);
-    if (K == 8) return forward_tc<24>(X, rows, params, L, Y, err, s);
+    if (K == 16) return forward_tc<48>(X, rows, params, L, Y, col_stride, err, s);
+    if (K == 8) return forward_tc<24>(X, rows, params, L, Y, col_stride, err, s);
     return cudaErrorInvalidValue;
 }
 

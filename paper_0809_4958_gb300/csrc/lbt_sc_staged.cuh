@@ -314,9 +314,11 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const StagedTile<
                     coords(k, x, y, z);
                 }
                 const int fc = owning_face(x, y, z, Ei, per, pp, qq);
+                float res[3];
+                load_mlp_residual(p, bd, th.mlp_s, fc, pp, qq, res);
                 R ub[3];
                 boundary_velocity<R>(ring, p.ring_slot_elems, bd, fc, pp, qq, tw, ub);
-                add_mlp_residual<R>(p, bd, th.mlp_s, fc, pp, qq, ub);
+                add_mlp_residual<R>(p, bd, res, ub);
                 drho[k] = th.drho_b;
                 ux[k] = (A)ub[0];
                 uy[k] = (A)ub[1];

@@ -7,6 +7,9 @@ captures (each holds a few GB of device memory at most).
   python -m paper_0809_4958_gb300.profile_cases mlp_forward [boxes]
       three launches of the upsampler forward over the face rows of that many
       64^3 boxes (K = 16)
+  python -m paper_0809_4958_gb300.profile_cases step_interp [mlp|hermite] [boxes] [steps]
+      that many 64^3 boxes (FP32, K = 16) stepped with the learned upsampler
+      (random-init network) or with Hermite time interpolation alone
 """
 from __future__ import annotations
 
@@ -51,7 +54,40 @@ def mlp_forward(boxes: int = 256) -> None:
     print("mlp_forward", rows, "rows")
 
 
+def step_interp(mode: str = "mlp", boxes: int = 64, steps: int = 32) -> None:
+    import torch
+
+    from . import inputs, lbtracer as lbt
+    lbt.load()
+    K, E = 16, 64
+    ti = lbt.LB_TIME_MLP if mode == "mlp" else lbt.LB_TIME_HERMITE
+    tr = lbt.Tracers([lbt.box_desc(E, 0.8, time_interp=ti, K=K) for _ in range(boxes)], lbt.LB_STORE_F32,
+                     stream=torch.cuda.Stream(), ring_slots=4)
+    torch.cuda.synchronize()
+    for b in range(boxes):
+        tr.lb_init(b, torch.zeros((3, E, E, E), device="cuda"))
+    if ti == lbt.LB_TIME_MLP:
+        params = lbt.Upsampler(K=K, batch_rows=1024, master=inputs.mlp_init(0, K)).export()
+        tr.lb_mlp_bind(params, 0.05)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    nface = boxes * 18 * E * E
+    nsamp = steps // K + 4
+    faces = [torch.randn(nface, device="cuda", generator=gen) * 0.01 for _ in range(nsamp)]
+    pushed = -1
+    for n in range(steps):
+        while pushed < n // K + 2:
+            pushed += 1
+            tr.lb_set_boundary(lbt.LB_ALL_BOXES, pushed, faces[pushed])
+        tr.lb_step(1)
+    tr.lb_sync()
+    print("step_interp", mode, boxes, "boxes", steps, "steps")
+
+
 if __name__ == "__main__":
     case = sys.argv[1] if len(sys.argv) > 1 else "batch"
-    args = [int(a) for a in sys.argv[2:]]
-    {"batch": batch, "mlp_forward": mlp_forward}[case](*args)
+    if case == "step_interp":
+        mode = sys.argv[2] if len(sys.argv) > 2 else "mlp"
+        step_interp(mode, *[int(a) for a in sys.argv[3:]])
+    else:
+        args = [int(a) for a in sys.argv[2:]]
+        {"batch": batch, "mlp_forward": mlp_forward}[case](*args)
