@@ -112,8 +112,8 @@ typedef struct lb_box_desc {
     int32_t time_interp;   /* LB_TIME_* */
     int32_t K;             /* LB steps per coarse sample interval, >= 1 */
     int32_t nbeads;        /* capacity for the chain of this box (0 = no chain), <= 256 */
-    int32_t zoom;          /* z = coarse grid spacing in sites (Sec. 3); 0 or 1: samples on every site */
-    int32_t reserved;      /* 0 */
+    int32_t zoom;          /* z = coarse grid spacing in sites (Sec. 2-3); 0 or 1: samples on every site */
+    int32_t frame_accel;   /* 1: the box also takes frame-acceleration samples (lb_set_frame_accel); 0 */
     double tau;            /* BGK relaxation time, > 1/2 */
     double rho_b;          /* density of the boundary equilibrium (1.0) */
     double body_accel[3];  /* uniform body acceleration a; force density rho a (Guo forcing) */
@@ -189,6 +189,19 @@ int32_t lb_init(lb_ctx* ctx, int32_t box, const void* u0);
  *   asynchronous).
  */
 int32_t lb_set_boundary(lb_ctx* ctx, int32_t box, int64_t sample_index, const void* face_u);
+
+/*
+ * lb_set_frame_accel -- push frame-acceleration sample j (taken at t = j K)
+ * of a box created with frame_accel = 1 (Sec. 2: in the co-moving frame of
+ * the tracer the flow w = u - v(t) feels the extra force density
+ * rho (-dv/dt)).  a: host, 3 doubles, the acceleration -dv/dt in lattice
+ * units at t = jK.  Step n -> n+1 applies the body acceleration
+ * body_accel + a(t_n), a(t_n) linear between samples j = n / K and j + 1
+ * (both must have been pushed; they share the boundary ring's slots, so the
+ * same ordering rule as lb_set_boundary holds).  Enqueued on the context
+ * stream.  LB_ERR_ARG for a box without frame_accel.
+ */
+int32_t lb_set_frame_accel(lb_ctx* ctx, int32_t box, int64_t sample_index, const double* a);
 
 /*
  * chain_couple -- place the bead-spring chain of a box (Sec. 1 and 2).

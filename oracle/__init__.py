@@ -425,3 +425,30 @@ def vorticity_mean(u, lo, hi):
     wy = d(0, 0) - d(2, 2)  # d u_x / dz - d u_z / dx
     wz = d(1, 2) - d(0, 1)  # d u_y / dx - d u_x / dy
     return float(np.sqrt(wx * wx + wy * wy + wz * wz).mean())
+
+
+def frame_accel_at(accel, frame_samples, K, n):
+    """Body acceleration of step n of a box in the tracer's co-moving frame
+    (Sec. 2: the transformed flow w = u - v(t) feels the force density
+    rho (-dv/dt)): the constant body acceleration plus the frame-acceleration
+    samples [J][3] (taken at t = jK) interpolated linearly at t_n between
+    samples j = n // K and j + 1."""
+    j = n // K
+    th = (n - j * K) / K
+    a = np.asarray(accel, dtype=np.float64) + (1.0 - th) * np.asarray(frame_samples[j], dtype=np.float64)
+    return a + th * np.asarray(frame_samples[j + 1], dtype=np.float64)
+
+
+def run_frame(box: BoxParams, A, samples, frame_samples, n0, nsteps, chain: ChainParams | None = None, pos=None,
+              vel=None):
+    """Steps n0 .. n0 + nsteps - 1 from state A with the body acceleration of
+    each step taken from frame_accel_at (the box's own accel is the constant
+    part).  Returns (status, A, pos, vel)."""
+    from dataclasses import replace
+    for n in range(n0, n0 + nsteps):
+        bn = replace(box, accel=tuple(frame_accel_at(box.accel, frame_samples, box.K, n)))
+        st, A, pos, vel, _ = step_from(bn, A, samples, n, chain, pos, vel)
+        if st:
+            return st, A, pos, vel
+    return 0, A, pos, vel
+

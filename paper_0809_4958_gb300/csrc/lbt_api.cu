@@ -80,6 +80,11 @@ int validate_boxes(const lb_box_desc* boxes, int nboxes, int storage, std::strin
             why = buf;
             return LB_ERR_ARG;
         }
+        if (d.frame_accel != 0 && d.frame_accel != 1) {
+            snprintf(buf, sizeof buf, "box %d: frame_accel must be 0 or 1", b);
+            why = buf;
+            return LB_ERR_ARG;
+        }
         if (d.K < 1 || d.nbeads < 0 || d.nbeads > kMaxBeads || !(d.rho_b > 0.0)) {
             snprintf(buf, sizeof buf, "box %d: need K >= 1, 0 <= nbeads <= %d, rho_b > 0", b, kMaxBeads);
             why = buf;
@@ -137,6 +142,10 @@ Layout plan_layout(const lb_box_desc* boxes, int nboxes, int storage, int ring_s
     off = align_up(off + sizeof(int64_t));
     L.tile_counter = off;
     off = align_up(off + sizeof(int64_t));
+    L.faccel = off;  // frame-acceleration samples [box][ring slot][4]
+    off = align_up(off + sizeof(double) * 4 * (size_t)nboxes * ring_slots);
+    L.chain_accel = off;  // body acceleration of the step per chain [chain][4]
+    off = align_up(off + sizeof(double) * 4 * (size_t)nboxes);
     // upsampler: feature-set table, bf16 features and f32 outputs of all its boxes
     L.mlp_rows = 0;
     L.mlp_boxes = 0;
@@ -182,6 +191,7 @@ struct lb_ctx {
     bool a_is_pop_a = true;            // which buffer holds the current state
     int64_t step = 0;                  // steps enqueued so far
     std::vector<int64_t> pushed;       // last boundary sample pushed per box (-1 none)
+    std::vector<double> faccel_host;   // host copy of the frame-acceleration samples [box][slot][4]
     int kernel = LB_KERNEL_STAGED;
     int max_beads = 0;  // largest chain capacity of the context
     int sms = 0;        // multiprocessors of the context's device
@@ -286,6 +296,16 @@ int check_samples(lb_ctx* ctx, int64_t n0, int64_t nsteps)
     return LB_OK;
 }
 
+// Box record with the body acceleration of the current step (reported fields)
+BoxDev box_at_step(const lb_ctx* ctx, int box)
+{
+    BoxDev bd = ctx->boxes[box];
+    double a[3];
+    frame_accel_at(bd, ctx->faccel_host.data(), ctx->L.ring_slots, ctx->step, a);
+    for (int c = 0; c < 3; c++) bd.accel[c] = a[c];
+    return bd;
+}
+
 // Enqueue one step n -> n+1 for every box; swaps the buffers.  At the start
 // of a coarse interval the upsampler boxes first get their residuals.
 int enqueue_step(lb_ctx* ctx, int64_t n)
@@ -319,6 +339,9 @@ int enqueue_step(lb_ctx* ctx, int64_t n)
         bp.pos = ctx->at<double>(ctx->L.pos);
         bp.vel = ctx->at<double>(ctx->L.vel);
         bp.forces = ctx->at<ForceEntry>(ctx->L.forces);
+        bp.faccel = ctx->at<double>(ctx->L.faccel);
+        bp.chain_accel = ctx->at<double>(ctx->L.chain_accel);
+        bp.ring_slots = ctx->L.ring_slots;
         bp.step = ctx->at<int64_t>(ctx->L.step);
         bp.status = ctx->at<int32_t>(ctx->L.status);
         CK(DISPATCH(ctx->storage, bead_couple(bp, nch, ctx->max_beads, ctx->bead_lanes, ctx->bead_bpt, ctx->side)));
@@ -330,6 +353,7 @@ int enqueue_step(lb_ctx* ctx, int64_t n)
     sp.ring = ctx->arena + ctx->L.ring;
     sp.ring_slot_elems = (int64_t)ctx->L.ring_slot_elems;
     sp.ring_slots = ctx->L.ring_slots;
+    sp.faccel = ctx->at<double>(ctx->L.faccel);
     sp.mlp_y = ctx->at<float>(ctx->L.mlp_y);
     sp.mlp_ystride = ctx->L.mlp_rows;
     sp.mlp_yunit = (float)(ctx->mlp_umax / kMlpOutDiv);
@@ -367,6 +391,7 @@ int enqueue_step(lb_ctx* ctx, int64_t n)
     fp.boxes = ctx->at<BoxDev>(ctx->L.boxes);
     fp.chains = ctx->at<ChainDev>(ctx->L.chains);
     fp.forces = ctx->at<ForceEntry>(ctx->L.forces);
+    fp.chain_accel = ctx->at<double>(ctx->L.chain_accel);
     fp.status = ctx->at<int32_t>(ctx->L.status);
     fp.step = ctx->at<int64_t>(ctx->L.step);
     fp.tile_counter = ctx->at<int64_t>(ctx->L.tile_counter);
@@ -473,6 +498,7 @@ int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int
     ctx->arena = reinterpret_cast<char*>(arena);
     ctx->stream = reinterpret_cast<cudaStream_t>(stream);
     ctx->pushed.assign(nboxes, -1);
+    ctx->faccel_host.assign((size_t)nboxes * ring_slots * 4, 0.0);
     ctx->vw = lbt_staged_default_spt(storage);  // the default kernel is the staged one
     ctx->threads = 0;
     int dev = 0;
@@ -516,10 +542,13 @@ int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int
         bd.time_interp = d.time_interp;
         bd.K = d.K;
         bd.chain = -1;
+        bd.frame = d.frame_accel;
+        bd.box = b;
         bd.tau = d.tau;
         bd.rho_b = d.rho_b;
         for (int a = 0; a < 3; a++) bd.accel[a] = d.body_accel[a];
-        bd.has_accel = (d.body_accel[0] != 0.0 || d.body_accel[1] != 0.0 || d.body_accel[2] != 0.0) ? 1 : 0;
+        bd.has_accel =
+            (d.frame_accel || d.body_accel[0] != 0.0 || d.body_accel[1] != 0.0 || d.body_accel[2] != 0.0) ? 1 : 0;
         if (d.nbeads > 0) {
             ChainDev ch{};
             ch.box = b;
@@ -653,6 +682,21 @@ int32_t lb_set_boundary(lb_ctx* ctx, int32_t box, int64_t j, const void* face_u)
         src += bytes;
         ctx->pushed[b] = j;
     }
+    return LB_OK;
+}
+
+int32_t lb_set_frame_accel(lb_ctx* ctx, int32_t box, int64_t sample_index, const double* a)
+{
+    if (!ctx || !a || sample_index < 0) return LB_ERR_ARG;
+    if (box < 0 || box >= ctx->nboxes) return ctx->fail(LB_ERR_ARG, "box index out of range");
+    if (!ctx->boxes[box].frame) return ctx->fail(LB_ERR_ARG, "box was created without frame_accel");
+    const int slot = (int)(sample_index % ctx->L.ring_slots);
+    double* h = ctx->faccel_host.data() + ((size_t)box * ctx->L.ring_slots + slot) * 4;
+    for (int c = 0; c < 3; c++) h[c] = a[c];
+    h[3] = 0.0;
+    // stream-ordered copy from pageable memory (staged when the call is made)
+    CK(cudaMemcpyAsync(ctx->at<double>(ctx->L.faccel) + ((size_t)box * ctx->L.ring_slots + slot) * 4, h,
+                       4 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     return LB_OK;
 }
 
@@ -800,7 +844,8 @@ int32_t lb_read_fields(lb_ctx* ctx, int32_t box, int32_t what, void* dst)
     } else if (what == LB_FIELD_RHO || what == LB_FIELD_U) {
         const size_t bytes = (what == LB_FIELD_RHO ? 1 : 3) * bd.n3 * rb;
         void* out = dev ? dst : reinterpret_cast<char*>(ctx->curB()) + bd.f_off * eb;  // staging in the free buffer
-        CK(DISPATCH(ctx->storage, fields(A, ctx->boxes.data(), box, bd.n3, what == LB_FIELD_RHO ? 0 : 1, out, ctx->stream)));
+        const BoxDev bn = box_at_step(ctx, box);
+        CK(DISPATCH(ctx->storage, fields(A, &bn, 0, bd.n3, what == LB_FIELD_RHO ? 0 : 1, out, ctx->stream)));
         if (!dev) CK(cudaMemcpyAsync(dst, out, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     } else if (what == LB_FIELD_DEV) {
         if (dev) {
@@ -858,7 +903,8 @@ int32_t lb_vorticity(lb_ctx* ctx, int32_t box, int32_t lo, int32_t hi, double* o
     char* stage = reinterpret_cast<char*>(ctx->curB()) + bd.f_off * eb;
     const size_t ubytes = (3 * (size_t)bd.n3 * rb + 255) / 256 * 256;
     double* sums = reinterpret_cast<double*>(stage + ubytes);
-    CK(DISPATCH(ctx->storage, fields(A, ctx->boxes.data(), box, bd.n3, 1, stage, ctx->stream)));
+    const BoxDev bn = box_at_step(ctx, box);
+    CK(DISPATCH(ctx->storage, fields(A, &bn, 0, bd.n3, 1, stage, ctx->stream)));
     CK(launch_vorticity(stage, ctx->storage == kF64, bd.E, lo, hi, sums, sums + 512, ctx->stream));
     double r = 0.0;
     CK(cudaMemcpyAsync(&r, sums + 512, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

@@ -33,12 +33,30 @@ struct BoxDev {
     int32_t has_accel;
     int32_t zoom;       // coarse grid spacing z in sites (1: samples on every site)
     int32_t Ec;         // coarse points per axis: point P at site P z, covering site E - 1
+    int32_t frame;      // 1: frame-acceleration samples add to accel (frame_accel_at)
+    int32_t box;        // index of this box in the box table
     uint64_t div_magic; // ceil(2^40 / E): site / E = (site * div_magic) >> 40
     int64_t mlp_row;    // first row of the box in the upsampler output, -1 if the box does not use it
     double tau;
     double rho_b;
     double accel[3];
 };
+
+// Body acceleration of box bd at step n: the constant body acceleration plus,
+// for a box with frame-acceleration samples, their linear interpolation at
+// t_n between samples j = n / K and j + 1 (Sec. 2: the force density
+// rho (-dv/dt) of the tracer's co-moving frame).  faccel: [box][slot][4].
+__host__ __device__ inline void frame_accel_at(const BoxDev& bd, const double* faccel, int slots, int64_t n,
+                                                        double a[3])
+{
+    for (int c = 0; c < 3; c++) a[c] = bd.accel[c];
+    if (!bd.frame) return;
+    const int64_t j = n / bd.K;
+    const double th = (double)(n - j * bd.K) / (double)bd.K;
+    const double* a0 = faccel + ((int64_t)bd.box * slots + j % slots) * 4;
+    const double* a1 = faccel + ((int64_t)bd.box * slots + (j + 1) % slots) * 4;
+    for (int c = 0; c < 3; c++) a[c] += (1.0 - th) * a0[c] + th * a1[c];
+}
 
 constexpr double kBeadSkin = 0.3;  // Verlet skin of the bead pair lists (lattice units)
 
@@ -90,7 +108,7 @@ struct ForceEntry {
 // Arena layout (byte offsets), computed by plan().
 struct Layout {
     size_t boxes, tile_prefix, chains, pop_a, pop_b, ring, pos, vel, forces, cons_partial, cons_out,
-        status, step, tile_counter, mlp_sets, mlp_x, mlp_y, total;
+        status, step, tile_counter, faccel, chain_accel, mlp_sets, mlp_x, mlp_y, total;
     size_t pop_bytes;        // bytes of one population buffer
     size_t ring_slot_elems;  // real elements per ring slot
     int32_t ring_slots;      // slots in the ring of coarse samples
@@ -115,6 +133,7 @@ struct SCParams {
     float mlp_yunit;              // velocity of one output unit (u_max / 64)
     const BoxDev* boxes;
     const int64_t* tile_prefix;   // [nboxes + 1] first tile of each box for the current block size
+    const double* faccel;         // frame-acceleration samples [box][ring slot][4]
     int32_t general;              // some box is periodic or carries a body force
     int32_t nboxes;
     int64_t total_tiles;
@@ -130,6 +149,9 @@ struct BeadParams {
     double* pos;
     double* vel;
     ForceEntry* forces;
+    const double* faccel;  // frame-acceleration samples [box][ring slot][4]
+    double* chain_accel;   // [chain][4]: the body acceleration of the step, for the forced sites
+    int32_t ring_slots;
     const int64_t* step;
     int32_t* status;
     int32_t max_beads;    // largest chain of the launch (shared-memory strides)
@@ -144,6 +166,7 @@ struct ForcedParams {
     const BoxDev* boxes;
     const ChainDev* chains;
     const ForceEntry* forces;
+    const double* chain_accel;    // [chain][4], written by the bead kernel of the step
     const int32_t* status;
     int64_t* step;                // incremented once per step by block 0
     int64_t* tile_counter;        // reset to zero once per step by block 0

@@ -32,7 +32,8 @@ namespace lbt {
 // warp shuffle, or loaded directly at a warp edge and at a periodic x wrap.
 // ---------------------------------------------------------------------------
 template <int ST, int VW, bool ACCEL>
-__device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, int64_t G, int64_t n, int lane)
+__device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, const double acc[3], int64_t G, int64_t n,
+                                        int lane)
 {
     using S = Stor<ST>;
     using E = typename S::E;
@@ -116,9 +117,9 @@ __device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, int
         const A rho = A(1) + r;
         const A inv = A(1) / rho;
         if (ACCEL) {
-            jx += A(0.5) * rho * (A)bd.accel[0];
-            jy += A(0.5) * rho * (A)bd.accel[1];
-            jz += A(0.5) * rho * (A)bd.accel[2];
+            jx += A(0.5) * rho * (A)acc[0];
+            jy += A(0.5) * rho * (A)acc[1];
+            jz += A(0.5) * rho * (A)acc[2];
         }
         drho[k] = r;
         ux[k] = jx * inv;
@@ -162,7 +163,7 @@ __device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, int
 #pragma unroll
     for (int k = 0; k < VW; k++) {
         usq[k] = A(1.5) * (ux[k] * ux[k] + uy[k] * uy[k] + uz[k] * uz[k]);
-        if (ACCEL) ua[k] = ux[k] * (A)bd.accel[0] + uy[k] * (A)bd.accel[1] + uz[k] * (A)bd.accel[2];
+        if (ACCEL) ua[k] = ux[k] * (A)acc[0] + uy[k] * (A)acc[1] + uz[k] * (A)acc[2];
     }
 #pragma unroll
     for (int i = 0; i < kQ; i++) {
@@ -180,7 +181,7 @@ __device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, int
             const A f = fval(i, k);
             A val = f + om * (deq - f);
             if (ACCEL) {
-                const A ca = (A)(cx * bd.accel[0] + cy * bd.accel[1] + cz * bd.accel[2]);
+                const A ca = (A)(cx * acc[0] + cy * acc[1] + cz * acc[2]);
                 val += srcfac * w * rho * (A(3) * (ca - ua[k]) + A(9) * cu * ca);
             }
             if (bmask & (1u << k)) val = deq;
@@ -220,8 +221,10 @@ __global__ void __launch_bounds__(256) k_stream_collide(SCParams p)
             copy_tile<ST, VW>(p, bd, G);  // frozen box: state does not change
             continue;
         }
-        if (bd.has_accel) sc_tile<ST, VW, true>(p, bd, G, n, lane);
-        else sc_tile<ST, VW, false>(p, bd, G, n, lane);
+        double acc[3];
+        frame_accel_at(bd, p.faccel, p.ring_slots, n, acc);  // body acceleration of step n
+        if (bd.has_accel) sc_tile<ST, VW, true>(p, bd, acc, G, n, lane);
+        else sc_tile<ST, VW, false>(p, bd, acc, G, n, lane);
     }
 }
 
@@ -774,9 +777,12 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     double* vel = p.vel + 3 * ch.bead_off;
     if (tid == 0) {
         sErr = 0;
+        double acc[3];  // body acceleration of step n, also handed to the forced sites
+        frame_accel_at(bd, p.faccel, p.ring_slots, n, acc);
         for (int a = 0; a < 3; a++) {
             sRc[a] = pos[a];
-            sAcc[a] = (A)bd.accel[a];
+            sAcc[a] = (A)acc[a];
+            p.chain_accel[4 * blockIdx.x + a] = acc[a];
         }
     }
     __syncthreads();
@@ -1013,7 +1019,7 @@ __global__ void __launch_bounds__(kForcedThreads) k_forced(ForcedParams p)
             const A rho = A(1) + dr;
             A F[3], u[3];
             for (int a = 0; a < 3; a++) {
-                F[a] = rho * (A)bd.accel[a] + (A)fe.g[a];
+                F[a] = rho * (A)p.chain_accel[4 * chain + a] + (A)fe.g[a];
                 u[a] = (j[a] + A(0.5) * F[a]) / rho;
             }
             const A om = A(1) / (A)bd.tau;

@@ -463,6 +463,11 @@ __device__ __forceinline__ void staged_produce(const SCParams& p, unsigned char*
         static_assert(sizeof(BoxDev) % 8 == 0, "box record copied in 8-byte words");
         for (int w = 0; w < (int)(sizeof(BoxDev) / 8); w++)  // word by word: few live registers
             reinterpret_cast<uint64_t*>(&th.bd)[w] = reinterpret_cast<const uint64_t*>(&bd)[w];
+        if (bd.frame) {  // the header carries the body acceleration of step n
+            double a[3];
+            frame_accel_at(bd, p.faccel, p.ring_slots, n, a);
+            for (int c = 0; c < 3; c++) th.bd.accel[c] = a[c];
+        }
         th.box = b;
         th.s0 = s0;
         th.mlp_s = mlp_s;

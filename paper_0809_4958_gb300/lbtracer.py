@@ -28,7 +28,8 @@ ERROR_NAMES = {0: "LB_OK", 1: "LB_ERR_ARG", 2: "LB_ERR_CUDA", 3: "LB_ERR_FENE", 
                5: "LB_ERR_NONFINITE", 6: "LB_ERR_TIMEOUT", 7: "LB_ERR_STATE", 8: "LB_ERR_SIZE", 9: "LB_ERR_CHAIN"}
 
 EXPORTS = ["lb_plan", "lb_create", "lb_destroy", "lb_init", "lb_set_boundary", "chain_couple", "lb_step",
-           "lb_graph_capture", "lb_graph_launch", "lb_read_fields", "lb_conservation", "lb_vorticity", "lb_sync", "lb_status",
+           "lb_graph_capture", "lb_graph_launch", "lb_read_fields", "lb_conservation", "lb_vorticity", "lb_set_frame_accel", "lb_sync",
+           "lb_status",
            "lb_current_step", "lb_set_launch", "lb_set_bead_launch", "lb_profile", "lb_profile_read", "lb_last_error", "lb_synth_workspace_bytes", "lb_synth_faces",
            "lb_synth_volume", "lb_population_sums_noalloc", "lb_mlp_param_bytes", "lb_mlp_bind", "lb_mlp_train_bytes",
            "lb_mlp_train_init", "lb_mlp_features", "lb_mlp_targets", "lb_mlp_forward", "lb_mlp_grad",
@@ -38,7 +39,7 @@ EXPORTS = ["lb_plan", "lb_create", "lb_destroy", "lb_init", "lb_set_boundary", "
 class lb_box_desc(ctypes.Structure):
     _fields_ = [("E", ctypes.c_int32), ("face_mode", ctypes.c_int32 * 6), ("time_interp", ctypes.c_int32),
                 ("K", ctypes.c_int32), ("nbeads", ctypes.c_int32), ("zoom", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("tau", ctypes.c_double), ("rho_b", ctypes.c_double),
+                ("frame_accel", ctypes.c_int32), ("tau", ctypes.c_double), ("rho_b", ctypes.c_double),
                 ("body_accel", ctypes.c_double * 3)]
 
 
@@ -85,6 +86,7 @@ def load(path: str | None = None, build_if_missing: bool = True):
         "lb_read_fields": (_i32, [_vp, _i32, _i32, _vp]),
         "lb_conservation": (_i32, [_vp, _i32, _vp]),
         "lb_vorticity": (_i32, [_vp, _i32, _i32, _i32, _vp]),
+        "lb_set_frame_accel": (_i32, [_vp, _i32, _i64, _vp]),
         "lb_sync": (_i32, [_vp, _i32]),
         "lb_status": (_i32, [_vp, _i32, ctypes.POINTER(_i32)]),
         "lb_current_step": (_i64, [_vp]),
@@ -143,10 +145,11 @@ def _torch():
 
 
 def box_desc(E, tau, periodic=(False, False, False), time_interp=LB_TIME_LINEAR, K=1, nbeads=0, rho_b=1.0,
-             accel=(0.0, 0.0, 0.0), zoom=1) -> lb_box_desc:
+             accel=(0.0, 0.0, 0.0), zoom=1, frame_accel=False) -> lb_box_desc:
     d = lb_box_desc()
     d.E = int(E)
     d.zoom = int(zoom)
+    d.frame_accel = 1 if frame_accel else 0
     for a in range(3):
         m = LB_FACE_PERIODIC if periodic[a] else LB_FACE_VELOCITY
         d.face_mode[2 * a] = m
@@ -226,6 +229,11 @@ class Tracers:
         out = np.zeros(7)
         _check(self.lib.lb_conservation(self.ctx, box, out.ctypes.data), self.ctx)
         return out
+
+    def lb_set_frame_accel(self, box, j, a):
+        """Frame-acceleration sample j (3 values, -dv/dt at t = jK) of a box created with frame_accel."""
+        arr = np.ascontiguousarray(a, dtype=np.float64).reshape(3)
+        _check(self.lib.lb_set_frame_accel(self.ctx, int(box), int(j), arr.ctypes.data), self.ctx)
 
     def lb_vorticity(self, box, lo, hi):
         """Mean |curl u| over the sites lo <= x, y, z <= hi of a box."""
