@@ -164,3 +164,18 @@ def mlp_init(seed: int, K: int, scale: float = 1.0) -> np.ndarray:
     W3 = rng.normal(0.0, np.sqrt(1.0 / 128), (128, 3 * K)) * scale * 0.1
     return np.concatenate([W1.ravel(), np.zeros(128), W2.ravel(), np.zeros(128), W3.ravel(),
                            np.zeros(3 * K)]).astype(np.float32)
+
+
+def tracer_velocity(modes: Modes, t) -> np.ndarray:
+    """Velocity of the synthetic field at the box centre (the tracer's own
+    velocity v(t), which the co-moving frame subtracts) at times t: [len(t)][3]."""
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    return np.cos(modes.omega[None, :] * t[:, None] + modes.phi[None, :]) @ modes.amp
+
+
+def tracer_frame_accel(modes: Modes, t) -> np.ndarray:
+    """Frame acceleration -dv/dt of the tracer at the box centre at times t:
+    [len(t)][3] (the time derivative of tracer_velocity, negated)."""
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    return (modes.omega[None, :] * np.sin(modes.omega[None, :] * t[:, None] + modes.phi[None, :])) @ modes.amp
+
