@@ -4,7 +4,7 @@
 Workload (default): one D3Q19 BGK box of 128^3 sites, tau 0.8, FP32
 populations stored as deviations f_i - w_i, velocity boundaries on all six
 faces from a synthetic Kolmogorov-spectrum field (1024 modes, |k| in
-[1, 64], one coarse sample per LB step), one 64-bead FENE chain with
+[1, 64], one coarse sample per LB step), one 64-bead Kremer-Grest chain (FENE + WCA) with
 Philox noise at kT 1e-4 coupled by Stokes friction.  One "step" is one full
 LB step: bead coupling, fused stream-collide + boundary layer, forced
 re-collision; the timed steps replay a CUDA graph of 16 steps, the samples
@@ -54,9 +54,10 @@ def parse():
     p.add_argument("--vw", type=int, default=0, help="sites per thread in stream-collide (0 = default)")
     p.add_argument("--kernel", default="staged", choices=["staged", "register"],
                    help="stream-collide kernel: TMA-staged pipeline or register tiles")
-    p.add_argument("--config", default="single", choices=["single", "batch", "precision", "mlp"],
+    p.add_argument("--config", default="single", choices=["single", "batch", "precision", "mlp", "paper"],
                    help="single 128^3 box (default), 512 uneven boxes under a CUDA graph, 256^3 16-bit storage, "
-                        "or 256 boxes of 64^3 with the learned boundary upsampler (K = 16)")
+                        "256 boxes of 64^3 with the learned boundary upsampler (K = 16), or the paper-shaped "
+                        "replay (z = 6, tau = 1, Eq. 1 time step, co-moving frame force)")
     return p.parse_args()
 
 
@@ -246,7 +247,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "tracer box %d^3 D3Q19 BGK tau %.2f, 64-bead FENE chain kT %g, Kolmogorov "
+            "config": {"workload": "tracer box %d^3 D3Q19 BGK tau %.2f, 64-bead Kremer-Grest chain kT %g, Kolmogorov "
                                    "velocity boundaries (K=1); FP64 CPU oracle" % (w["E"], w["tau"], w["kT"])},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": "each step: one oracle LB step of a %d^3 box with the same recipe" % Es},
@@ -256,7 +257,8 @@ def run_reference(args):
 
 def main():
     args = parse()
-    defaults = {"single": (10000, 50), "batch": (1008, 112), "precision": (5000, 20), "mlp": (1024, 64)}[args.config]
+    defaults = {"single": (10000, 50), "batch": (1008, 112), "precision": (5000, 20), "mlp": (1024, 64),
+                "paper": (4000, 64)}[args.config]
     if args.steps is None:
         args.steps = defaults[0]
     if args.warmup is None:
@@ -272,6 +274,9 @@ def main():
         return
     if args.config == "mlp":
         run_mlp(args)
+        return
+    if args.config == "paper":
+        run_paper(args)
         return
     import torch
     import torch.distributed as dist
@@ -547,6 +552,83 @@ def run_batch(args):
 
 
 PRECISION = dict(E=256, tau=0.8, M=2048, k_min=1.0, k_max=128.0, K=1, seed=3)
+
+
+def run_paper(args):
+    """The paper-shaped replay: one box of 128^3 (the paper's 121 sites
+    rounded to the 8-site alignment) zoomed z = 6 from a 23^2 coarse face
+    grid, tau = 1, one coarse sample every 0.05 tau_eta mapped by Eq. (1)
+    (113 LB steps), the flow in the tracer's co-moving frame with the frame
+    force from the tracer's acceleration, a 64-bead chain at the centre; FP32,
+    graphs of 16 steps, samples pushed before each replay."""
+    import torch
+
+    from paper_0809_4958_gb300 import inputs, lbtracer as lbt, scaling
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    eta, tau_eta = scaling.kolmogorov(1.0 / 400.0, 0.1)
+    um = scaling.UnitMap(eta=eta, tau_eta=tau_eta, delta=2 * np.pi / 1024, z=6, tau=1.0)
+    K = int(round(um.steps(0.05 * tau_eta)))
+    E, z, nb, G = 128, 6, 64, 16
+    steps = (args.steps + G - 1) // G * G
+    warm = (args.warmup + G - 1) // G * G
+    u_eta = um.eta_lb / um.tau_eta_lb
+    modes = inputs.mode_table(21, 256, 1.0, 10.0, E, u_max=3 * u_eta)
+    J = (warm + steps + G) // K + 3
+    faces = lbt.synth_faces(modes, E, K, 0, J, torch.float32, zoom=z)
+    v = inputs.tracer_velocity(modes, np.arange(J) * K)
+    faces -= torch.from_numpy(v).to(faces)[:, None, :, None, None]  # co-moving frame
+    u0 = lbt.synth_volume(modes, E, 0.0, torch.float32, zoom=z) - torch.from_numpy(v[0]).to(faces)[:, None, None, None]
+    fsamp = inputs.tracer_frame_accel(modes, np.arange(J) * K)
+    stream = torch.cuda.Stream()
+    tr = lbt.Tracers([lbt.box_desc(E, 1.0, K=K, nbeads=nb, zoom=z, frame_accel=True)], lbt.LB_STORE_F32,
+                     stream=stream)
+    torch.cuda.synchronize()
+    tr.lb_init(0, u0.contiguous())
+    tr.chain_couple(0, lbt.chain_desc(nb, kT=1e-4, seed=5), inputs.chain_start(3, nb, E))
+    pushed = [-1]
+
+    def push_until(n):  # samples needed by the steps before n
+        while pushed[0] < (n - 1) // K + 1:
+            pushed[0] += 1
+            tr.lb_set_boundary(0, pushed[0], faces[pushed[0]])
+            tr.lb_set_frame_accel(0, pushed[0], fsamp[pushed[0]])
+
+    for _ in range(warm):
+        push_until(tr.lb_current_step() + 1)
+        tr.lb_step(1)
+    tr.lb_sync()
+    tr.lb_graph_capture(G)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    for _ in range(steps // G):
+        push_until(tr.lb_current_step() + G)
+        tr.lb_graph_launch()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    tr.lb_sync()
+    ms = ev0.elapsed_time(ev1)
+    value = E ** 3 * steps / (ms * 1e-3) / 1e6
+    tr.close()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warm,
+            "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "paper-shaped replay: 128^3 box zoomed z = 6 from a 23^2 coarse face grid, tau 1, "
+                                   "one coarse sample every %d LB steps (0.05 tau_eta by Eq. 1), co-moving frame "
+                                   "with the tracer's frame force, 64-bead chain, synthetic field (|k| in [1, 10], "
+                                   "3 u_eta); CUDA graphs of %d steps" % (K, G),
+                       "eta_lb_sites": um.eta_lb, "tau_eta_lb_steps": um.tau_eta_lb, "mach": um.mach,
+                       "l2": "working set 2 x 159 MB > L2, no flush"},
+            "roofline": None, "clocks": clk, "e2e": None, "gpu_launches": steps * 3}
+    print(json.dumps(line), flush=True)
 
 
 def run_precision(args):
