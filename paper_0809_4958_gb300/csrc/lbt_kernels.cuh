@@ -45,6 +45,8 @@ __device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, con
     const int Ei = bd.E;
     const int64_t n3 = bd.n3;
     const int gpr = Ei / VW;
+    // body acceleration of the step in the arithmetic type, converted once
+    const A acA[3] = {(A)acc[0], (A)acc[1], (A)acc[2]};
     const int64_t groups = n3 / VW;
     const bool active = G < groups;
     const int64_t Gc = active ? G : 0;
@@ -117,9 +119,9 @@ __device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, con
         const A rho = A(1) + r;
         const A inv = A(1) / rho;
         if (ACCEL) {
-            jx += A(0.5) * rho * (A)acc[0];
-            jy += A(0.5) * rho * (A)acc[1];
-            jz += A(0.5) * rho * (A)acc[2];
+            jx += A(0.5) * rho * acA[0];
+            jy += A(0.5) * rho * acA[1];
+            jz += A(0.5) * rho * acA[2];
         }
         drho[k] = r;
         ux[k] = jx * inv;
@@ -163,7 +165,7 @@ __device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, con
 #pragma unroll
     for (int k = 0; k < VW; k++) {
         usq[k] = A(1.5) * (ux[k] * ux[k] + uy[k] * uy[k] + uz[k] * uz[k]);
-        if (ACCEL) ua[k] = ux[k] * (A)acc[0] + uy[k] * (A)acc[1] + uz[k] * (A)acc[2];
+        if (ACCEL) ua[k] = ux[k] * acA[0] + uy[k] * acA[1] + uz[k] * acA[2];
     }
 #pragma unroll
     for (int i = 0; i < kQ; i++) {
@@ -181,7 +183,10 @@ __device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, con
             const A f = fval(i, k);
             A val = f + om * (deq - f);
             if (ACCEL) {
-                const A ca = (A)(cx * acc[0] + cy * acc[1] + cz * acc[2]);
+                A ca = A(0);  // c_i . a in the arithmetic type (FP64 is slow on this part)
+                if (cx) ca += cx * acA[0];
+                if (cy) ca += cy * acA[1];
+                if (cz) ca += cz * acA[2];
                 val += srcfac * w * rho * (A(3) * (ca - ua[k]) + A(9) * cu * ca);
             }
             if (bmask & (1u << k)) val = deq;

@@ -215,6 +215,10 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const StagedTile<
 
     const int Ei = bd.E;
     const int n3 = (int)bd.n3;
+    // body acceleration of the step in the arithmetic type, converted once
+    A acA[3] = {A(0), A(0), A(0)};
+    if (ACCEL)
+        for (int c = 0; c < 3; c++) acA[c] = (A)bd.accel[c];
     const uint64_t mE = bd.div_magic;
     const int per = bd.per_mask;
     const bool px = per & 1, py = per & 2, pz = per & 4;
@@ -284,9 +288,9 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const StagedTile<
         const A rho = A(1) + r;
         const A inv = A(1) / rho;
         if (ACCEL) {
-            jx += A(0.5) * rho * (A)bd.accel[0];
-            jy += A(0.5) * rho * (A)bd.accel[1];
-            jz += A(0.5) * rho * (A)bd.accel[2];
+            jx += A(0.5) * rho * acA[0];
+            jy += A(0.5) * rho * acA[1];
+            jz += A(0.5) * rho * acA[2];
         }
         drho[k] = r;
         ux[k] = jx * inv;
@@ -332,7 +336,7 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const StagedTile<
     for (int k = 0; k < SPT; k++) {
         usq[k] = A(1.5) * (ux[k] * ux[k] + uy[k] * uy[k] + uz[k] * uz[k]);
         rho_[k] = A(1) + drho[k];
-        if (ACCEL) ua[k] = ux[k] * (A)bd.accel[0] + uy[k] * (A)bd.accel[1] + uz[k] * (A)bd.accel[2];
+        if (ACCEL) ua[k] = ux[k] * acA[0] + uy[k] * acA[1] + uz[k] * acA[2];
     }
     // post-collision value of population i at site k from its equilibrium deviation
     // populations are written in order 0, 1, ..., 18 through one running
@@ -344,7 +348,10 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const StagedTile<
             val = om1 * f[i][k] + om * deq;
             if (ACCEL) {
                 const A w = wgt<A>(i);
-                const A ca = (A)(cvec(i, 0) * bd.accel[0] + cvec(i, 1) * bd.accel[1] + cvec(i, 2) * bd.accel[2]);
+                A ca = A(0);  // c_i . a in the arithmetic type (FP64 is slow on this part)
+                if (cvec(i, 0)) ca += cvec(i, 0) * acA[0];
+                if (cvec(i, 1)) ca += cvec(i, 1) * acA[1];
+                if (cvec(i, 2)) ca += cvec(i, 2) * acA[2];
                 val += srcfac * w * rho_[k] * (A(3) * (ca - ua[k]) + A(9) * cu * ca);
             }
         }
