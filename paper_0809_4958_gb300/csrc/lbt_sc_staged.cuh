@@ -435,7 +435,7 @@ __device__ __forceinline__ void staged_consume(const SCParams& p, unsigned char*
 // (reset to zero by the forced re-collision at the end of every step, so a
 // block that starts late -- its SM still busy with the bead kernel -- simply
 // takes fewer tiles) and fill the stages as the consumers free them.
-template <int ST, int SPT>
+template <int ST, int SPT, bool GENERAL>
 __device__ __forceinline__ void staged_produce(const SCParams& p, unsigned char* smem, StagedHeader<ST>* hd, int64_t n)
 {
     using G = Staged<ST, SPT>;
@@ -470,7 +470,8 @@ __device__ __forceinline__ void staged_produce(const SCParams& p, unsigned char*
         static_assert(sizeof(BoxDev) % 8 == 0, "box record copied in 8-byte words");
         for (int w = 0; w < (int)(sizeof(BoxDev) / 8); w++)  // word by word: few live registers
             reinterpret_cast<uint64_t*>(&th.bd)[w] = reinterpret_cast<const uint64_t*>(&bd)[w];
-        if (bd.frame) {  // the header carries the body acceleration of step n
+        if (GENERAL && bd.frame) {  // the header carries the body acceleration of step n (frame
+                                    // boxes carry a body force, so they run the general kernel)
             double a[3];
             frame_accel_at(bd, p.faccel, p.ring_slots, n, a);
             for (int c = 0; c < 3; c++) th.bd.accel[c] = a[c];
@@ -508,7 +509,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_stream_collide_staged(SCP
     }
     __syncthreads();
     if (threadIdx.x >= kStagedConsumers) {
-        if (threadIdx.x == kStagedConsumers) staged_produce<ST, SPT>(p, smem, hd, n);
+        if (threadIdx.x == kStagedConsumers) staged_produce<ST, SPT, GENERAL>(p, smem, hd, n);
         return;
     }
     staged_consume<ST, SPT, GENERAL>(p, smem, hd);
