@@ -49,3 +49,20 @@ def test_plan_validates_without_a_gpu():
     n20 = ctypes.c_size_t()
     assert lib.lb_plan(good, 1, lbt.LB_STORE_F32, 20, ctypes.byref(n20)) == lbt.LB_OK
     assert n20.value >= n.value + 16 * 6 * 3 * 32 * 32 * 4  # 16 more slots of six 32^2 faces
+
+
+def test_plan_checks_frame_accel_and_zoom_without_a_gpu():
+    from paper_0809_4958_gb300 import lbtracer as lbt
+    lib = lbt.load()
+    n = ctypes.c_size_t()
+    ok = lbt.box_desc(32, 0.8, frame_accel=True, zoom=6)
+    assert lib.lb_plan((lbt.lb_box_desc * 1)(ok), 1, lbt.LB_STORE_F32, 0, ctypes.byref(n)) == lbt.LB_OK
+    bad = lbt.box_desc(32, 0.8)
+    bad.frame_accel = 2
+    assert lib.lb_plan((lbt.lb_box_desc * 1)(bad), 1, lbt.LB_STORE_F32, 0, ctypes.byref(n)) == lbt.LB_ERR_ARG
+    assert b"frame_accel" in lib.lb_last_error(None)
+    for zoom in (-1, 32):  # zoom must lie in [0, E - 1]
+        bz = lbt.box_desc(32, 0.8, zoom=zoom)
+        assert lib.lb_plan((lbt.lb_box_desc * 1)(bz), 1, lbt.LB_STORE_F32, 0, ctypes.byref(n)) == lbt.LB_ERR_ARG
+    mlpz = lbt.box_desc(32, 0.8, time_interp=lbt.LB_TIME_MLP, K=16, zoom=2)  # the upsampler needs zoom <= 1
+    assert lib.lb_plan((lbt.lb_box_desc * 1)(mlpz), 1, lbt.LB_STORE_F32, 0, ctypes.byref(n)) == lbt.LB_ERR_ARG
