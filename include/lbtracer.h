@@ -234,7 +234,9 @@ int32_t lb_graph_launch(lb_ctx* ctx);
  * lb_read_fields -- observables of one box at the current step.
  *   LB_FIELD_RHO / LB_FIELD_U: on boundary sites the moments of the stored
  *   equilibrium; elsewhere the moments of the pulled populations
- *   f_i(x) = A_i(x - c_i), u = (j + rho a / 2) / rho.
+ *   f_i(x) = A_i(x - c_i), u = (j + rho a / 2) / rho, a the body
+ *   acceleration of the current step (body_accel plus, for a box with
+ *   frame_accel, the frame acceleration at t_n).
  *   dst: host or device memory of the size given with the LB_FIELD_* code.
  *   Synchronising (bounded wait, see lb_sync); returns a pending box error.
  */
