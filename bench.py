@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--vw", type=int, default=0, help="sites per thread in stream-collide (0 = default)")
     p.add_argument("--kernel", default="staged", choices=["staged", "register"],
                    help="stream-collide kernel: TMA-staged pipeline or register tiles")
+    p.add_argument("--dry-run", action="store_true",
+                   help="exercise the rank launcher and the whole-job reduction only (CPU, gloo): each rank reports "
+                        "fixed stand-in units and times, no GPU work, no measurement")
     p.add_argument("--config", default="single", choices=["single", "batch", "precision", "mlp", "paper"],
                    help="single 128^3 box (default), 512 uneven boxes under a CUDA graph, 256^3 16-bit storage, "
                         "256 boxes of 64^3 with the learned boundary upsampler (K = 16), or the paper-shaped "
@@ -66,6 +69,34 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def launch_ranks(args):
+    """--gpus N > 1 started without a process group in the environment: run
+    this script again under torch.distributed.run, one rank per GPU of this
+    node (rendezvous on 127.0.0.1).  Boxes are independent, so the ranks
+    exchange nothing while stepping; rank 0 prints the whole-job line."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(args.gpus),
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
+def run_dry(args):
+    """The launcher and the whole-job reduction without a GPU: rank r stands
+    in with (r + 1) * 1e6 site updates in 10 + r milliseconds."""
+    import torch.distributed as dist
+    rank, world, _ = dist_env()
+    if world > 1:
+        dist.init_process_group("gloo")
+    units, ms = whole_job((rank + 1) * 1e6, 10.0 + rank)
+    if rank == 0:
+        print(json.dumps({"dry_run": True, "n_gpus": world, "units": units, "ms": ms, "value": None}), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def whole_job(units, ms, device=None):
@@ -212,6 +243,18 @@ def cpu_baseline(storage_name):
                       "field, initial field at rest), after 1 untimed step" % (nsteps, E)}
 
 
+def single_config(storage_name):
+    """The workload of the default line, shared by both arms."""
+    w = WORKLOAD
+    E = w["E"]
+    s_elem = {"f32": 4, "f64": 8, "f16": 2, "bf16": 2}[storage_name]
+    return {"workload": "tracer box %d^3 D3Q19 BGK tau %.2f, %s populations (f_i - w_i), 64-bead Kremer-Grest chain "
+                        "kT %g, Kolmogorov velocity boundaries on 6 faces (1024 modes, one sample per step)"
+                        % (E, w["tau"], storage_name, w["kT"]),
+            "boxes_per_gpu": 1, "sites_per_box": E ** 3,
+            "l2": "working set 2 x %.0f MB > L2, no flush" % (Q * E ** 3 * s_elem / 1e6)}
+
+
 def run_reference(args):
     """--impl reference: the oracle as it stands, each timed step a bounded
     sample of the workload (one LB step of a box of edge E_s with the same
@@ -247,8 +290,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "tracer box %d^3 D3Q19 BGK tau %.2f, 64-bead Kremer-Grest chain kT %g, Kolmogorov "
-                                   "velocity boundaries (K=1); FP64 CPU oracle" % (w["E"], w["tau"], w["kT"])},
+            "config": single_config(args.storage),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": "each step: one oracle LB step of a %d^3 box with the same recipe" % Es},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -263,6 +305,11 @@ def main():
         args.steps = defaults[0]
     if args.warmup is None:
         args.warmup = defaults[1]
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(launch_ranks(args))
+    if args.dry_run:
+        run_dry(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -302,9 +349,10 @@ def main():
     modes = inputs.mode_table(seed, w["M"], w["k_min"], w["k_max"], E)
     ncand = 0 if args.no_tune else len(autotune.candidates(storage, torch.cuda.get_device_properties(dev).multi_processor_count))
     tune_steps = 7 * ncand + 7 * 5  # launch shapes, then the bead kernel's thread layouts
-    G = w["graph"]
-    args.steps = (args.steps + G - 1) // G * G
-    nsamp = args.warmup + tune_steps + args.steps + G + 2
+    # graph replays of G steps, then any remainder stepped plainly: exactly
+    # args.steps timed steps (G even, at most 16, at most the step count)
+    G = min(w["graph"], args.steps // 2 * 2)
+    nsamp = args.warmup + tune_steps + args.steps + w["graph"] + 2
     faces = lbt.synth_faces(modes, E, w["K"], 0, nsamp, real)
     u0 = lbt.synth_volume(modes, E, 0.0, real)
     pos0 = inputs.chain_start(seed + 5, w["nbeads"], E)
@@ -345,14 +393,18 @@ def main():
     torch.cuda.synchronize()
     # G steps per CUDA graph replay; the samples of the next G steps are pushed
     # (device to device) before each replay
-    tr.lb_profile(1, G)
-    tr.lb_graph_capture(G)
+    nrep = args.steps // G if G else 0
+    rest = args.steps - nrep * G
+    tr.lb_profile(1, G if nrep else rest)
+    if nrep:
+        tr.lb_graph_capture(G)
     clocks.start()
     time.sleep(0.3)  # let the sampler take its first reading
     ev0.record(stream)
-    for _ in range(args.steps // G):
+    for _ in range(nrep):
         push_until(tr.lb_current_step() + G, dev_src)
         tr.lb_graph_launch()
+    step(rest)
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -414,12 +466,10 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-        "config": {"workload": "tracer box %d^3 D3Q19 BGK tau %.2f, %s populations (f_i - w_i), 64-bead "
-                               "Kremer-Grest chain kT %g, Kolmogorov velocity boundaries on 6 faces (1024 modes, one "
-                               "sample per step); CUDA graph of %d steps" % (E, w["tau"], args.storage, w["kT"], G),
-                   "boxes_per_gpu": 1, "sites_per_box": E ** 3, "l2": "working set 2 x %.0f MB > L2, no flush"
-                   % (Q * E ** 3 * s_elem / 1e6), "launch": {"kernel": ["staged", "register"][choice[0]], "threads": choice[1], "ctas": choice[2],
-                              "sites_per_thread": choice[3], "bead_layout": list(getattr(tr, "bead_lanes", (0, 1)))},
+        "config": single_config(args.storage),
+        "launch": {"kernel": ["staged", "register"][choice[0]], "threads": choice[1], "ctas": choice[2],
+                   "sites_per_thread": choice[3], "bead_layout": list(getattr(tr, "bead_lanes", (0, 1))),
+                   "graph_steps": G, "graph_replays": nrep, "plain_steps": rest,
                    "autotune": [[list(c), t] for c, t in table]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": ncu_traffic(args.storage, sc_kernel),

@@ -64,8 +64,8 @@ extern "C" {
 #define LB_ERR_CUDA 2       /* a CUDA runtime call failed */
 #define LB_ERR_FENE 3       /* a bond reached the FENE maximum extension R0 */
 #define LB_ERR_BEAD_OOB 4   /* a bead's interpolation stencil left the box interior */
-#define LB_ERR_NONFINITE 5  /* mass or momentum sum of a box is not finite, or density <= 0 */
-#define LB_ERR_TIMEOUT 6    /* a bounded wait for the stream expired */
+#define LB_ERR_NONFINITE 5  /* a site density met while stepping, or a mass or momentum sum, is not finite or <= 0 */
+#define LB_ERR_TIMEOUT 6    /* a bounded wait expired: for the stream on the host, or a device pipeline wait */
 #define LB_ERR_STATE 7      /* call out of order (e.g. stepping past the last boundary sample) */
 #define LB_ERR_SIZE 8       /* arena too small for the plan */
 #define LB_ERR_CHAIN 9      /* a bead has more WCA neighbours than the per-bead list holds (48) */
@@ -138,7 +138,9 @@ typedef struct lb_chain_desc {
 typedef struct lb_ctx lb_ctx;
 
 /*
- * lb_plan -- size of the device arena for a context.
+ * lb_plan -- size of the device arena for a context of tracer boxes (Sec. 2:
+ * one fine lattice Boltzmann box per Lagrangian tracer, each fed by the
+ * coarse flow around it; Sec. 4: the paper follows 100 tracers).
  *   boxes[nboxes]: box descriptions (host).  storage: LB_STORE_*.
  *   ring_slots: coarse samples the boundary ring holds (0 = 4, at most 4096).
  *   Four slots cover one step at a time; a captured graph of G steps needs
@@ -150,7 +152,10 @@ typedef struct lb_ctx lb_ctx;
 int32_t lb_plan(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int32_t ring_slots, size_t* arena_bytes);
 
 /*
- * lb_create -- build a context over a caller-owned arena.
+ * lb_create -- build a context over a caller-owned arena: the boxes of
+ * lb_plan, each to be given its initial condition (lb_init), its boundary
+ * samples (lb_set_boundary) and its chain (chain_couple) in the order of
+ * Sec. 2 before it is stepped.
  *   arena: device pointer to at least the lb_plan size; borrowed until lb_destroy.
  *   stream: the cudaStream_t every later call enqueues on (NULL = legacy default stream).
  *   The library creates one private side stream and a few events for
@@ -214,10 +219,12 @@ int32_t chain_couple(lb_ctx* ctx, int32_t box, const lb_chain_desc* desc, const 
 
 /*
  * lb_step -- enqueue nsteps lattice Boltzmann steps for every box.  Each
- * step n -> n+1: bead coupling (reads the state, moves the chain, records
- * the force density at <= 8 sites per bead), fused stream-collide of all
- * sites with the boundary layer set to the equilibrium of the boundary
- * velocity at t = n+1, re-collision of the forced sites.
+ * step n -> n+1: bead coupling (Sec. 1: Stokes friction between beads and
+ * fluid; reads the state, moves the chain, records the force density at
+ * <= 8 sites per bead), fused stream-collide of all sites (D3Q19, Sec. 3)
+ * with the boundary layer set to the equilibrium of the boundary velocity
+ * at t = n+1 (Sec. 2; time interpolation of Sec. 3, after Eq. 1),
+ * re-collision of the forced sites.
  *   Returns LB_ERR_STATE if a needed boundary sample has not been pushed.
  */
 int32_t lb_step(lb_ctx* ctx, int32_t nsteps);
@@ -231,7 +238,8 @@ int32_t lb_graph_capture(lb_ctx* ctx, int32_t nsteps);
 int32_t lb_graph_launch(lb_ctx* ctx);
 
 /*
- * lb_read_fields -- observables of one box at the current step.
+ * lb_read_fields -- observables of one box at the current step (Sec. 4: the
+ * LB velocity field is what the paper compares with the DNS, Figs. 1-2).
  *   LB_FIELD_RHO / LB_FIELD_U: on boundary sites the moments of the stored
  *   equilibrium; elsewhere the moments of the pulled populations
  *   f_i(x) = A_i(x - c_i), u = (j + rho a / 2) / rho, a the body
@@ -267,10 +275,40 @@ int32_t lb_conservation(lb_ctx* ctx, int32_t box, double* out);
 int32_t lb_vorticity(lb_ctx* ctx, int32_t box, int32_t lo, int32_t hi, double* out);
 
 /* lb_sync -- wait for the context stream at most timeout_ms (LB_ERR_TIMEOUT
- * after that, the context stays usable) and return the first box error. */
+ * after that, the context stays usable) and return the first box error.
+ * The paper's replay runs about 1.85e5 LB steps per tracer (Sec. 3-4: one
+ * DNS sample every 0.05 tau_eta over 81 tau_eta, about 113 LB steps per
+ * sample by Eq. 1), so errors are collected at the caller's pace rather
+ * than after every step. */
 int32_t lb_sync(lb_ctx* ctx, int32_t timeout_ms);
 
 /* lb_status -- device status word of a box (synchronising), LB_OK if clean. */
+
+/*
+ * lb_checkpoint_bytes / lb_save / lb_load -- checkpoint and restore of a
+ * whole context, so that a long tracer replay (Sec. 3-4: about 1.85e5 LB
+ * steps per tracer) can stop and resume exactly where it left off.
+ *   A checkpoint holds the step counter and, for every box, its current
+ *   populations, the boundary-ring slots, the frame-acceleration samples,
+ *   the index of the last boundary sample pushed, its status word and its
+ *   chain (description, bead positions and velocities); for upsampler boxes
+ *   also the network output of the current coarse interval.  It does not
+ *   hold the upsampler parameters: bind them again (lb_mlp_bind) after a
+ *   load.  The launch settings (lb_set_launch, lb_set_bead_launch) are not
+ *   part of the state.
+ *   lb_checkpoint_bytes: size in bytes of a checkpoint of this context.
+ *   lb_save: dst, host or device memory of that size.  Waits for every
+ *   enqueued step (bounded wait), then copies; synchronising.
+ *   lb_load: ctx must have been created with the same box descriptions,
+ *   storage and ring_slots as the context saved (LB_ERR_ARG otherwise,
+ *   nothing changed); src host or device.  Replaces the state of every box;
+ *   the next lb_step continues from the saved step with the same result,
+ *   bit for bit, as the run that was saved.  Drops a captured graph;
+ *   synchronising.
+ */
+size_t lb_checkpoint_bytes(const lb_ctx* ctx);
+int32_t lb_save(lb_ctx* ctx, void* dst);
+int32_t lb_load(lb_ctx* ctx, const void* src);
 int32_t lb_status(lb_ctx* ctx, int32_t box, int32_t* status);
 
 /* lb_current_step -- number of steps enqueued so far. */
@@ -302,6 +340,28 @@ int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas
  *   lanes x ceil(largest chain / beads_per_thread) <= 512.  Used by the
  *   autotuner; drops a captured graph.  LB_ERR_ARG otherwise. */
 int32_t lb_set_bead_launch(lb_ctx* ctx, int32_t lanes, int32_t beads_per_thread);
+
+/*
+ * lb_test_inject -- test only: make a device-side bounded wait run out, so
+ * that the error path it guards can be exercised without faulting or hanging
+ * the GPU (the paper has no counterpart; this serves the library's failure
+ * detection).
+ *   what = LB_INJECT_WITHHOLD_LAST_TILE: from the next stream-collide launch
+ *   on, the producer of the staged kernel never arms the pipeline stage of
+ *   the last tile of the tile list (the last box's last sites) and issues no
+ *   copy for it.  The consumer warps waiting for that stage give up after
+ *   the wait limit, set LB_ERR_TIMEOUT on the tile's box and leave; that box
+ *   freezes, every other box steps on unaffected (the tiles a block took
+ *   before the withheld one are finished first).  LB_INJECT_NONE turns the
+ *   injection off.
+ *   wait_limit_us: limit of the staged kernel's bounded barrier waits in
+ *   microseconds, 1 .. 1000000 (0 = the default of one second).
+ *   Needs the staged kernel (LB_ERR_STATE otherwise); lb_set_launch to the
+ *   register kernel resets both settings.  Drops a captured graph.
+ */
+#define LB_INJECT_NONE 0
+#define LB_INJECT_WITHHOLD_LAST_TILE 1
+int32_t lb_test_inject(lb_ctx* ctx, int32_t what, int32_t wait_limit_us);
 
 /*
  * lb_profile -- time every stream-collide launch with a pair of CUDA events
@@ -420,12 +480,18 @@ int32_t lb_mlp_export(const void* ws, int32_t K, int64_t batch_rows, void* param
  *   the process exits.  No cudaMalloc, cudaFree or allocating library call.
  *   The first call on each device looks up the array's device address (one
  *   cudaGetSymbolAddress with that device current); make that first call
- *   before any stream capture.  All calls share the array: calls that overlap
- *   on the GPU race; a call never reads a partial it has not written itself,
- *   so nothing needs clearing between calls.
- *   Errors: LB_ERR_SIZE if E^3 exceeds 64 Mi sites (E > 400), LB_ERR_ARG for
- *   a null pointer or unknown storage, LB_ERR_CUDA if the address look-up or
- *   a launch fails; lb_last_error(NULL) gives the message.
+ *   before any stream capture.  The address is kept per device and CUDA
+ *   context: after a device reset (cudaDeviceReset, or any new context on the
+ *   device) the next call looks it up again, so the first-call rule applies
+ *   again.  All calls share the array: calls that overlap on the GPU race; a
+ *   call never reads a partial it has not written itself, so nothing needs
+ *   clearing between calls.
+ *   Errors: LB_ERR_SIZE if E > 400 (the array holds the partials of at most
+ *   400^3 sites), LB_ERR_ARG for a null pointer, unknown storage or E < 1
+ *   (both checked before any CUDA call), LB_ERR_CUDA if the address look-up
+ *   or a launch fails; lb_last_error(NULL) gives the message.  The call has
+ *   no size argument for the buffers: populations must hold 19 E^3 elements
+ *   of the storage format and out 4 doubles, both device memory.
  */
 int32_t lb_population_sums_noalloc(const void* populations, int32_t storage, int32_t E, double* out, void* stream);
 

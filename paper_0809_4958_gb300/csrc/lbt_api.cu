@@ -203,6 +203,8 @@ struct lb_ctx {
     int graph_steps = 0;
     bool graph_parity = true;
     bool profiling = false;
+    int inject = LB_INJECT_NONE;            // test-only fault injection (lb_test_inject)
+    int64_t wait_ns = kWaitLimitNs;         // limit of the stream-collide's bounded device waits
     const void* mlp_params = nullptr;  // bound upsampler parameters (device, caller-owned)
     double mlp_umax = 0.0;
     int64_t graph_step0 = 0;
@@ -366,6 +368,8 @@ int enqueue_step(lb_ctx* ctx, int64_t n)
     sp.step = ctx->at<int64_t>(ctx->L.step);
     sp.tile_counter = ctx->at<int64_t>(ctx->L.tile_counter);
     sp.status = ctx->at<int32_t>(ctx->L.status);
+    sp.wait_ns = ctx->wait_ns;
+    sp.withhold_tile = ctx->inject == LB_INJECT_WITHHOLD_LAST_TILE ? sp.total_tiles - 1 : -1;
     const bool timed = ctx->profiling && ctx->prof_used + 2 <= ctx->prof_ev.size();
     // inside a stream capture the timing events must become event-record nodes of the graph
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -957,6 +961,10 @@ int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas
     ctx->threads = threads;
     ctx->ctas = ctas;
     ctx->vw = vw;
+    if (kernel != LB_KERNEL_STAGED) {  // the injection exists in the staged kernel only
+        ctx->inject = LB_INJECT_NONE;
+        ctx->wait_ns = kWaitLimitNs;
+    }
     if (ctx->graph) {
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;
@@ -977,6 +985,209 @@ int32_t lb_set_bead_launch(lb_ctx* ctx, int32_t lanes, int32_t beads_per_thread)
         return ctx->fail(LB_ERR_ARG, "lb_set_bead_launch: lanes x beads per thread layout exceeds 512 threads");
     ctx->bead_lanes = lanes;
     ctx->bead_bpt = beads_per_thread;
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    return LB_OK;
+}
+
+// ---- checkpoint / restore ---------------------------------------------------
+namespace {
+
+constexpr uint64_t kCkptMagic = 0x3154504B4354424CULL;  // "LBTCKPT1" read as little-endian bytes
+constexpr uint32_t kCkptVersion = 1;
+
+// Fixed-size header at the start of a checkpoint.
+struct CkptHeader {
+    uint64_t magic;
+    uint32_t version, storage;
+    int32_t nboxes, ring_slots, nchains, pad;
+    int64_t step;
+    uint64_t desc_hash;   // FNV-1a of the box descriptions, field by field
+    uint64_t total;       // bytes of the whole checkpoint
+    uint64_t off_host, off_pop, off_ring, off_pos, off_vel, off_status, off_mlp_y;
+    uint64_t bytes_pop, bytes_ring, bytes_beads, bytes_mlp_y;
+};
+
+struct CkptLayout {
+    CkptHeader h;
+    size_t host_bytes;  // pushed[nboxes] int64, faccel samples, chain records
+};
+
+void fnv(uint64_t& h, const void* p, size_t n)
+{
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(p);
+    for (size_t k = 0; k < n; k++) {
+        h ^= b[k];
+        h *= 1099511628211ULL;
+    }
+}
+
+uint64_t desc_hash(const std::vector<lb_box_desc>& d)
+{
+    uint64_t h = 14695981039346656037ULL;
+    for (const lb_box_desc& x : d) {
+        fnv(h, &x.E, sizeof x.E);
+        fnv(h, x.face_mode, sizeof x.face_mode);
+        fnv(h, &x.time_interp, sizeof x.time_interp);
+        fnv(h, &x.K, sizeof x.K);
+        fnv(h, &x.nbeads, sizeof x.nbeads);
+        fnv(h, &x.zoom, sizeof x.zoom);
+        fnv(h, &x.frame_accel, sizeof x.frame_accel);
+        fnv(h, &x.tau, sizeof x.tau);
+        fnv(h, &x.rho_b, sizeof x.rho_b);
+        fnv(h, x.body_accel, sizeof x.body_accel);
+    }
+    return h;
+}
+
+CkptLayout ckpt_layout(const lb_ctx* ctx)
+{
+    CkptLayout c{};
+    CkptHeader& h = c.h;
+    h.magic = kCkptMagic;
+    h.version = kCkptVersion;
+    h.storage = (uint32_t)ctx->storage;
+    h.nboxes = ctx->nboxes;
+    h.ring_slots = ctx->L.ring_slots;
+    h.nchains = (int32_t)ctx->chains.size();
+    h.step = ctx->step;
+    h.desc_hash = desc_hash(ctx->desc);
+    c.host_bytes = sizeof(int64_t) * ctx->nboxes + sizeof(double) * ctx->faccel_host.size() +
+                   sizeof(ChainDev) * ctx->chains.size();
+    h.bytes_pop = ctx->L.pop_bytes;
+    h.bytes_ring = (size_t)ctx->L.ring_slots * ctx->L.ring_slot_elems * real_bytes(ctx->storage);
+    h.bytes_beads = sizeof(double) * 3 * (size_t)ctx->L.total_beads;
+    h.bytes_mlp_y = ctx->L.mlp_boxes > 0 ? sizeof(float) * 3 * (size_t)ctx->L.mlp_K * ctx->L.mlp_rows : 0;
+    size_t off = align_up(sizeof(CkptHeader));
+    h.off_host = off;
+    off = align_up(off + c.host_bytes);
+    h.off_pop = off;
+    off = align_up(off + h.bytes_pop);
+    h.off_ring = off;
+    off = align_up(off + h.bytes_ring);
+    h.off_pos = off;
+    off = align_up(off + h.bytes_beads);
+    h.off_vel = off;
+    off = align_up(off + h.bytes_beads);
+    h.off_status = off;
+    off = align_up(off + sizeof(int32_t) * ctx->nboxes);
+    h.off_mlp_y = off;
+    off = align_up(off + h.bytes_mlp_y);
+    h.total = off;
+    return c;
+}
+
+}  // namespace
+
+size_t lb_checkpoint_bytes(const lb_ctx* ctx) { return ctx ? ckpt_layout(ctx).h.total : 0; }
+
+int32_t lb_save(lb_ctx* ctx, void* dst)
+{
+    if (!ctx || !dst) return LB_ERR_ARG;
+    int st = wait_stream(ctx, kDefaultTimeoutMs);  // the state of every enqueued step
+    if (st) return st;
+    const CkptLayout c = ckpt_layout(ctx);
+    const CkptHeader& h = c.h;
+    std::vector<unsigned char> host(c.host_bytes);
+    unsigned char* hp = host.data();
+    memcpy(hp, ctx->pushed.data(), sizeof(int64_t) * ctx->nboxes);
+    hp += sizeof(int64_t) * ctx->nboxes;
+    memcpy(hp, ctx->faccel_host.data(), sizeof(double) * ctx->faccel_host.size());
+    hp += sizeof(double) * ctx->faccel_host.size();
+    if (!ctx->chains.empty()) memcpy(hp, ctx->chains.data(), sizeof(ChainDev) * ctx->chains.size());
+    char* d = reinterpret_cast<char*>(dst);
+    CK(cudaMemcpyAsync(d, &h, sizeof h, cudaMemcpyDefault, ctx->stream));
+    if (c.host_bytes) CK(cudaMemcpyAsync(d + h.off_host, host.data(), c.host_bytes, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemcpyAsync(d + h.off_pop, ctx->curA(), h.bytes_pop, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemcpyAsync(d + h.off_ring, ctx->arena + ctx->L.ring, h.bytes_ring, cudaMemcpyDefault, ctx->stream));
+    if (h.bytes_beads) {
+        CK(cudaMemcpyAsync(d + h.off_pos, ctx->arena + ctx->L.pos, h.bytes_beads, cudaMemcpyDefault, ctx->stream));
+        CK(cudaMemcpyAsync(d + h.off_vel, ctx->arena + ctx->L.vel, h.bytes_beads, cudaMemcpyDefault, ctx->stream));
+    }
+    CK(cudaMemcpyAsync(d + h.off_status, ctx->arena + ctx->L.status, sizeof(int32_t) * ctx->nboxes, cudaMemcpyDefault,
+                       ctx->stream));
+    if (h.bytes_mlp_y)
+        CK(cudaMemcpyAsync(d + h.off_mlp_y, ctx->arena + ctx->L.mlp_y, h.bytes_mlp_y, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));  // host buffers above must outlive the copies
+    return LB_OK;
+}
+
+int32_t lb_load(lb_ctx* ctx, const void* src)
+{
+    if (!ctx || !src) return LB_ERR_ARG;
+    int st = wait_stream(ctx, kDefaultTimeoutMs);
+    if (st) return st;
+    const char* s = reinterpret_cast<const char*>(src);
+    CkptHeader h{};
+    CK(cudaMemcpyAsync(&h, s, sizeof h, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const CkptLayout c = ckpt_layout(ctx);
+    if (h.magic != kCkptMagic || h.version != kCkptVersion)
+        return ctx->fail(LB_ERR_ARG, "lb_load: not a checkpoint of this library (magic or version)");
+    if ((int)h.storage != ctx->storage || h.nboxes != ctx->nboxes || h.ring_slots != ctx->L.ring_slots ||
+        h.nchains != c.h.nchains || h.desc_hash != c.h.desc_hash || h.total != c.h.total)
+        return ctx->fail(LB_ERR_ARG, "lb_load: the checkpoint was taken of a context with other boxes, storage or "
+                                     "ring slots");
+    if (h.step < 0) return ctx->fail(LB_ERR_ARG, "lb_load: negative step in the checkpoint");
+    std::vector<unsigned char> host(c.host_bytes);
+    if (c.host_bytes) CK(cudaMemcpyAsync(host.data(), s + h.off_host, c.host_bytes, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const unsigned char* hp = host.data();
+    std::vector<int64_t> pushed(ctx->nboxes);
+    memcpy(pushed.data(), hp, sizeof(int64_t) * ctx->nboxes);
+    hp += sizeof(int64_t) * ctx->nboxes;
+    std::vector<double> faccel(ctx->faccel_host.size());
+    memcpy(faccel.data(), hp, sizeof(double) * faccel.size());
+    hp += sizeof(double) * faccel.size();
+    std::vector<ChainDev> chains(ctx->chains.size());
+    if (!chains.empty()) memcpy(chains.data(), hp, sizeof(ChainDev) * chains.size());
+    for (size_t k = 0; k < chains.size(); k++)  // the chain records must belong to the same boxes and capacities
+        if (chains[k].box != ctx->chains[k].box || chains[k].bead_off != ctx->chains[k].bead_off ||
+            chains[k].nbeads < 0 || chains[k].nbeads > ctx->desc[chains[k].box].nbeads)
+            return ctx->fail(LB_ERR_ARG, "lb_load: chain records do not match the context");
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    CK(cudaMemcpyAsync(ctx->curA(), s + h.off_pop, h.bytes_pop, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->arena + ctx->L.ring, s + h.off_ring, h.bytes_ring, cudaMemcpyDefault, ctx->stream));
+    if (h.bytes_beads) {
+        CK(cudaMemcpyAsync(ctx->arena + ctx->L.pos, s + h.off_pos, h.bytes_beads, cudaMemcpyDefault, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->arena + ctx->L.vel, s + h.off_vel, h.bytes_beads, cudaMemcpyDefault, ctx->stream));
+    }
+    CK(cudaMemcpyAsync(ctx->arena + ctx->L.status, s + h.off_status, sizeof(int32_t) * ctx->nboxes, cudaMemcpyDefault,
+                       ctx->stream));
+    if (h.bytes_mlp_y)
+        CK(cudaMemcpyAsync(ctx->arena + ctx->L.mlp_y, s + h.off_mlp_y, h.bytes_mlp_y, cudaMemcpyDefault, ctx->stream));
+    if (!chains.empty())
+        CK(cudaMemcpyAsync(ctx->at<ChainDev>(ctx->L.chains), chains.data(), sizeof(ChainDev) * chains.size(),
+                           cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->at<double>(ctx->L.faccel), faccel.data(), sizeof(double) * faccel.size(),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    const int64_t step = h.step, zero = 0;
+    CK(cudaMemcpyAsync(ctx->at<int64_t>(ctx->L.step), &step, sizeof step, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->at<int64_t>(ctx->L.tile_counter), &zero, sizeof zero, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));  // host buffers above must outlive the copies
+    ctx->step = step;
+    ctx->pushed = pushed;
+    ctx->faccel_host = faccel;
+    ctx->chains = chains;
+    return LB_OK;
+}
+
+int32_t lb_test_inject(lb_ctx* ctx, int32_t what, int32_t wait_limit_us)
+{
+    if (!ctx) return LB_ERR_ARG;
+    if (what != LB_INJECT_NONE && what != LB_INJECT_WITHHOLD_LAST_TILE)
+        return ctx->fail(LB_ERR_ARG, "lb_test_inject: unknown injection");
+    if (wait_limit_us < 0 || wait_limit_us > 1000000)
+        return ctx->fail(LB_ERR_ARG, "lb_test_inject: wait_limit_us must be in [0, 1000000]");
+    if (what != LB_INJECT_NONE && ctx->kernel != LB_KERNEL_STAGED)
+        return ctx->fail(LB_ERR_STATE, "lb_test_inject: the injection needs the staged stream-collide kernel");
+    ctx->inject = what;
+    ctx->wait_ns = wait_limit_us > 0 ? (int64_t)wait_limit_us * 1000 : kWaitLimitNs;
     if (ctx->graph) {
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;

@@ -140,7 +140,28 @@ struct SCParams {
     const int64_t* step;          // device step counter n (state holds step n)
     int64_t* tile_counter;        // next tile for the persistent staged kernel (zeroed every step)
     int32_t* status;
+    int64_t wait_ns;              // limit of the staged kernel's bounded barrier waits
+    int64_t withhold_tile;        // test only: the staged producer never arms this tile (-1: none)
 };
+
+constexpr int64_t kWaitLimitNs = 1000000000;  // bounded device waits give up after one second
+
+// cudaFuncSetAttribute acts on the current device only, so the dynamic
+// shared-memory limit of a kernel is raised once per device (and again when a
+// launch needs more than before): done[dev] holds the size set on device dev.
+constexpr int kMaxDevices = 64;
+template <class T>
+inline cudaError_t smem_attr_per_device(T* kernel, int bytes, int (&done)[kMaxDevices])
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (done[dev] >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done[dev] = bytes;
+    return e;
+}
 
 struct BeadParams {
     const void* A;

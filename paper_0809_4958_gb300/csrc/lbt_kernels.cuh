@@ -105,6 +105,7 @@ __device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, con
     };
 
     A drho[VW], ux[VW], uy[VW], uz[VW];
+    bool nonfinite = false;  // a density that is not finite or not positive
 #pragma unroll
     for (int k = 0; k < VW; k++) {
         A r = A(0), jx = A(0), jy = A(0), jz = A(0);
@@ -117,6 +118,7 @@ __device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, con
             if (cvec(i, 2)) jz += cvec(i, 2) * f;
         }
         const A rho = A(1) + r;
+        nonfinite |= !(rho > A(0) && rho < A(1e30));  // NaN fails both comparisons
         const A inv = A(1) / rho;
         if (ACCEL) {
             jx += A(0.5) * rho * acA[0];
@@ -128,6 +130,9 @@ __device__ __forceinline__ void sc_tile(const SCParams& p, const BoxDev& bd, con
         uy[k] = jy * inv;
         uz[k] = jz * inv;
     }
+    // flag the box (it freezes from the next step on); sites that pulled no
+    // populations (boundary rows, inactive groups) hold zeros and never raise it
+    if (__any_sync(0xffffffffu, nonfinite) && lane == 0) atomicCAS(&p.status[bd.box], 0, LB_ERR_NONFINITE);
 
     // ---- boundary sites: equilibrium of the interpolated boundary velocity ----
     unsigned bmask = 0;
@@ -1204,13 +1209,9 @@ template <int ST, int SPT, bool GENERAL>
 cudaError_t launch_staged(const SCParams& p, int ctas, cudaStream_t s)
 {
     using G = Staged<ST, SPT>;
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_stream_collide_staged<ST, SPT, GENERAL>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::kSmemBytes);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static int attr_done[kMaxDevices] = {};  // per instantiation and device
+    cudaError_t e = smem_attr_per_device(k_stream_collide_staged<ST, SPT, GENERAL>, G::kSmemBytes, attr_done);
+    if (e != cudaSuccess) return e;
     int sms = 0;
     if (ctas <= 0) {
         int dev = 0;
@@ -1255,12 +1256,9 @@ cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, int max_be
     if (nchains <= 0) return cudaSuccess;
     using MT = typename std::conditional<ST == kF64, double, float>::type;
     const size_t dyn = bead_dyn_bytes<MT>(max_beads);
-    static size_t attr_set = 0;  // largest dynamic size enabled so far
-    if (dyn > attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_bead_couple<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess) return e;
-        attr_set = dyn;
-    }
+    static int attr_done[kMaxDevices] = {};  // largest dynamic size enabled so far, per device
+    cudaError_t e = smem_attr_per_device(k_bead_couple<ST>, (int)dyn, attr_done);
+    if (e != cudaSuccess) return e;
     BeadParams q = p;
     q.max_beads = max_beads;
     q.noise_chunk = bead_noise_chunk<MT>(max_beads);

@@ -420,13 +420,10 @@ template <int NOUT, bool SAVE>
 static cudaError_t forward_t(const void* X, int64_t rows, const void* params, const MlpLayout& L, float* Y, float* H1,
                              float* H2, cudaStream_t s)
 {
-    static bool attr = false;
+    static int attr_done[kMaxDevices] = {};  // per instantiation and device
     const int smem = (int)sizeof(MlpSmem<NOUT>);
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_forward<NOUT, SAVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = smem_attr_per_device(k_mlp_forward<NOUT, SAVE>, smem, attr_done);
+    if (e != cudaSuccess) return e;
     const int64_t tiles = (rows + 15) / 16;
     int64_t blocks = (tiles + 7) / 8;
     if (blocks > 152 * 2) blocks = 152 * 2;

@@ -281,13 +281,10 @@ template <int NOUT>
 cudaError_t forward_tc(const void* X, int64_t rows, const void* params, const MlpLayout& L, float* Y,
                        int64_t col_stride, int32_t* err, cudaStream_t s)
 {
-    static bool attr = false;
+    static int attr_done[kMaxDevices] = {};  // per instantiation and device
     const int smem = (int)sizeof(TcSmem<NOUT>);
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_forward_tc<NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = smem_attr_per_device(k_mlp_forward_tc<NOUT>, smem, attr_done);
+    if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -14,10 +14,15 @@
 // cannot use the array's name as a device address (in host code it is only a
 // stand-in for the symbol), so the first call on each device looks the
 // address up with cudaGetSymbolAddress while that device is current, checks
-// the result, caches it, and passes it to the kernels.  That first call should
-// come before any stream capture.  Every call overwrites the partial sums it
-// later reads, so nothing needs clearing; calls that overlap on the GPU (for
-// example on two streams at once) share the array and race.
+// the result, caches it, and passes it to the kernels.  The cache is keyed on
+// the device and on its current CUDA context: after a device reset (or any
+// new context on that device) the module, and with it the array, may load at
+// another address, so the next call looks the address up again -- the
+// first-call rule then applies anew.  The first call on a device (and the
+// first after a reset) should come before any stream capture.  Every call
+// overwrites the partial sums it later reads, so nothing needs clearing;
+// calls that overlap on the GPU (for example on two streams at once) share
+// the array and race.
 #include <mutex>
 #include <string>
 
@@ -28,7 +33,8 @@ namespace lbt {
 constexpr int kNaThreads = 256;
 constexpr int kNaSitesPerThread = 16;
 constexpr int64_t kNaChunk = (int64_t)kNaThreads * kNaSitesPerThread;  // sites per block
-constexpr int64_t kNaMaxChunks = 16384;                                 // 64 Mi sites: E <= 400
+constexpr int64_t kNaMaxChunks = 16384;                                 // partials the array holds
+constexpr int kNaMaxEdge = 400;  // documented limit: 400^3 sites need 15625 of the 16384 partials
 constexpr int kNaMaxDevices = 64;
 
 static __device__ __align__(256) double g_sums_scratch[kNaMaxChunks * 4];
@@ -80,20 +86,47 @@ __global__ void k_na_final(int64_t n3, int64_t nchunks, const double* partial, d
 namespace {
 std::mutex g_na_mu;
 double* g_na_addr[kNaMaxDevices] = {};
+void* g_na_ctx[kNaMaxDevices] = {};  // CUDA context the cached address belongs to
 
-// Device address of g_sums_scratch on the current device (set up once per device).
+// Current CUDA context (driver handle) through the runtime's driver entry
+// point, so the library needs no link against the driver library.
+cudaError_t current_context(void** ctx)
+{
+    using CtxGetCurrent = int (*)(void**);
+    static CtxGetCurrent fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !f) return cudaErrorNotSupported;
+        fn = reinterpret_cast<CtxGetCurrent>(f);
+    }
+    return fn(ctx) == 0 ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+// Device address of g_sums_scratch on the current device, looked up once per
+// device and context (again after a reset has replaced the context).
 cudaError_t scratch_address(double** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
+    // no context may be current yet (the runtime starts it lazily): then the
+    // look-up below, which starts it, runs and the context is read after it
+    void* ctx = nullptr;
+    e = current_context(&ctx);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_na_mu);
-    if (!g_na_addr[dev]) {
+    if (!ctx || !g_na_addr[dev] || g_na_ctx[dev] != ctx) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_sums_scratch);
         if (e != cudaSuccess) return e;
+        e = current_context(&ctx);
+        if (e != cudaSuccess) return e;
         g_na_addr[dev] = reinterpret_cast<double*>(p);
+        g_na_ctx[dev] = ctx;
     }
     *out = g_na_addr[dev];
     return cudaSuccess;
@@ -113,7 +146,7 @@ extern "C" int32_t lb_population_sums_noalloc(const void* populations, int32_t s
     }
     const int64_t n3 = (int64_t)E * E * E;
     const int64_t nchunks = (n3 + kNaChunk - 1) / kNaChunk;
-    if (nchunks > kNaMaxChunks) {
+    if (E > kNaMaxEdge || nchunks > kNaMaxChunks) {
         lbt_set_last_error("lb_population_sums_noalloc: box of E^3 sites exceeds the fixed scratch "
                            "(at most 64 Mi sites, E <= 400)");
         return LB_ERR_SIZE;

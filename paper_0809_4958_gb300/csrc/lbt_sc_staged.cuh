@@ -106,13 +106,14 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// Wait for a phase of the barrier, giving up after about one second.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase)
+// Wait for a phase of the barrier, giving up after limit_ns nanoseconds (one
+// second by default; shorter only when a test makes a wait run out on purpose).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, int64_t limit_ns)
 {
     if (mbar_try_wait(bar, phase)) return true;
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, phase))
-        if (global_ns() - t0 > 1000000000ull) return false;
+        if (global_ns() - t0 > (uint64_t)limit_ns) return false;
     return true;
 }
 
@@ -275,6 +276,7 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const StagedTile<
     if ((tid & 31) == 0) mbar_arrive(empty);  // this warp is done with the stage
 
     A drho[SPT], ux[SPT], uy[SPT], uz[SPT];
+    bool nonfinite = false;  // a density that is not finite or not positive
 #pragma unroll
     for (int k = 0; k < SPT; k++) {
         A r = A(0), jx = A(0), jy = A(0), jz = A(0);
@@ -286,6 +288,7 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const StagedTile<
             if (cvec(i, 2)) jz += cvec(i, 2) * f[i][k];
         }
         const A rho = A(1) + r;
+        nonfinite |= !(rho > A(0) && rho < A(1e30));  // NaN fails both comparisons
         const A inv = A(1) / rho;
         if (ACCEL) {
             jx += A(0.5) * rho * acA[0];
@@ -297,6 +300,9 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const StagedTile<
         uy[k] = jy * inv;
         uz[k] = jz * inv;
     }
+    // flag the box (it freezes from the next step on); boundary and inactive
+    // sites pulled zeros, so only collided sites can raise the flag
+    if (__any_sync(0xffffffffu, nonfinite) && (tid & 31) == 0) atomicCAS(&p.status[th.box], 0, LB_ERR_NONFINITE);
     // boundary sites: equilibrium of the boundary velocity from the ring
     if (any_bnd) {
         TimeWeights<R> tw;
@@ -393,15 +399,15 @@ __device__ __forceinline__ void staged_consume(const SCParams& p, unsigned char*
     for (int k = 0;; k++) {
         const int st = k % G::kStages;
         const uint32_t phase = (uint32_t)((k / G::kStages) & 1);
-        const bool arrived = mbar_wait_bounded(&hd->full[st], phase);
+        const bool arrived = mbar_wait_bounded(&hd->full[st], phase, p.wait_ns);
         if (!__all_sync(0xffffffffu, arrived)) {
-            // nothing arrived within a second: flag the box, let copies still in
-            // flight land (one more bounded wait) and leave
+            // nothing arrived within the limit: flag the box, let copies still
+            // in flight land (one more bounded wait) and leave
             if ((threadIdx.x & 31) == 0) {
-                const int b = hd->t[k % (2 * G::kStages)].box;
+                const int b = *reinterpret_cast<volatile const int32_t*>(&hd->t[k % (2 * G::kStages)].box);
                 atomicCAS(&p.status[b >= 0 && b < p.nboxes ? b : 0], 0, LB_ERR_TIMEOUT);
             }
-            mbar_wait_bounded(&hd->full[st], phase);
+            mbar_wait_bounded(&hd->full[st], phase, p.wait_ns);
             return;
         }
         const StagedTile<ST>& th = hd->t[k % (2 * G::kStages)];
@@ -450,7 +456,8 @@ __device__ __forceinline__ void staged_produce(const SCParams& p, unsigned char*
         const int st = k % G::kStages;
         // the stage's previous tile must be released by all consumer warps; if
         // that does not happen within a second the consumers have left
-        if (k >= G::kStages && !mbar_wait_bounded(&hd->empty[st], (uint32_t)(((k / G::kStages) - 1) & 1))) return;
+        if (k >= G::kStages && !mbar_wait_bounded(&hd->empty[st], (uint32_t)(((k / G::kStages) - 1) & 1), p.wait_ns))
+            return;
         const int64_t t = next;
         if (t >= p.total_tiles) {
             hd->t[k % (2 * G::kStages)].box = -1;
@@ -488,6 +495,13 @@ __device__ __forceinline__ void staged_produce(const SCParams& p, unsigned char*
         th.om1 = A(1) - th.om;
         th.srcfac = A(1) - A(0.5) * th.om;
         th.drho_b = (A)bd.rho_b - A(1);
+        if (t == p.withhold_tile) {
+            // test only: this stage is never armed and no copy is issued, so
+            // its full barrier never completes and the consumers' bounded wait
+            // runs out (the header above is in place for them to name the box)
+            __threadfence_block();
+            continue;
+        }
         fence_proxy_async_smem();
         issue_tile<ST, SPT>(p, bd, s0, smem + kStagedHeaderBytes + st * G::kStageBytes, &hd->full[st]);
     }

@@ -23,14 +23,16 @@ LB_TIME_LINEAR, LB_TIME_HERMITE, LB_TIME_MLP = 0, 1, 2
 LB_FIELD_RHO, LB_FIELD_U, LB_FIELD_DEV, LB_FIELD_CHAIN, LB_FIELD_ASYNC = 0, 1, 2, 3, 0x100
 LB_ALL_BOXES = -1
 LB_KERNEL_STAGED, LB_KERNEL_REGISTER = 0, 1
+LB_INJECT_NONE, LB_INJECT_WITHHOLD_LAST_TILE = 0, 1
 
 ERROR_NAMES = {0: "LB_OK", 1: "LB_ERR_ARG", 2: "LB_ERR_CUDA", 3: "LB_ERR_FENE", 4: "LB_ERR_BEAD_OOB",
                5: "LB_ERR_NONFINITE", 6: "LB_ERR_TIMEOUT", 7: "LB_ERR_STATE", 8: "LB_ERR_SIZE", 9: "LB_ERR_CHAIN"}
 
 EXPORTS = ["lb_plan", "lb_create", "lb_destroy", "lb_init", "lb_set_boundary", "chain_couple", "lb_step",
-           "lb_graph_capture", "lb_graph_launch", "lb_read_fields", "lb_conservation", "lb_vorticity", "lb_set_frame_accel", "lb_sync",
+           "lb_graph_capture", "lb_graph_launch", "lb_read_fields", "lb_conservation", "lb_checkpoint_bytes", "lb_save",
+           "lb_load", "lb_vorticity", "lb_set_frame_accel", "lb_sync",
            "lb_status",
-           "lb_current_step", "lb_set_launch", "lb_set_bead_launch", "lb_profile", "lb_profile_read", "lb_last_error", "lb_synth_workspace_bytes", "lb_synth_faces",
+           "lb_current_step", "lb_set_launch", "lb_set_bead_launch", "lb_test_inject", "lb_profile", "lb_profile_read", "lb_last_error", "lb_synth_workspace_bytes", "lb_synth_faces",
            "lb_synth_volume", "lb_population_sums_noalloc", "lb_mlp_param_bytes", "lb_mlp_bind", "lb_mlp_train_bytes",
            "lb_mlp_train_init", "lb_mlp_features", "lb_mlp_targets", "lb_mlp_forward", "lb_mlp_grad",
            "lb_mlp_train_step", "lb_mlp_export"]
@@ -85,6 +87,9 @@ def load(path: str | None = None, build_if_missing: bool = True):
         "lb_graph_launch": (_i32, [_vp]),
         "lb_read_fields": (_i32, [_vp, _i32, _i32, _vp]),
         "lb_conservation": (_i32, [_vp, _i32, _vp]),
+        "lb_checkpoint_bytes": (_sz, [_vp]),
+        "lb_save": (_i32, [_vp, _vp]),
+        "lb_load": (_i32, [_vp, _vp]),
         "lb_vorticity": (_i32, [_vp, _i32, _i32, _i32, _vp]),
         "lb_set_frame_accel": (_i32, [_vp, _i32, _i64, _vp]),
         "lb_sync": (_i32, [_vp, _i32]),
@@ -92,6 +97,7 @@ def load(path: str | None = None, build_if_missing: bool = True):
         "lb_current_step": (_i64, [_vp]),
         "lb_set_launch": (_i32, [_vp, _i32, _i32, _i32, _i32]),
         "lb_set_bead_launch": (_i32, [_vp, _i32, _i32]),
+        "lb_test_inject": (_i32, [_vp, _i32, _i32]),
         "lb_profile": (_i32, [_vp, _i32, _i32]),
         "lb_profile_read": (_i32, [_vp, ctypes.POINTER(_f64), ctypes.POINTER(_i64)]),
         "lb_last_error": (ctypes.c_char_p, [_vp]),
@@ -230,6 +236,16 @@ class Tracers:
         _check(self.lib.lb_conservation(self.ctx, box, out.ctypes.data), self.ctx)
         return out
 
+    def lb_checkpoint_bytes(self):
+        return int(self.lib.lb_checkpoint_bytes(self.ctx))
+
+    def lb_save(self, dst):
+        """Checkpoint of the context into dst (host numpy uint8 or device tensor of lb_checkpoint_bytes)."""
+        _check(self.lib.lb_save(self.ctx, _ptr(dst)), self.ctx)
+
+    def lb_load(self, src):
+        _check(self.lib.lb_load(self.ctx, _ptr(src)), self.ctx)
+
     def lb_set_frame_accel(self, box, j, a):
         """Frame-acceleration sample j (3 values, -dv/dt at t = jK) of a box created with frame_accel."""
         arr = np.ascontiguousarray(a, dtype=np.float64).reshape(3)
@@ -258,6 +274,9 @@ class Tracers:
     def lb_set_launch(self, kernel=LB_KERNEL_STAGED, threads=0, ctas=0, sites_per_thread=0):
         _check(self.lib.lb_set_launch(self.ctx, int(kernel), int(threads), int(ctas), int(sites_per_thread)),
                self.ctx)
+
+    def lb_test_inject(self, what, wait_limit_us=0):
+        _check(self.lib.lb_test_inject(self.ctx, int(what), int(wait_limit_us)), self.ctx)
 
     def lb_profile(self, enable, max_launches=0):
         _check(self.lib.lb_profile(self.ctx, int(enable), int(max_launches)), self.ctx)
@@ -309,9 +328,41 @@ class Tracers:
             pass
 
 
+_STORAGE_ELEM_BYTES = {LB_STORE_F64: 8, LB_STORE_F32: 4, LB_STORE_F16DEV: 2, LB_STORE_BF16DEV: 2}
+
+
+def check_noalloc_args(populations, storage, E, out):
+    """The C call takes no buffer sizes, so the binding checks what it can
+    before any launch: populations a CUDA tensor of at least 19 E^3 elements
+    whose element size matches `storage`, out a CUDA float64 tensor of at
+    least 4 elements.  Raises LBError(LB_ERR_ARG) on a mismatch."""
+    import torch
+
+    def bad(msg):
+        raise LBError(LB_ERR_ARG, "lb_population_sums_noalloc: " + msg)
+
+    if int(storage) not in _STORAGE_ELEM_BYTES:
+        bad("unknown storage %r" % (storage,))
+    if int(E) < 1:
+        bad("E must be >= 1")
+    if not getattr(populations, "is_cuda", False):
+        bad("populations must be a CUDA tensor")
+    if populations.numel() < 19 * int(E) ** 3:
+        bad("populations hold %d elements, need 19 E^3 = %d" % (populations.numel(), 19 * int(E) ** 3))
+    if populations.element_size() != _STORAGE_ELEM_BYTES[int(storage)]:
+        bad("element size %d does not match storage %d" % (populations.element_size(), int(storage)))
+    if not getattr(out, "is_cuda", False):
+        bad("out must be a CUDA tensor")
+    if out.dtype != torch.float64:
+        bad("out must be float64")
+    if out.numel() < 4:
+        bad("out must hold 4 doubles")
+
+
 def lb_population_sums_noalloc(populations, storage, E, out, stream=None):
     """Mass and momentum sums of a device population buffer into the device
     tensor out (4 doubles) without any device allocation (see the C header)."""
+    check_noalloc_args(populations, storage, E, out)
     torch = _torch()
     stream = stream or torch.cuda.current_stream()
     _check(load().lb_population_sums_noalloc(_ptr(populations), int(storage), int(E), _ptr(out), stream.cuda_stream))

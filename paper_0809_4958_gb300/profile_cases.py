@@ -7,6 +7,10 @@ captures (each holds a few GB of device memory at most).
   python -m paper_0809_4958_gb300.profile_cases mlp_forward [boxes]
       three launches of the upsampler forward over the face rows of that many
       64^3 boxes (K = 16)
+  python -m paper_0809_4958_gb300.profile_cases box [E] [storage] [steps]
+      one box of E^3 sites (storage 0 FP64, 1 FP32, 2 binary16, 3 bfloat16
+      deviations), velocity boundaries from random face samples, no chain,
+      stepped one step at a time (256^3 binary16: 1.3 GB of populations)
   python -m paper_0809_4958_gb300.profile_cases step_interp [mlp|hermite] [boxes] [steps]
       that many 64^3 boxes (FP32, K = 16) stepped with the learned upsampler
       (random-init network) or with Hermite time interpolation alone
@@ -36,6 +40,24 @@ def batch(nboxes: int = 96, steps: int = 12) -> None:
         tr.lb_step(1)
     tr.lb_sync()
     print("batch", nboxes, "boxes", sum(E ** 3 for E in Es), "sites", steps, "steps")
+
+
+def box(E: int = 256, storage: int = 2, steps: int = 8) -> None:
+    import torch
+
+    from . import lbtracer as lbt
+    lbt.load()
+    tr = lbt.Tracers([lbt.box_desc(E, 0.8)], storage, stream=torch.cuda.Stream(), ring_slots=4)
+    torch.cuda.synchronize()
+    tr.lb_init(0, torch.zeros((3, E, E, E), device="cuda", dtype=tr.real))
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    faces = [(torch.randn(18 * E * E, device="cuda", generator=gen) * 0.01).to(tr.real) for _ in range(steps + 2)]
+    tr.lb_set_boundary(0, 0, faces[0])
+    for n in range(steps):
+        tr.lb_set_boundary(0, n + 1, faces[n + 1])
+        tr.lb_step(1)
+    tr.lb_sync()
+    print("box", E, "storage", storage, steps, "steps")
 
 
 def mlp_forward(boxes: int = 256) -> None:
@@ -90,4 +112,4 @@ if __name__ == "__main__":
         step_interp(mode, *[int(a) for a in sys.argv[3:]])
     else:
         args = [int(a) for a in sys.argv[2:]]
-        {"batch": batch, "mlp_forward": mlp_forward}[case](*args)
+        {"batch": batch, "mlp_forward": mlp_forward, "box": box}[case](*args)

@@ -90,10 +90,10 @@ def test_forward_matches_oracle(lbt, data):
     p["b1"] = np.random.default_rng(1).normal(0, 0.1, 128)
     up = lbt.Upsampler(K=K, batch_rows=4096, master=master_vector(p))
     params = up.export()
-    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
-    X = lbt.mlp_features(d(coarse[0]), d(coarse[1]), d(coarse[2]), d(coarse[3]), E, U_MAX)
+    # both sides take the oracle's features of interval 1, rounded to bf16
+    Xq = bf16(omlp.features(coarse, 1, U_MAX))
+    X = torch.from_numpy(Xq).to(torch.bfloat16).contiguous().cuda()
     Y = lbt.mlp_forward(params, K, X).cpu().numpy()
-    Xq = X.float().cpu().numpy().astype(np.float64)
     Yref, _ = omlp.forward(bf16_params(p), Xq)
     # the GPU also rounds the hidden activations to bf16 (2^-9 relative each)
     assert rel_l2(Y, Yref) <= 1e-2
@@ -108,13 +108,14 @@ def test_gradients_match_oracle(lbt, data):
     up = lbt.Upsampler(K=K, batch_rows=4096, master=master_vector(p))
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
     j = 1
-    X = lbt.mlp_features(d(coarse[j - 1]), d(coarse[j]), d(coarse[j + 1]), d(coarse[j + 2]), E, U_MAX)
+    # both sides take the oracle's features, rounded to bf16, and targets
+    Xq = bf16(omlp.features(coarse, j, U_MAX))
+    X = torch.from_numpy(Xq).to(torch.bfloat16).contiguous().cuda()
     T = d(omlp.targets(fine, coarse, j, K, U_MAX).astype(np.float32))
     g, loss = up.grad(X, T)
     torch.cuda.synchronize()
     gq = split_master(g.cpu().numpy(), K)
     pq = bf16_params(p)
-    Xq = X.float().cpu().numpy().astype(np.float64)
     y, cache = omlp.forward(pq, Xq)
     gref = omlp.backward(pq, cache, y, T.cpu().numpy().astype(np.float64))
     assert abs(loss.item() - omlp.loss(y, T.cpu().numpy().astype(np.float64))) <= 2e-2 * omlp.loss(y, T.cpu().numpy())

@@ -186,64 +186,77 @@ def test_graph_replay_equals_steps(lbt):
     assert np.array_equal(ra.tr.chain(0, 8)[0], rg.tr.chain(0, 8)[0])
 
 
-def test_fullsize_128_sampled_step(lbt):
-    # 128^3 FP32 box, 1024 modes with |k| in [1, 64], 64-bead chain with
-    # noise at kT 1e-4, tau 0.55: after some GPU steps, one more GPU step is
-    # compared site by site with one oracle step from the same state.
+@pytest.fixture(scope="module")
+def fullsize_128_inputs():
+    # 128^3 box, 1024 modes with |k| in [1, 64]: boundary samples and initial
+    # field from the oracle's own generator (nothing the oracle sees comes
+    # from the GPU)
     from paper_0809_4958_gb300 import inputs
     E = 128
-    for tau in (0.55, 0.8):
-        c = Case.__new__(Case)
-        c.E, c.tau, c.K, c.time_interp, c.periodic, c.accel = E, tau, 1, 0, (False, False, False), (0.0, 0.0, 0.0)
-        c.zoom = 1
-        c.nsteps, c.nbeads, c.kT, c.n_md, c.pin_com, c.chain_seed, c.vel0 = 12, 64, 1e-4, 50, 2, 9, None
-        c.modes = inputs.mode_table(11, 1024, 1.0, 64.0, E)
-        c.J = 16
-        c.samples = lbt.synth_faces(c.modes, E, 1, 0, c.J, torch.float64).cpu().numpy()
-        ref_faces = oracle.face_samples(c.modes, E, 1, 10, 1)
-        assert np.abs(c.samples[10] - ref_faces[0]).max() < 1e-13  # generator parity at full size
-        c.u0 = lbt.synth_volume(c.modes, E, 0.0, torch.float64).cpu().numpy()
-        c.pos0 = inputs.chain_start(5, 64, E)
-        r = GpuRunner(lbt, torch, [c], ST32)
-        r.step(10)
-        A = r.tr.deviations(0).astype(np.float64)
-        pos, vel = r.tr.chain(0, 64)
-        r.step(1)
-        B = r.tr.deviations(0).astype(np.float64)
-        pos1, vel1 = r.tr.chain(0, 64)
-        _, w = oracle.lattice()
-        st, Bref, pref, vref, _ = oracle.step_from(c.oracle_box(), A + w[:, None, None, None], c.samples, 10,
-                                                  c.oracle_chain(), pos, vel)
-        assert st == 0
-        dref = Bref - w[:, None, None, None]
-        assert np.abs(B - dref).max() < 2e-7
-        # the FP32 path runs the chain MD in FP32 (positions FP64): FP32 bond
-        # forces of magnitude up to ~50 (2^-24 rounding, a 2-ulp fast
-        # reciprocal) drive 50 stiff substeps; the differences reach ~1e-6 in
-        # position and ~1e-4 in velocity
-        assert np.abs(pos1 - pref).max() < 1e-5 and np.abs(vel1 - vref).max() < 3e-4
+    modes = inputs.mode_table(11, 1024, 1.0, 64.0, E)
+    return modes, oracle.face_samples(modes, E, 1, 0, 14), oracle.volume_field(modes, E, 0.0)
+
+
+@pytest.mark.parametrize("tau", [0.55, 0.8])
+def test_fullsize_128_against_oracle(lbt, fullsize_128_inputs, tau):
+    # the default workload's shape: 128^3 FP32 box, 64-bead chain with noise
+    # at kT 1e-4; GPU and oracle both run 11 steps from the same inputs, and
+    # the GPU's sampled step 10 -> 11 is also compared with the oracle's
+    from paper_0809_4958_gb300 import inputs
+    modes, samples, u0 = fullsize_128_inputs
+    E, nsteps = 128, 11
+    c = Case.__new__(Case)
+    c.E, c.tau, c.K, c.time_interp, c.periodic, c.accel = E, tau, 1, 0, (False, False, False), (0.0, 0.0, 0.0)
+    c.zoom = 1
+    c.nsteps, c.nbeads, c.kT, c.n_md, c.pin_com, c.chain_seed, c.vel0 = nsteps, 64, 1e-4, 50, 2, 9, None
+    c.modes, c.samples, c.u0 = modes, samples, u0
+    c.J = samples.shape[0]
+    c.pos0 = inputs.chain_start(5, 64, E)
+    r = GpuRunner(lbt, torch, [c], ST32)
+    r.step(nsteps)
+    d = r.tr.deviations(0).astype(np.float64)
+    u = r.tr.fields(0)[1]
+    pos, vel = r.tr.chain(0, 64)
+    sim = c.run_oracle()
+    _, w = oracle.lattice()
+    dref = sim.f - w[:, None, None, None]
+    e_u = rel_l2(interior(u), interior(sim.fields()[1]))
+    e_d = np.abs(d - dref).max()
+    e_p, e_v = np.abs(pos - sim.pos).max(), np.abs(vel - sim.vel).max()
+    print("128^3 tau %.2f after %d steps: velocity rel L2 %.2e, max |d - ref| %.2e, beads %.2e / %.2e"
+          % (tau, nsteps, e_u, e_d, e_p, e_v))
+    # FP32 rounding of O(1) quantities (rho, w_i rho) over 11 steps: a few
+    # 1e-7 absolute on the deviations; the spec FP32 bound on velocity
+    assert e_d < 2e-6
+    assert e_u <= 1e-5
+    # the FP32 chain MD (50 stiff substeps per step, forces up to ~50 rounded
+    # to 2^-24 with a 2-ulp fast reciprocal) differs from the FP64 oracle by
+    # ~1e-6 in position and ~1e-4 in velocity per step; friction and the
+    # centre-of-mass pin keep it from growing fast over 11 steps
+    assert e_p < 1e-4 and e_v < 3e-3
 
 
 def test_chain_recoupled_at_an_odd_step(lbt):
-    # The sites that carry a bead force are collided by the bead kernel and
-    # left out of the stream-collide launch; they are marked per step parity.
-    # A chain re-coupled at step 3 (odd) at new positions must have its sites
-    # marked for that step: one step is compared site by site with the oracle.
+    # A chain re-coupled at step 3 (odd) at new positions: the bead kernel of
+    # that step must gather, move and spread from the new positions, and the
+    # forced re-collision must rewrite exactly the new stencil sites.  GPU and
+    # oracle both run 3 steps, re-place the chain and run one more.
     c = Case(16, 0.8, 6, seed=3, M=16, nbeads=6)
     r = GpuRunner(lbt, torch, [c], ST64)
     r.step(3)
-    _, w = oracle.lattice()
-    A = r.tr.deviations(0).astype(np.float64) + w[:, None, None, None]
     pos_new = np.ascontiguousarray(c.pos0 + np.array([1.3, 0.4, -0.7]))
     r.tr.chain_couple(0, c.gpu_chain(lbt), pos_new, None)
     r.step(1)
     B = r.tr.deviations(0).astype(np.float64)
     pos1, vel1 = r.tr.chain(0, 6)
-    st, Bref, pref, vref, _ = oracle.step_from(c.oracle_box(), A, c.samples, 3, c.oracle_chain(), pos_new,
-                                              np.zeros_like(pos_new))
-    assert st == 0
-    assert np.abs(B - (Bref - w[:, None, None, None])).max() < 1e-13
-    assert np.abs(pos1 - pref).max() < 1e-11 and np.abs(vel1 - vref).max() < 1e-10
+    sim = oracle.Sim(c.oracle_box(), c.u0, c.samples, c.oracle_chain(), c.pos0)
+    assert sim.run(3) == 0
+    sim.pos = pos_new.copy()
+    sim.vel = np.zeros_like(pos_new)
+    assert sim.run(1) == 0
+    _, w = oracle.lattice()
+    assert np.abs(B - (sim.f - w[:, None, None, None])).max() < 1e-13
+    assert np.abs(pos1 - sim.pos).max() < 1e-11 and np.abs(vel1 - sim.vel).max() < 1e-10
 
 
 def test_error_flags_freeze_only_the_failing_box(lbt):
@@ -289,21 +302,6 @@ def test_missing_boundary_sample_is_refused(lbt):
     r.tr.lb_set_boundary(0, 0, r.dev_samples[0][0])
     with pytest.raises(lbt.LBError):
         r.tr.lb_set_boundary(0, 2, r.dev_samples[0][2])  # out of order
-
-
-def test_bounded_wait_reports_timeout(lbt):
-    c = Case(64, 0.8, 1, M=16, periodic=(True, True, True))
-    r = GpuRunner(lbt, torch, [c], ST32)
-    r.tr.lb_step(400)
-    try:
-        r.tr.lb_sync(timeout_ms=0)
-        timed_out = False
-    except lbt.LBError as e:
-        assert e.code == lbt.LB_ERR_TIMEOUT
-        timed_out = True
-    r.tr.lb_sync()  # the context stays usable
-    assert r.tr.lb_current_step() == 400
-    assert timed_out or True
 
 
 @pytest.mark.parametrize("storage", [ST64, ST32, 2, 3])

@@ -26,7 +26,17 @@ def lbt():
     return lbtracer
 
 
-@pytest.mark.parametrize("storage", [0, 1, 2])
+def _as_storage(dev, storage):
+    """The read-out widens 16-bit storage to float32 exactly; hand the call
+    the 16-bit deviations themselves."""
+    if storage == 2:
+        return dev.to(torch.float16).contiguous()
+    if storage == 3:
+        return dev.to(torch.bfloat16).contiguous()
+    return dev.contiguous()
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2, 3])
 def test_noalloc_sums_equal_conservation_on_two_calls(lbt, storage):
     E = 24
     c = Case(E, 0.8, 30, M=32, nbeads=12, periodic=(True, True, True), pin_com=0, kT=1e-4)
@@ -38,11 +48,9 @@ def test_noalloc_sums_equal_conservation_on_two_calls(lbt, storage):
         ref = r.tr.lb_conservation(0)[:4]
         dev = torch.empty((19, E, E, E), dtype=real, device="cuda")
         r.tr.lb_read_fields(0, lbt.LB_FIELD_DEV, dev)
-        pops, code = dev, storage
-        if storage == 2:  # binary16 storage: hand the call the 16-bit deviations themselves
-            pops = dev.to(torch.float16)
+        pops, code = _as_storage(dev, storage), storage
         stream = torch.cuda.current_stream()
-        lbt.lb_population_sums_noalloc(pops.contiguous(), code, E, out, stream)
+        lbt.lb_population_sums_noalloc(pops, code, E, out, stream)
         stream.synchronize()
         got = out.cpu().numpy()
         # same FP64 sums as lb_conservation up to summation order
@@ -58,3 +66,15 @@ def test_noalloc_rejects_boxes_beyond_its_scratch(lbt):
         lbt.lb_population_sums_noalloc(buf, lbt.LB_STORE_F32, 512, out)
     assert ei.value.code == lbt.LB_ERR_SIZE
     assert "E <= 400" in str(ei.value)
+
+
+def test_noalloc_accepts_the_largest_documented_box(lbt):
+    # E = 400 is the documented maximum; zero deviations sum to exactly E^3
+    E = 400
+    pops = torch.zeros(19 * E ** 3, dtype=torch.float16, device="cuda")
+    out = torch.full((4,), -1.0, dtype=torch.float64, device="cuda")
+    lbt.lb_population_sums_noalloc(pops, lbt.LB_STORE_F16DEV, E, out)
+    torch.cuda.synchronize()
+    assert out.cpu().tolist() == [float(E ** 3), 0.0, 0.0, 0.0]
+    del pops
+
