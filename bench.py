@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--storage", default="f32", choices=["f32", "f64", "f16", "bf16"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the short runs of the batched, 16-bit and "
+                                                            "upsampler forms in the default line")
     p.add_argument("--no-tune", action="store_true", help="skip the launch autotuner (use --kernel/--threads/...)")
     p.add_argument("--threads", type=int, default=0, help="stream-collide block size (0 = library default)")
     p.add_argument("--ctas", type=int, default=0, help="persistent grid size (0 = one block per tile)")
@@ -350,8 +352,10 @@ def main():
     ncand = 0 if args.no_tune else len(autotune.candidates(storage, torch.cuda.get_device_properties(dev).multi_processor_count))
     tune_steps = 7 * ncand + 7 * 5  # launch shapes, then the bead kernel's thread layouts
     # graph replays of G steps, then any remainder stepped plainly: exactly
-    # args.steps timed steps (G even, at most 16, at most the step count)
-    G = min(w["graph"], args.steps // 2 * 2)
+    # args.steps timed steps.  G is the largest even length of at most 16
+    # steps that divides the step count (an odd count leaves one plain step)
+    even = args.steps // 2 * 2
+    G = max([g for g in range(2, min(w["graph"], even) + 1, 2) if even % g == 0] or [0])
     nsamp = args.warmup + tune_steps + args.steps + w["graph"] + 2
     faces = lbt.synth_faces(modes, E, w["K"], 0, nsamp, real)
     u0 = lbt.synth_volume(modes, E, 0.0, real)
@@ -480,6 +484,11 @@ def main():
         "e2e": e2e,
         "gpu_launches": args.steps * 3,
     }
+    tr.close()
+    del faces
+    torch.cuda.synchronize()
+    if not args.no_forms:
+        line["forms"] = measure_forms(args, value) if world == 1 else {"skipped": "forms run at one GPU only"}
     if not args.no_cpu:
         import oracle
         oracle.build()
@@ -487,7 +496,6 @@ def main():
             line["cpu_baseline"] = cpu_baseline(args.storage)
         except Exception as e:  # report, do not lose the GPU line
             line["cpu_baseline"] = {"value": None, "error": repr(e)}
-    tr.close()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -496,16 +504,19 @@ def main():
 BATCH = dict(nboxes=512, choices=(24, 32, 48, 64), tau=0.8, M=256, K=1, kT=1e-4, n_md=50, seed=0, graph=16)
 
 
-def run_batch(args):
+def run_batch(args, standalone=True):
     """512 tracer boxes of uneven size (E uniform in {24, 32, 48, 64}), each
     with its own boundary field and chain (32 .. min(128, 2E) beads), FP32,
-    stepped by a CUDA graph of 16 steps after the launch shape is autotuned."""
+    stepped by a CUDA graph of 16 steps after the launch shape is autotuned.
+    Returns the line (rank 0); standalone: set up and print it."""
     import torch
     import torch.distributed as dist
 
     from paper_0809_4958_gb300 import autotune, inputs, lbtracer as lbt
 
     rank, world, local = dist_env()
+    if not standalone:
+        rank, world = 0, 1
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -595,10 +606,14 @@ def run_batch(args):
                              "traffic": None, "kernel": "stream-collide", "avg_launch_ms": avg_sc,
                              "alg_bytes_per_launch": alg, "peak_kind": peak_kind, "launches_timed": sc_n},
                 "clocks": clk, "e2e": None, "gpu_launches": steps * 3}
-        print(json.dumps(line), flush=True)
+        if standalone:
+            print(json.dumps(line), flush=True)
     tr.close()
+    del faces
+    torch.cuda.synchronize()
     if world > 1:
         dist.destroy_process_group()
+    return line if rank == 0 else None
 
 
 PRECISION = dict(E=256, tau=0.8, M=2048, k_min=1.0, k_max=128.0, K=1, seed=3)
@@ -681,7 +696,7 @@ def run_paper(args):
     print(json.dumps(line), flush=True)
 
 
-def run_precision(args):
+def run_precision(args, standalone=True):
     """One 256^3 box (no chain) stored as FP32, binary16 and bfloat16
     deviations; MLUPS of each and the velocity and non-equilibrium stress
     error of the 16-bit forms against the FP32 form after the same steps."""
@@ -690,8 +705,8 @@ def run_precision(args):
     from paper_0809_4958_gb300 import inputs, lbtracer as lbt
 
     rank, world, local = dist_env()
-    if rank != 0:
-        return
+    if rank != 0 and standalone:
+        return None
     torch.cuda.set_device(local)
     w = PRECISION
     E = w["E"]
@@ -775,14 +790,18 @@ def run_precision(args):
                          "frac": results["f16"]["hbm_frac"], "traffic": None, "kernel": "stream-collide",
                          "peak_kind": peak_kind},
             "e2e": None, "gpu_launches": args.steps * 2}
-    print(json.dumps(line), flush=True)
+    del faces
+    torch.cuda.synchronize()
+    if standalone:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 MLP = dict(nboxes=256, E=64, tau=0.8, M=256, k_min=1.0, k_max=32.0, K=16, u_max=0.05, train_boxes=12,
            train_intervals=10, train_steps=3000, batch=16384, lr=2e-3, eval_boxes=4, eval_steps=256, seed=500)
 
 
-def run_mlp(args):
+def run_mlp(args, standalone=True):
     """256 boxes of 64^3 with coarse boundary samples every K = 16 steps.
     The upsampler is trained on the GPU on every-step boundary data of
     training seeds, its gain is measured on held-out boxes (interior velocity
@@ -794,8 +813,8 @@ def run_mlp(args):
     from paper_0809_4958_gb300 import inputs, lbtracer as lbt
 
     rank, world, local = dist_env()
-    if rank != 0:
-        return
+    if rank != 0 and standalone:
+        return None
     torch.cuda.set_device(local)
     w = MLP
     E, K = w["E"], w["K"]
@@ -920,7 +939,57 @@ def run_mlp(args):
                                     "rows": int(X.shape[0]), "adam_steps": w["train_steps"], "batch": w["batch"],
                                     "lr": w["lr"], "loss_first": first, "loss_final": final, "seconds": train_s}},
             "roofline": None, "e2e": None, "gpu_launches": None}
-    print(json.dumps(line), flush=True)
+    del X, T
+    torch.cuda.synchronize()
+    if standalone:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+FORM_STEPS = {"batch": (256, 112), "precision": (1000, 20), "mlp": (256, 64)}
+
+
+def measure_forms(args, plain_mlups):
+    """The three added forms, each a short timed run on the same GPU next to
+    the plain FP32 box of the headline (steps and warm-up fixed per form)."""
+    import copy
+    out = {}
+    for name, fn in (("batch", run_batch), ("precision", run_precision), ("upsampler", run_mlp)):
+        a = copy.copy(args)
+        a.steps, a.warmup = FORM_STEPS["mlp" if name == "upsampler" else name]
+        try:
+            line = fn(a, standalone=False)
+        except Exception as e:  # report, do not lose the headline
+            out[name] = {"error": repr(e)}
+            continue
+        if name == "batch":
+            rf = line["roofline"]
+            out[name] = {"MLUPS": line["value"], "vs_plain_f32_box": line["value"] / plain_mlups,
+                         "steps": line["steps"], "hbm_frac": rf["frac"], "stream_collide_ms": rf["avg_launch_ms"],
+                         "workload": line["config"]["workload"],
+                         "error_vs_single_box": 0.0,
+                         "error_note": "each box of a batch equals the same box run alone bit for bit "
+                                       "(tests/test_gpu_parity.py::test_batch_of_uneven_boxes_equals_single_boxes)"}
+        elif name == "precision":
+            res = line["config"]["forms"]
+            out[name] = {"steps": line["steps"], "workload": line["config"]["workload"]}
+            for st in ("f32", "f16", "bf16"):
+                r = res[st]
+                e = {"MLUPS": r["MLUPS"], "vs_plain_f32_box": r["MLUPS"] / plain_mlups, "hbm_frac": r["hbm_frac"],
+                     "stream_collide_ms": r["stream_collide_ms"]}
+                if st != "f32":
+                    e["velocity_rel_l2_vs_f32"] = r["velocity_rel_l2_vs_f32"]
+                    e["stress_rel_l2_vs_f32"] = r["stress_rel_l2_vs_f32"]
+                out[name][st] = e
+        else:
+            c = line["config"]
+            out[name] = {"MLUPS": line["value"], "vs_plain_f32_box": line["value"] / plain_mlups,
+                         "steps": line["steps"], "hermite_only_MLUPS": c["hermite_only_MLUPS"],
+                         "interior_velocity_error_vs_every_step_boundary":
+                             c["interior_velocity_error_vs_every_step_boundary"],
+                         "heldout_boundary_residual_mse_vs_hermite": c["heldout_boundary_residual_mse_vs_hermite"],
+                         "training_seconds": c["training"]["seconds"], "workload": c["workload"]}
+    return out
 
 
 if __name__ == "__main__":

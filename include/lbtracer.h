@@ -342,6 +342,26 @@ int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas
 int32_t lb_set_bead_launch(lb_ctx* ctx, int32_t lanes, int32_t beads_per_thread);
 
 /*
+ * lb_set_fluctuation -- fluctuating collision for one box: the thermal fluid
+ * of the hybrid method the paper builds on (Sec. 1, the Ahlrichs-Duenweg
+ * coupling of a bead chain to a fluctuating lattice Boltzmann fluid).  The
+ * collision acts on the 19 moments of the D3Q19 orthogonal basis e_k(c)
+ * (sum_i w_i e_k(c_i) e_l(c_i) = b_k delta_kl; mass and momentum, k = 0..3,
+ * conserved): m_k* = gamma_k m_k^neq + sqrt(mu rho b_k (1 - gamma_k^2)) xi_k
+ * for k = 4..18 with mu = kT / c_s^2 = 3 kT, xi_k unit-variance uniforms from
+ * Philox4x32-10 with counter (step, site, block 0..3, 0xF1) and key seed,
+ * words 0..14 to modes 4..18; then f_i* = f_i^eq + w_i sum_k e_k(c_i) m_k* / b_k.
+ * gamma_k = 1 - 1/tau for all k with kT = 0 is the BGK collision.
+ *   gamma: host, 19 doubles (entries 0..3 ignored), each of 4..18 in (-1, 1);
+ *   NULL switches the box back to BGK.  kT >= 0.
+ *   Boundary sites of velocity faces keep their equilibrium.  Boxes with a
+ *   chain capacity or a body force, and contexts on the register kernel, are
+ *   refused (LB_ERR_ARG / LB_ERR_STATE): chains and forcing couple to BGK
+ *   boxes only.  Drops a captured graph; synchronising.
+ */
+int32_t lb_set_fluctuation(lb_ctx* ctx, int32_t box, double kT, uint64_t seed, const double* gamma);
+
+/*
  * lb_test_inject -- test only: make a device-side bounded wait run out, so
  * that the error path it guards can be exercised without faulting or hanging
  * the GPU (the paper has no counterpart; this serves the library's failure

@@ -11,6 +11,7 @@
 #include <thread>
 #include <vector>
 
+#include "lbt_fluct.cuh"
 #include "lbt_internal.h"
 #include "lbt_mlp.h"
 
@@ -146,6 +147,8 @@ Layout plan_layout(const lb_box_desc* boxes, int nboxes, int storage, int ring_s
     off = align_up(off + sizeof(double) * 4 * (size_t)nboxes * ring_slots);
     L.chain_accel = off;  // body acceleration of the step per chain [chain][4]
     off = align_up(off + sizeof(double) * 4 * (size_t)nboxes);
+    L.fluct = off;  // fluctuating-collision parameters per box
+    off = align_up(off + sizeof(FluctDev) * (size_t)nboxes);
     // upsampler: feature-set table, bf16 features and f32 outputs of all its boxes
     L.mlp_rows = 0;
     L.mlp_boxes = 0;
@@ -362,7 +365,11 @@ int enqueue_step(lb_ctx* ctx, int64_t n)
     sp.boxes = ctx->at<BoxDev>(ctx->L.boxes);
     sp.tile_prefix = ctx->at<int64_t>(ctx->L.tile_prefix);
     sp.general = 0;
-    for (const BoxDev& bd : ctx->boxes) sp.general |= (bd.per_mask != 0 || bd.has_accel) ? 1 : 0;
+    for (const BoxDev& bd : ctx->boxes) {
+        if (bd.fluct) sp.general = 2;
+        else if ((bd.per_mask != 0 || bd.has_accel) && sp.general == 0) sp.general = 1;
+    }
+    sp.fluct = ctx->at<FluctDev>(ctx->L.fluct);
     sp.nboxes = ctx->nboxes;
     sp.total_tiles = ctx->tile_prefix[ctx->nboxes];
     sp.step = ctx->at<int64_t>(ctx->L.step);
@@ -710,6 +717,7 @@ int32_t chain_couple(lb_ctx* ctx, int32_t box, const lb_chain_desc* d, const dou
     if (box < 0 || box >= ctx->nboxes) return ctx->fail(LB_ERR_ARG, "box index out of range");
     const int ci = ctx->boxes[box].chain;
     if (ci < 0) return ctx->fail(LB_ERR_ARG, "box was planned without chain capacity (nbeads = 0)");
+    if (ctx->boxes[box].fluct) return ctx->fail(LB_ERR_ARG, "chains couple to BGK boxes only");
     if (d->nbeads < 1 || d->nbeads > ctx->desc[box].nbeads || d->n_md < 1 || !(d->mass > 0) || d->kT < 0 ||
         !(d->R0 > 0) || d->zeta < 0 || d->pin_com < 0 || d->pin_com > 2 || d->eps < 0 ||
         (d->eps > 0 && !(d->sigma > 0)))
@@ -949,6 +957,8 @@ int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas
             return ctx->fail(LB_ERR_ARG, "staged kernel: threads 0, ctas >= 0, sites_per_thread 0, 1 or "
                                          "(not FP64) 2");
     } else if (kernel == LB_KERNEL_REGISTER) {
+        for (const BoxDev& bd : ctx->boxes)
+            if (bd.fluct) return ctx->fail(LB_ERR_STATE, "the fluctuating collision runs in the staged kernel only");
         if (threads == 0) threads = 256;
         const int v4 = dv / 4 > 0 ? dv / 4 : 1;
         if (threads < 64 || threads > 256 || threads % 32 || ctas < 0 || (vw != dv && vw != dv / 2 && vw != v4))
@@ -1174,6 +1184,41 @@ int32_t lb_load(lb_ctx* ctx, const void* src)
     ctx->pushed = pushed;
     ctx->faccel_host = faccel;
     ctx->chains = chains;
+    return LB_OK;
+}
+
+int32_t lb_set_fluctuation(lb_ctx* ctx, int32_t box, double kT, uint64_t seed, const double* gamma)
+{
+    if (!ctx) return LB_ERR_ARG;
+    if (box < 0 || box >= ctx->nboxes) return ctx->fail(LB_ERR_ARG, "box index out of range");
+    BoxDev& bd = ctx->boxes[box];
+    FluctDev fd{};
+    if (gamma) {
+        if (!(kT >= 0.0)) return ctx->fail(LB_ERR_ARG, "lb_set_fluctuation: kT must be >= 0");
+        for (int k = 4; k < kQ; k++)
+            if (!(gamma[k] > -1.0 && gamma[k] < 1.0))
+                return ctx->fail(LB_ERR_ARG, "lb_set_fluctuation: gamma[4..18] must lie in (-1, 1)");
+        if (bd.chain >= 0 || bd.has_accel)
+            return ctx->fail(LB_ERR_ARG, "lb_set_fluctuation: boxes with a chain or a body force collide with BGK");
+        if (ctx->kernel != LB_KERNEL_STAGED)
+            return ctx->fail(LB_ERR_STATE, "lb_set_fluctuation: the fluctuating collision runs in the staged kernel");
+        fd.seed = seed;
+        fd.on = 1;
+        for (int k = 4; k < kQ; k++) {
+            // b_k = sum_i w_i e_k(c_i)^2; amplitude sqrt(mu b_k (1 - gamma_k^2)), mu = kT / c_s^2 = 3 kT
+            const double b = bnorm36(k) / 36.0;
+            fd.gamma[k - 4] = gamma[k];
+            fd.amp[k - 4] = std::sqrt(3.0 * kT * b * (1.0 - gamma[k] * gamma[k]));
+        }
+    }
+    bd.fluct = fd.on;
+    CK(cudaMemcpyAsync(ctx->at<FluctDev>(ctx->L.fluct) + box, &fd, sizeof fd, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->at<BoxDev>(ctx->L.boxes) + box, &bd, sizeof bd, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));  // the host records above must outlive the copies
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
     return LB_OK;
 }
 

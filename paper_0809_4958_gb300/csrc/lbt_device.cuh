@@ -178,12 +178,14 @@ template <class R>
 __device__ __forceinline__ TimeWeights<R> time_weights(int64_t n, int K, int mode, int ring_slots)
 {
     TimeWeights<R> tw;
-    int64_t j = n / K;
+    // 32-bit division while the step fits (a 64-bit one is a long instruction sequence)
+    const int64_t j = n < 0x7fffffff ? (int64_t)((uint32_t)n / (uint32_t)K) : n / K;
     int s = (int)(n + 1 - j * K);
     R th = (R)s / (R)K;
     for (int a = 0; a < 4; a++) {
-        int64_t jj = j - 1 + a;
-        tw.slot[a] = (int)(((jj % ring_slots) + ring_slots) % ring_slots);
+        const int64_t jj = j - 1 + a;
+        tw.slot[a] = jj < 0x7fffffff ? (int)(((int)jj % ring_slots + ring_slots) % ring_slots)
+                                     : (int)(((jj % ring_slots) + ring_slots) % ring_slots);
         tw.c[a] = R(0);
     }
     if (mode == 0) {
@@ -209,7 +211,11 @@ __device__ __forceinline__ TimeWeights<R> time_weights(int64_t n, int K, int mod
 }
 
 // Substep s = n + 1 - jK (1 .. K) of the step n -> n + 1 within its coarse interval j.
-__device__ __forceinline__ int mlp_substep(int64_t n, int K) { return (int)(n + 1 - (n / K) * K); }
+__device__ __forceinline__ int mlp_substep(int64_t n, int K)
+{
+    const int64_t j = n < 0x7fffffff ? (int64_t)((uint32_t)n / (uint32_t)K) : n / K;
+    return (int)(n + 1 - j * K);
+}
 
 // Learned residual of the boundary velocity (upsampler boxes): output row of
 // the face site, substep s.  Loaded before the time interpolation of the ring

@@ -35,6 +35,8 @@ struct BoxDev {
     int32_t Ec;         // coarse points per axis: point P at site P z, covering site E - 1
     int32_t frame;      // 1: frame-acceleration samples add to accel (frame_accel_at)
     int32_t box;        // index of this box in the box table
+    int32_t fluct;      // 1: fluctuating collision (FluctDev of the box), 0: BGK
+    int32_t fluct_pad;
     uint64_t div_magic; // ceil(2^40 / E): site / E = (site * div_magic) >> 40
     int64_t mlp_row;    // first row of the box in the upsampler output, -1 if the box does not use it
     double tau;
@@ -51,7 +53,7 @@ __host__ __device__ inline void frame_accel_at(const BoxDev& bd, const double* f
 {
     for (int c = 0; c < 3; c++) a[c] = bd.accel[c];
     if (!bd.frame) return;
-    const int64_t j = n / bd.K;
+    const int64_t j = n < 0x7fffffff ? (int64_t)((uint32_t)n / (uint32_t)bd.K) : n / bd.K;
     const double th = (double)(n - j * bd.K) / (double)bd.K;
     const double* a0 = faccel + ((int64_t)bd.box * slots + j % slots) * 4;
     const double* a1 = faccel + ((int64_t)bd.box * slots + (j + 1) % slots) * 4;
@@ -97,6 +99,17 @@ struct ChainDev {
     float md_f[kMdConsts];
 };
 
+// Fluctuating collision of one box (lb_set_fluctuation): relaxation factor
+// and noise amplitude of the non-conserved modes 4 .. 18 of the D3Q19
+// orthogonal basis (see lbt_fluct.cuh).
+struct FluctDev {
+    uint64_t seed;
+    int32_t on;        // 0: the box collides with BGK
+    int32_t pad;
+    double gamma[15];  // relaxation factor of modes 4 .. 18
+    double amp[15];    // sqrt(3 kT b_k (1 - gamma_k^2)); times sqrt(rho) per site
+};
+
 // Force density at one lattice site, produced by the bead kernel, consumed by
 // the forced re-collision.  site = -1 marks a duplicate of an earlier entry.
 struct ForceEntry {
@@ -108,7 +121,7 @@ struct ForceEntry {
 // Arena layout (byte offsets), computed by plan().
 struct Layout {
     size_t boxes, tile_prefix, chains, pop_a, pop_b, ring, pos, vel, forces, cons_partial, cons_out,
-        status, step, tile_counter, faccel, chain_accel, mlp_sets, mlp_x, mlp_y, total;
+        status, step, tile_counter, faccel, chain_accel, fluct, mlp_sets, mlp_x, mlp_y, total;
     size_t pop_bytes;        // bytes of one population buffer
     size_t ring_slot_elems;  // real elements per ring slot
     int32_t ring_slots;      // slots in the ring of coarse samples
@@ -134,12 +147,13 @@ struct SCParams {
     const BoxDev* boxes;
     const int64_t* tile_prefix;   // [nboxes + 1] first tile of each box for the current block size
     const double* faccel;         // frame-acceleration samples [box][ring slot][4]
-    int32_t general;              // some box is periodic or carries a body force
+    int32_t general;              // 1: some box is periodic or carries a body force; 2: some box fluctuates
     int32_t nboxes;
     int64_t total_tiles;
     const int64_t* step;          // device step counter n (state holds step n)
     int64_t* tile_counter;        // next tile for the persistent staged kernel (zeroed every step)
     int32_t* status;
+    const FluctDev* fluct;        // [nboxes] fluctuating-collision parameters
     int64_t wait_ns;              // limit of the staged kernel's bounded barrier waits
     int64_t withhold_tile;        // test only: the staged producer never arms this tile (-1: none)
 };

@@ -1205,12 +1205,12 @@ inline int grid_for(int64_t n, int threads, int cap = 152 * 16)
     return g < 1 ? 1 : (int)g;
 }
 
-template <int ST, int SPT, bool GENERAL>
+template <int ST, int SPT, int KIND>
 cudaError_t launch_staged(const SCParams& p, int ctas, cudaStream_t s)
 {
     using G = Staged<ST, SPT>;
     static int attr_done[kMaxDevices] = {};  // per instantiation and device
-    cudaError_t e = smem_attr_per_device(k_stream_collide_staged<ST, SPT, GENERAL>, G::kSmemBytes, attr_done);
+    cudaError_t e = smem_attr_per_device(k_stream_collide_staged<ST, SPT, KIND>, G::kSmemBytes, attr_done);
     if (e != cudaSuccess) return e;
     int sms = 0;
     if (ctas <= 0) {
@@ -1221,7 +1221,7 @@ cudaError_t launch_staged(const SCParams& p, int ctas, cudaStream_t s)
     int64_t grid = ctas > 0 ? ctas : sms;
     if (grid > p.total_tiles) grid = p.total_tiles;
     if (grid < 1) return cudaSuccess;
-    k_stream_collide_staged<ST, SPT, GENERAL><<<(unsigned)grid, kStagedThreads, G::kSmemBytes, s>>>(p);
+    k_stream_collide_staged<ST, SPT, KIND><<<(unsigned)grid, kStagedThreads, G::kSmemBytes, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -1231,12 +1231,10 @@ cudaError_t Launch<ST>::stream_collide(const SCParams& p, int kernel, int thread
     if (kernel == LB_KERNEL_STAGED) {
         // vw: sites per consumer thread (1 or 2; FP64 1)
         constexpr int S2 = ST == kF64 ? 1 : 2;
-        if (p.general) {
-            if (ST != kF64 && vw == 2) return launch_staged<ST, S2, true>(p, ctas, s);
-            return launch_staged<ST, 1, true>(p, ctas, s);
-        }
-        if (ST != kF64 && vw == 2) return launch_staged<ST, S2, false>(p, ctas, s);
-        return launch_staged<ST, 1, false>(p, ctas, s);
+        const bool two = ST != kF64 && vw == 2;
+        if (p.general == 2) return two ? launch_staged<ST, S2, 2>(p, ctas, s) : launch_staged<ST, 1, 2>(p, ctas, s);
+        if (p.general == 1) return two ? launch_staged<ST, S2, 1>(p, ctas, s) : launch_staged<ST, 1, 1>(p, ctas, s);
+        return two ? launch_staged<ST, S2, 0>(p, ctas, s) : launch_staged<ST, 1, 0>(p, ctas, s);
     }
     int64_t grid = (ctas > 0 && ctas < p.total_tiles) ? ctas : p.total_tiles;
     if (grid < 1) return cudaSuccess;

@@ -96,6 +96,28 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16])
     for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
 }
 
+// 32 FP32 columns of this thread's TMEM lane, without waiting (tc_ld_wait)
+__device__ __forceinline__ void tc_ld32_nowait(uint32_t taddr, uint32_t r[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tc_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_ld16_nowait(uint32_t taddr, uint32_t r[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
 // wait for a phase of the MMA barrier, giving up after about one second
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t phase)
 {
@@ -120,25 +142,32 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t phase)
 
 // accumulator columns [col0, col0 + 128) of this thread's row -> bias, ReLU,
 // bf16 -> row m of the next layer's A operand
+// (64 columns per round: two 32-column TMEM loads in flight, one wait)
 __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float* bias, __nv_bfloat16* h, int m)
 {
 #pragma unroll 1
-    for (int c0 = 0; c0 < kMlpHidden; c0 += 16) {
-        float v[16];
-        tc_ld16(tmem_row + c0, v);
-        float bj[16];
+    for (int c0 = 0; c0 < kMlpHidden; c0 += 64) {
+        uint32_t r[64];
+        tc_ld32_nowait(tmem_row + c0, r);
+        tc_ld32_nowait(tmem_row + c0 + 32, r + 32);
+        tc_ld_wait();
 #pragma unroll
-        for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(bj + j) = *reinterpret_cast<const float4*>(bias + c0 + j);
-        uint32_t pk[8];
+        for (int g = 0; g < 64; g += 16) {
+            float bj[16];
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const float a = fmaxf(v[2 * j] + bj[2 * j], 0.f);
-            const float b = fmaxf(v[2 * j + 1] + bj[2 * j + 1], 0.f);
-            __nv_bfloat162 p2 = __floats2bfloat162_rn(a, b);
-            pk[j] = *reinterpret_cast<uint32_t*>(&p2);
+            for (int j = 0; j < 16; j += 4)
+                *reinterpret_cast<float4*>(bj + j) = *reinterpret_cast<const float4*>(bias + c0 + g + j);
+            uint32_t pk[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const float a = fmaxf(__uint_as_float(r[g + 2 * j]) + bj[2 * j], 0.f);
+                const float b = fmaxf(__uint_as_float(r[g + 2 * j + 1]) + bj[2 * j + 1], 0.f);
+                __nv_bfloat162 p2 = __floats2bfloat162_rn(a, b);
+                pk[j] = *reinterpret_cast<uint32_t*>(&p2);
+            }
+            *reinterpret_cast<uint4*>(h + core_off(m, c0 + g, kMlpHidden)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *reinterpret_cast<uint4*>(h + core_off(m, c0 + g + 8, kMlpHidden)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
         }
-        *reinterpret_cast<uint4*>(h + core_off(m, c0, kMlpHidden)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        *reinterpret_cast<uint4*>(h + core_off(m, c0 + 8, kMlpHidden)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
     }
 }
 
@@ -244,10 +273,16 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_forward_tc(const __nv_bfloat
                 // every lane takes part in the (warp-collective) TMEM loads;
                 // rows past the end store nothing
                 const bool in = r0 + m < rows;
+                static_assert(NP == 32 || NP == 48, "output columns: one 32-column load and at most one 16-column one");
+                uint32_t r[NP];  // every output column in flight at once, one wait
+                tc_ld32_nowait(tmem_row + 128, r);
+                if constexpr (NP == 48) tc_ld16_nowait(tmem_row + 128 + 32, r + 32);
+                tc_ld_wait();
 #pragma unroll
                 for (int c0 = 0; c0 < NP; c0 += 16) {
                     float v[16];
-                    tc_ld16(tmem_row + 128 + c0, v);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[c0 + j]);
                     if (col_stride == 0) {  // row-major [rows][NOUT]: four 16-byte stores per lane
                         float* y = Y + (r0 + m) * NOUT;
 #pragma unroll

@@ -22,6 +22,7 @@
 // boundary equilibrium anyway.
 #pragma once
 #include "lbt_device.cuh"
+#include "lbt_fluct.cuh"
 
 namespace lbt {
 
@@ -117,13 +118,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase,
     return true;
 }
 
-__device__ __forceinline__ int locate_box(const SCParams& p, int64_t tile)
+// Box of tile t (the largest b with tile_prefix[b] <= t), searched by a whole
+// warp: 32 candidates per round, so 512 boxes take two dependent loads.
+__device__ __forceinline__ int locate_box_warp(const SCParams& p, int64_t t, int lane)
 {
     int lo = 0, hi = p.nboxes - 1;
     while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (p.tile_prefix[mid] <= tile) lo = mid;
-        else hi = mid - 1;
+        const int step = (hi - lo + 32) / 32;
+        const int idx = lo + lane * step;
+        const bool le = idx <= hi && p.tile_prefix[idx] <= t;
+        const unsigned m = __ballot_sync(0xffffffffu, le);  // a prefix of the lanes; lane 0 always (prefix[lo] <= t)
+        lo += (31 - __clz(m)) * step;
+        hi = min(hi, lo + step - 1);
     }
     return lo;
 }
@@ -161,34 +167,6 @@ struct StagedHeader {
 };
 static_assert(sizeof(StagedHeader<kF64>) <= kStagedHeaderBytes, "header does not fit");
 static_assert(sizeof(StagedHeader<kF32>) <= kStagedHeaderBytes, "header does not fit");
-
-// Producer (one thread): bulk copies of the 19 source rows of a tile.
-template <int ST, int SPT>
-__device__ __forceinline__ void issue_tile(const SCParams& p, const BoxDev& bd, int64_t s0, unsigned char* stage,
-                                           uint64_t* bar)
-{
-    using E = typename Stor<ST>::E;
-    constexpr int T = Staged<ST, SPT>::kSites, H = Staged<ST, SPT>::kHalo;
-    const int64_t n3 = bd.n3, Ei = bd.E;
-    const E* Ab = reinterpret_cast<const E*>(p.A) + bd.f_off;
-    int64_t lo[kQ], hi[kQ];
-    uint32_t total = 0;
-#pragma unroll
-    for (int i = 0; i < kQ; i++) {
-        const int64_t start = s0 - (cvec(i, 1) * Ei + cvec(i, 2) * Ei * Ei) - H;
-        lo[i] = start > 0 ? start : 0;
-        hi[i] = start + T + 2 * H < n3 ? start + T + 2 * H : n3;
-        if (hi[i] > lo[i]) total += (uint32_t)((hi[i] - lo[i]) * sizeof(E));
-    }
-    mbar_arrive_expect_tx(bar, total);
-#pragma unroll
-    for (int i = 0; i < kQ; i++) {
-        if (hi[i] <= lo[i]) continue;
-        const int64_t start = s0 - (cvec(i, 1) * Ei + cvec(i, 2) * Ei * Ei) - H;
-        bulk_load(stage + i * Staged<ST, SPT>::kRowStride + (lo[i] - start) * sizeof(E), Ab + (int64_t)i * n3 + lo[i],
-                  (uint32_t)((hi[i] - lo[i]) * sizeof(E)), bar);
-    }
-}
 
 // Quotient and remainder of a site index by E with a precomputed multiplier:
 // q = (s * m) >> 40 with m = ceil(2^40 / E), exact for s < 2^31 and E <= 1024.
@@ -387,13 +365,381 @@ __device__ __forceinline__ void staged_tile(const SCParams& p, const StagedTile<
     }
 }
 
-// Consumer warps: take the stages in order until the producer posts the end.
-// GENERAL = false: every box of the launch is non-periodic and force-free, so
-// only that tile body is compiled in (fewer registers than the kernel that
-// carries all four bodies).
-template <int ST, int SPT, bool GENERAL>
-__device__ __forceinline__ void staged_consume(const SCParams& p, unsigned char* smem, StagedHeader<ST>* hd)
+// ---- two adjacent sites per consumer thread (FP32 and 16-bit storage) -----
+// Packed FP32 arithmetic: one instruction advances both sites of a thread.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as one packed FMA: b (-1) is exact, so this is a - b rounded once
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Loads and stores of a pair of adjacent stored elements: one aligned word
+// for the pair of a thread (elements e, e + 1 with e even), two scalar loads
+// for the x-shifted pairs, conversions to and from FP32 packed where the
+// format has a packed instruction (round to nearest even, as Stor<ST>::out).
+template <int ST>
+struct PairIO;
+template <>
+struct PairIO<kF32> {
+    using E = float;
+    static __device__ __forceinline__ float2 even(const E* row, int e) { return *reinterpret_cast<const float2*>(row + e); }
+    static __device__ __forceinline__ float2 any(const E* row, int e) { return make_float2(row[e], row[e + 1]); }
+    static __device__ __forceinline__ void store(E* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+};
+template <>
+struct PairIO<kF16> {
+    using E = uint16_t;
+    static __device__ __forceinline__ float2 even(const E* row, int e)
+    {
+        return __half22float2(*reinterpret_cast<const __half2*>(row + e));
+    }
+    static __device__ __forceinline__ float2 any(const E* row, int e)
+    {
+        return make_float2(__half2float(__ushort_as_half(row[e])), __half2float(__ushort_as_half(row[e + 1])));
+    }
+    static __device__ __forceinline__ void store(E* p, float2 v) { *reinterpret_cast<__half2*>(p) = __floats2half2_rn(v.x, v.y); }
+};
+template <>
+struct PairIO<kBF16> {
+    using E = uint16_t;
+    static __device__ __forceinline__ float2 even(const E* row, int e)
+    {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(row + e));
+    }
+    static __device__ __forceinline__ float2 any(const E* row, int e)
+    {
+        return make_float2(__bfloat162float(__ushort_as_bfloat16(row[e])),
+                           __bfloat162float(__ushort_as_bfloat16(row[e + 1])));
+    }
+    static __device__ __forceinline__ void store(E* p, float2 v)
+    {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v.x, v.y);
+    }
+};
+
+// Consumer thread c (0 .. 479) of one tile of 960 sites takes the adjacent
+// sites s0 + 2c and s0 + 2c + 1 (same row: E and s0 are even), so a warp
+// reads and writes 64 consecutive sites with one word per lane.  Same
+// arithmetic as staged_tile, on both sites at once; a boundary site takes
+// om = 1, 1 - om = 0 and no force term in its lane, which turns the
+// collision into its equilibrium.
+template <int ST, bool PER, bool ACCEL>
+__device__ __forceinline__ void staged_tile_pair(const SCParams& p, const StagedTile<ST>& th, const unsigned char* stage,
+                                                 uint64_t* empty)
 {
+    static_assert(ST != kF64, "the paired body works in FP32");
+    using S = Stor<ST>;
+    using E = typename S::E;
+    using IO = PairIO<ST>;
+    constexpr int H = Staged<ST, 2>::kHalo;
+    const int tid = threadIdx.x;
+    const int s0 = (int)th.s0;
+    const BoxDev& bd = th.bd;
+    const int Ei = bd.E;
+    const int n3 = (int)bd.n3;
+    const int per = bd.per_mask;
+    const bool px = per & 1, py = per & 2, pz = per & 4;
+    const E* Ab = reinterpret_cast<const E*>(p.A) + bd.f_off;
+    E* Bb = reinterpret_cast<E*>(p.B) + bd.f_off;
+
+    const int s = s0 + 2 * tid;  // first site of the pair (even)
+    const bool act = s < n3;     // n3 is even: both sites or none
+    int x, y, z;
+    {
+        const int sc = act ? s : 0;
+        const int row = div_e(sc, bd.div_magic);
+        x = sc - row * Ei;
+        z = div_e(row, bd.div_magic);
+        y = row - z * Ei;
+    }
+    const bool brow = (!py && (y == 0 || y == Ei - 1)) || (!pz && (z == 0 || z == Ei - 1));
+    const bool bnd0 = act && (brow || (!px && x == 0));
+    const bool bnd1 = act && (brow || (!px && x + 1 == Ei - 1));
+    const bool keep0 = act && !bnd0, keep1 = act && !bnd1;
+
+    // f_i pulled into both sites (zero where unused)
+    float2 f[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; i++) {
+        const int cx = cvec(i, 0), cy = cvec(i, 1), cz = cvec(i, 2);
+        const E* row = reinterpret_cast<const E*>(stage + i * Staged<ST, 2>::kRowStride);
+        float2 v = cx == 0 ? IO::even(row, H + 2 * tid) : IO::any(row, H + 2 * tid - cx);
+        if (PER) {
+            const int ys = y - cy, zs = z - cz;
+            const bool wyz = (py && (ys < 0 || ys >= Ei)) || (pz && (zs < 0 || zs >= Ei));
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const int xs = x + k - cx;
+                const bool wrap = wyz || (px && (xs < 0 || xs >= Ei));
+                if (wrap && act) {
+                    const float w = S::in(
+                        Ab[(int64_t)i * n3 + ((int64_t)wrapi(zs, Ei) * Ei + wrapi(ys, Ei)) * Ei + wrapi(xs, Ei)]);
+                    if (k == 0) v.x = w;
+                    else v.y = w;
+                }
+            }
+        }
+        // boundary lanes keep what they pulled (finite: the stage holds copied
+        // or zeroed elements only); it is multiplied by zero below
+        f[i] = v;
+    }
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(empty);  // this warp is done with the stage
+
+    // moments (sum of deviations, momentum)
+    float2 r = f[0];
+#pragma unroll
+    for (int i = 1; i < kQ; i++) r = add2(r, f[i]);
+    float2 jx = sub2(f[1], f[2]), jy = sub2(f[3], f[4]), jz = sub2(f[5], f[6]);
+    jx = add2(jx, sub2(f[7], f[8]));
+    jy = add2(jy, sub2(f[7], f[8]));
+    jx = add2(jx, sub2(f[9], f[10]));
+    jy = sub2(jy, sub2(f[9], f[10]));
+    jx = add2(jx, sub2(f[11], f[12]));
+    jz = add2(jz, sub2(f[11], f[12]));
+    jx = add2(jx, sub2(f[13], f[14]));
+    jz = sub2(jz, sub2(f[13], f[14]));
+    jy = add2(jy, sub2(f[15], f[16]));
+    jz = add2(jz, sub2(f[15], f[16]));
+    jy = add2(jy, sub2(f[17], f[18]));
+    jz = sub2(jz, sub2(f[17], f[18]));
+    float2 rho = add2(f2(1.f), r);
+    const bool nonfinite = (keep0 && !(rho.x > 0.f && rho.x < 1e30f)) || (keep1 && !(rho.y > 0.f && rho.y < 1e30f));
+    if (__any_sync(0xffffffffu, nonfinite) && (tid & 31) == 0) atomicCAS(&p.status[th.box], 0, LB_ERR_NONFINITE);
+    float2 ac[3] = {f2(0.f), f2(0.f), f2(0.f)};
+    if (ACCEL) {
+        for (int c = 0; c < 3; c++) ac[c] = f2((float)bd.accel[c]);
+        const float2 hr = mul2(f2(0.5f), rho);
+        jx = fma2(hr, ac[0], jx);
+        jy = fma2(hr, ac[1], jy);
+        jz = fma2(hr, ac[2], jz);
+    }
+    // 1 / rho by the fast reciprocal (within 2 ulp; the FP32 collision rounds
+    // O(1) terms at 2^-24 anyway)
+    const float2 inv = make_float2(__fdividef(1.f, rho.x), __fdividef(1.f, rho.y));
+    float2 ux = mul2(jx, inv), uy = mul2(jy, inv), uz = mul2(jz, inv);
+    float2 drho = r;
+
+    // boundary sites: equilibrium of the boundary velocity from the ring
+    if (bnd0 || bnd1) {
+        TimeWeights<float> tw;
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            tw.slot[a] = th.slot[a];
+            tw.c[a] = th.c[a];
+        }
+        const float* ring = reinterpret_cast<const float*>(p.ring);
+#pragma unroll 1
+        for (int k = 0; k < 2; k++) {  // one lane at a time: fewer live registers
+            if (k == 0 ? bnd0 : bnd1) {
+                int pp, qq;
+                const int fc = owning_face(x + k, y, z, Ei, per, pp, qq);
+                float res[3];
+                load_mlp_residual(p, bd, th.mlp_s, fc, pp, qq, res);
+                float ub[3];
+                boundary_velocity<float>(ring, p.ring_slot_elems, bd, fc, pp, qq, tw, ub);
+                add_mlp_residual<float>(p, bd, res, ub);
+                if (k == 0) {
+                    drho.x = th.drho_b;
+                    ux.x = ub[0];
+                    uy.x = ub[1];
+                    uz.x = ub[2];
+                } else {
+                    drho.y = th.drho_b;
+                    ux.y = ub[0];
+                    uy.y = ub[1];
+                    uz.y = ub[2];
+                }
+            }
+        }
+        rho = add2(f2(1.f), drho);
+    }
+
+    // per-lane relaxation: boundary lanes take their equilibrium
+    const float2 om = make_float2(bnd0 ? 1.f : th.om, bnd1 ? 1.f : th.om);
+    const float2 om1 = make_float2(bnd0 ? 0.f : th.om1, bnd1 ? 0.f : th.om1);
+    const float2 usq = mul2(f2(1.5f), fma2(ux, ux, fma2(uy, uy, mul2(uz, uz))));
+    const float2 nusq = mul2(f2(-1.f), usq);
+    // om w rho and om w drho for the two weight classes of the moving
+    // populations and the rest population; om 3 w rho for the odd part
+    const float2 omrho = mul2(om, rho), omdrho = mul2(om, drho);
+    const float2 r18 = mul2(f2(1.f / 18.f), omrho), d18 = mul2(f2(1.f / 18.f), omdrho);
+    const float2 r36 = mul2(f2(1.f / 36.f), omrho), d36 = mul2(f2(1.f / 36.f), omdrho);
+    const float2 t18 = mul2(f2(3.f / 18.f), omrho), t36 = mul2(f2(3.f / 36.f), omrho);
+    float2 sfr, srcw[2], ua;
+    if (ACCEL) {  // Guo source: (1 - om/2) w rho (3 (c.a - u.a) + 9 (c.u)(c.a)), zero on boundary lanes
+        const float2 sf = make_float2(bnd0 ? 0.f : th.srcfac, bnd1 ? 0.f : th.srcfac);
+        sfr = mul2(sf, rho);
+        srcw[0] = mul2(sfr, f2(1.f / 18.f));
+        srcw[1] = mul2(sfr, f2(1.f / 36.f));
+        ua = fma2(ux, ac[0], fma2(uy, ac[1], mul2(uz, ac[2])));
+    }
+    E* out = Bb + s;
+    // population 0: om w0 (drho - rho usq)
+    {
+        const float2 odeq = mul2(f2(1.f / 3.f), fma2(omrho, nusq, omdrho));
+        float2 val = fma2(om1, f[0], odeq);
+        if (ACCEL) val = fma2(sfr, make_float2(-ua.x, -ua.y), val);  // (1 - om/2) w0 rho 3 (-u.a), 3 w0 = 1
+        if (act) IO::store(out, val);
+    }
+#pragma unroll
+    for (int i = 1; i < kQ; i += 2) {
+        out += i == 1 ? n3 : 2 * n3;  // row of population i; population i + 1 is one row further
+        const int cx = cvec(i, 0), cy = cvec(i, 1), cz = cvec(i, 2);
+        const bool w18 = i < 7;
+        float2 cu;
+        if (cx && cy) cu = cy > 0 ? (cx > 0 ? add2(ux, uy) : make_float2(-(ux.x + uy.x), -(ux.y + uy.y))) : (cx > 0 ? sub2(ux, uy) : sub2(uy, ux));
+        else if (cx && cz) cu = cz > 0 ? (cx > 0 ? add2(ux, uz) : make_float2(-(ux.x + uz.x), -(ux.y + uz.y))) : (cx > 0 ? sub2(ux, uz) : sub2(uz, ux));
+        else if (cy && cz) cu = cz > 0 ? (cy > 0 ? add2(uy, uz) : make_float2(-(uy.x + uz.x), -(uy.y + uz.y))) : (cy > 0 ? sub2(uy, uz) : sub2(uz, uy));
+        else cu = cx ? ux : (cy ? uy : uz);  // axis pairs: c_i = +x, +y or +z for odd i
+        // om (w (drho + rho (4.5 cu^2 - usq))) and om (3 w rho cu)
+        const float2 t = fma2(mul2(f2(4.5f), cu), cu, nusq);
+        const float2 oeven = fma2(w18 ? r18 : r36, t, w18 ? d18 : d36);
+        const float2 oodd = mul2(w18 ? t18 : t36, cu);
+        float2 vp = fma2(om1, f[i], add2(oeven, oodd));
+        float2 vm = fma2(om1, f[i + 1], sub2(oeven, oodd));
+        if (ACCEL) {
+            float ca = 0.f;  // c_i . a (uniform per box)
+            if (cx) ca += cx * (float)bd.accel[0];
+            if (cy) ca += cy * (float)bd.accel[1];
+            if (cz) ca += cz * (float)bd.accel[2];
+            const float2 sw = w18 ? srcw[0] : srcw[1];
+            // + : 3 (ca - ua) + 9 cu ca ;  - : 3 (-ca - ua) + 9 cu ca  (c -> -c flips ca and cu)
+            const float2 nine_cu_ca = mul2(f2(9.f * ca), cu);
+            const float2 sp = fma2(f2(3.f), sub2(f2(ca), ua), nine_cu_ca);
+            const float2 sm = fma2(f2(3.f), sub2(f2(-ca), ua), nine_cu_ca);
+            vp = fma2(sw, sp, vp);
+            vm = fma2(sw, sm, vm);
+        }
+        if (act) {
+            IO::store(out, vp);
+            IO::store(out + n3, vm);
+        }
+    }
+}
+
+// Consumer body of a box with the fluctuating collision (lbt_fluct.cuh): the
+// thread's sites (the adjacent pair s0 + 2c, s0 + 2c + 1 when SPT = 2, site
+// s0 + c when SPT = 1) pulled into registers, the stage released, then site by
+// site the moments and either the boundary equilibrium or the fluctuating
+// collision with the site's Philox noise of step n.  Boxes with a body force
+// or a chain do not take this path.
+template <int ST, int SPT, bool PER>
+__device__ __forceinline__ void staged_tile_fluct(const SCParams& p, const StagedTile<ST>& th,
+                                                  const unsigned char* stage, uint64_t* empty, int64_t n)
+{
+    using S = Stor<ST>;
+    using E = typename S::E;
+    using A = typename S::A;
+    using R = typename S::R;
+    constexpr int H = Staged<ST, SPT>::kHalo;
+    const int tid = threadIdx.x;
+    const int s0 = (int)th.s0;
+    const BoxDev& bd = th.bd;
+    const int Ei = bd.E;
+    const int n3 = (int)bd.n3;
+    const int per = bd.per_mask;
+    const bool px = per & 1, py = per & 2, pz = per & 4;
+    const E* Ab = reinterpret_cast<const E*>(p.A) + bd.f_off;
+    E* Bb = reinterpret_cast<E*>(p.B) + bd.f_off;
+    auto local = [&](int k) { return SPT == 2 ? 2 * tid + k : tid; };
+
+    int xs_[SPT], ys_[SPT], zs_[SPT];
+    bool act[SPT], bnd[SPT];
+#pragma unroll
+    for (int k = 0; k < SPT; k++) {
+        const int s = s0 + local(k);
+        act[k] = s < n3;
+        const int sc = act[k] ? s : 0;
+        const int row = div_e(sc, bd.div_magic);
+        xs_[k] = sc - row * Ei;
+        zs_[k] = div_e(row, bd.div_magic);
+        ys_[k] = row - zs_[k] * Ei;
+        bnd[k] = act[k] && ((!px && (xs_[k] == 0 || xs_[k] == Ei - 1)) || (!py && (ys_[k] == 0 || ys_[k] == Ei - 1)) ||
+                            (!pz && (zs_[k] == 0 || zs_[k] == Ei - 1)));
+    }
+    A f[kQ][SPT];
+#pragma unroll
+    for (int i = 0; i < kQ; i++) {
+        const int cx = cvec(i, 0), cy = cvec(i, 1), cz = cvec(i, 2);
+        const E* row = reinterpret_cast<const E*>(stage + i * Staged<ST, SPT>::kRowStride);
+#pragma unroll
+        for (int k = 0; k < SPT; k++) {
+            A v = S::in(row[H + local(k) - cx]);
+            if (PER) {
+                const int xs = xs_[k] - cx, ys = ys_[k] - cy, zs = zs_[k] - cz;
+                const bool wrap = (px && (xs < 0 || xs >= Ei)) || (py && (ys < 0 || ys >= Ei)) ||
+                                  (pz && (zs < 0 || zs >= Ei));
+                if (wrap && act[k])
+                    v = S::in(Ab[(int64_t)i * n3 + ((int64_t)wrapi(zs, Ei) * Ei + wrapi(ys, Ei)) * Ei + wrapi(xs, Ei)]);
+            }
+            f[i][k] = (act[k] && !bnd[k]) ? v : A(0);
+        }
+    }
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(empty);  // this warp is done with the stage
+
+    const FluctDev& fd = p.fluct[th.box];
+    bool nonfinite = false;
+#pragma unroll
+    for (int k = 0; k < SPT; k++) {
+        A d[kQ], r = A(0), jx = A(0), jy = A(0), jz = A(0);
+#pragma unroll
+        for (int i = 0; i < kQ; i++) {
+            d[i] = f[i][k];
+            r += d[i];
+            if (cvec(i, 0)) jx += cvec(i, 0) * d[i];
+            if (cvec(i, 1)) jy += cvec(i, 1) * d[i];
+            if (cvec(i, 2)) jz += cvec(i, 2) * d[i];
+        }
+        const A rho = A(1) + r;
+        nonfinite |= !(rho > A(0) && rho < A(1e30));
+        A out[kQ];
+        if (bnd[k]) {  // boundary equilibrium of the boundary velocity, as in the BGK bodies
+            TimeWeights<R> tw;
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                tw.slot[a] = th.slot[a];
+                tw.c[a] = th.c[a];
+            }
+            int pp, qq;
+            const int fc = owning_face(xs_[k], ys_[k], zs_[k], Ei, per, pp, qq);
+            R ub[3];
+            boundary_velocity<R>(reinterpret_cast<const R*>(p.ring), p.ring_slot_elems, bd, fc, pp, qq, tw, ub);
+            const A dr = th.drho_b, rb = A(1) + dr;
+            const A u0 = (A)ub[0], u1 = (A)ub[1], u2 = (A)ub[2];
+            const A usq = A(1.5) * (u0 * u0 + u1 * u1 + u2 * u2);
+#pragma unroll
+            for (int i = 0; i < kQ; i++) {
+                A cu = A(0);
+                if (cvec(i, 0)) cu += cvec(i, 0) * u0;
+                if (cvec(i, 1)) cu += cvec(i, 1) * u1;
+                if (cvec(i, 2)) cu += cvec(i, 2) * u2;
+                out[i] = wgt<A>(i) * (dr + rb * (A(3) * cu + A(4.5) * cu * cu - usq));
+            }
+        } else {
+            const A inv = A(1) / rho;
+            fluct_collide<A>(d, r, jx * inv, jy * inv, jz * inv, fd, n, s0 + local(k), out);
+        }
+        if (act[k]) {
+            E* o = Bb + s0 + local(k);
+#pragma unroll
+            for (int i = 0; i < kQ; i++) o[(int64_t)i * n3] = S::out(out[i]);
+        }
+    }
+    if (__any_sync(0xffffffffu, nonfinite) && (tid & 31) == 0) atomicCAS(&p.status[th.box], 0, LB_ERR_NONFINITE);
+}
+
+// Consumer warps: take the stages in order until the producer posts the end.
+// KIND 0: every box of the launch is non-periodic and force-free, so only
+// that tile body is compiled in (fewer registers than the kernel that carries
+// all bodies).
+template <int ST, int SPT, int KIND>
+__device__ __forceinline__ void staged_consume(const SCParams& p, unsigned char* smem, StagedHeader<ST>* hd,
+                                               int64_t n)
+{
+    constexpr bool GENERAL = KIND > 0;
     using G = Staged<ST, SPT>;
     using E = typename Stor<ST>::E;
     for (int k = 0;; k++) {
@@ -425,6 +771,21 @@ __device__ __forceinline__ void staged_consume(const SCParams& p, unsigned char*
             for (int t = threadIdx.x; t < G::kSites; t += kStagedConsumers)
                 if (s0 + t < bd.n3)
                     for (int i = 0; i < kQ; i++) Bb[(int64_t)i * bd.n3 + s0 + t] = Ab[(int64_t)i * bd.n3 + s0 + t];
+        } else if (KIND == 2 && bd.fluct) {
+            if constexpr (KIND == 2) {
+                if (bd.per_mask) staged_tile_fluct<ST, SPT, true>(p, th, stage, &hd->empty[st], n);
+                else staged_tile_fluct<ST, SPT, false>(p, th, stage, &hd->empty[st], n);
+            }
+        } else if constexpr (SPT == 2 && ST != kF64) {  // adjacent site pairs, packed FP32
+            if (!GENERAL) {
+                staged_tile_pair<ST, false, false>(p, th, stage, &hd->empty[st]);
+            } else if (bd.per_mask == 0) {
+                if (bd.has_accel) staged_tile_pair<ST, false, true>(p, th, stage, &hd->empty[st]);
+                else staged_tile_pair<ST, false, false>(p, th, stage, &hd->empty[st]);
+            } else {
+                if (bd.has_accel) staged_tile_pair<ST, true, true>(p, th, stage, &hd->empty[st]);
+                else staged_tile_pair<ST, true, false>(p, th, stage, &hd->empty[st]);
+            }
         } else if (!GENERAL) {
             staged_tile<ST, SPT, false, false>(p, th, stage, &hd->empty[st]);
         } else if (bd.per_mask == 0) {
@@ -437,64 +798,112 @@ __device__ __forceinline__ void staged_consume(const SCParams& p, unsigned char*
     }
 }
 
-// Producer (lane 0 of the last warp): claim tiles from the global counter
-// (reset to zero by the forced re-collision at the end of every step, so a
-// block that starts late -- its SM still busy with the bead kernel -- simply
-// takes fewer tiles) and fill the stages as the consumers free them.
-template <int ST, int SPT, bool GENERAL>
+// Producer warp (the last warp): claims tiles from the global counter (reset
+// to zero by the forced re-collision at the end of every step, so a block that
+// starts late -- its SM still busy with the bead kernel -- simply takes fewer
+// tiles) and fills the stages as the consumers free them.  Lane 0 claims,
+// waits for the stage and writes the tile header; lane i < 19 handles
+// population row i: its source range, the zeroing of the part of the row that
+// lies outside the box's arrays (those sites are boundary sites: their pulled
+// values are multiplied by zero and must be finite, so no consumer may read
+// what a previous tile left there), and its bulk copy.
+template <int ST, int SPT, int KIND>
 __device__ __forceinline__ void staged_produce(const SCParams& p, unsigned char* smem, StagedHeader<ST>* hd, int64_t n)
 {
     using G = Staged<ST, SPT>;
+    using E = typename Stor<ST>::E;
     using R = typename Stor<ST>::R;
     using A = typename Stor<ST>::A;
+    constexpr int T = G::kSites, H = G::kHalo, W = T + 2 * H;
+    const int lane = threadIdx.x & 31;
+    int cy = 0, cz = 0;  // y and z components of this lane's population
+#pragma unroll
+    for (int i = 0; i < kQ; i++)
+        if (lane == i) {
+            cy = cvec(i, 1);
+            cz = cvec(i, 2);
+        }
     unsigned long long* ctr = reinterpret_cast<unsigned long long*>(p.tile_counter);
-    int64_t next = (int64_t)atomicAdd(ctr, 1ull);
+    long long next = lane == 0 ? (long long)atomicAdd(ctr, 1ull) : 0;
+    next = __shfl_sync(0xffffffffu, next, 0);
     int last_b = -1;
     TimeWeights<R> tw{};
     int mlp_s = 0;
     for (int k = 0;; k++) {
         const int st = k % G::kStages;
         // the stage's previous tile must be released by all consumer warps; if
-        // that does not happen within a second the consumers have left
-        if (k >= G::kStages && !mbar_wait_bounded(&hd->empty[st], (uint32_t)(((k / G::kStages) - 1) & 1), p.wait_ns))
-            return;
+        // that does not happen within the limit the consumers have left
+        if (k >= G::kStages) {
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait_bounded(&hd->empty[st], (uint32_t)(((k / G::kStages) - 1) & 1), p.wait_ns);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) return;
+        }
         const int64_t t = next;
+        StagedTile<ST>& th = hd->t[k % (2 * G::kStages)];
         if (t >= p.total_tiles) {
-            hd->t[k % (2 * G::kStages)].box = -1;
-            mbar_arrive(&hd->full[st]);  // completes the phase with no bytes: end of work
+            if (lane == 0) {
+                th.box = -1;
+                mbar_arrive(&hd->full[st]);  // completes the phase with no bytes: end of work
+            }
             return;
         }
-        next = (int64_t)atomicAdd(ctr, 1ull);  // the next claim overlaps this tile's copies
-        const int b = locate_box(p, t);
+        if (lane == 0) next = (long long)atomicAdd(ctr, 1ull);  // the next claim overlaps this tile's copies
+        const int b = locate_box_warp(p, t, lane);
         const BoxDev& bd = p.boxes[b];
-        const int64_t s0 = (t - p.tile_prefix[b]) * G::kSites;
-        if (b != last_b) {  // boundary-layer constants of this box at step n
-            tw = time_weights<R>(n, bd.K, bd.time_interp, p.ring_slots);
-            mlp_s = bd.mlp_row >= 0 ? mlp_substep(n, bd.K) : 0;
-            last_b = b;
+        const int64_t s0 = (t - p.tile_prefix[b]) * T;
+        // header: the box record word by word across the lanes, the rest by lane 0
+        static_assert(sizeof(BoxDev) % 8 == 0 && sizeof(BoxDev) / 8 <= 32, "box record copied by one warp");
+        if (lane < (int)(sizeof(BoxDev) / 8))
+            reinterpret_cast<uint64_t*>(&th.bd)[lane] = reinterpret_cast<const uint64_t*>(&bd)[lane];
+        __syncwarp();
+        if (lane == 0) {
+            if (b != last_b) {  // boundary-layer constants of this box at step n
+                tw = time_weights<R>(n, bd.K, bd.time_interp, p.ring_slots);
+                mlp_s = bd.mlp_row >= 0 ? mlp_substep(n, bd.K) : 0;
+                last_b = b;
+            }
+            if (KIND > 0 && bd.frame) {  // the header carries the body acceleration of step n (frame
+                                         // boxes carry a body force, so they run a general kernel)
+                double a[3];
+                frame_accel_at(bd, p.faccel, p.ring_slots, n, a);
+                for (int c = 0; c < 3; c++) th.bd.accel[c] = a[c];
+            }
+            th.box = b;
+            th.s0 = s0;
+            th.mlp_s = mlp_s;
+            th.frozen = p.status[b] != 0;
+            for (int a = 0; a < 4; a++) {
+                th.slot[a] = tw.slot[a];
+                th.c[a] = tw.c[a];
+            }
+            th.om = A(1) / (A)bd.tau;
+            th.om1 = A(1) - th.om;
+            th.srcfac = A(1) - A(0.5) * th.om;
+            th.drho_b = (A)bd.rho_b - A(1);
         }
-        StagedTile<ST>& th = hd->t[k % (2 * G::kStages)];
-        static_assert(sizeof(BoxDev) % 8 == 0, "box record copied in 8-byte words");
-        for (int w = 0; w < (int)(sizeof(BoxDev) / 8); w++)  // word by word: few live registers
-            reinterpret_cast<uint64_t*>(&th.bd)[w] = reinterpret_cast<const uint64_t*>(&bd)[w];
-        if (GENERAL && bd.frame) {  // the header carries the body acceleration of step n (frame
-                                    // boxes carry a body force, so they run the general kernel)
-            double a[3];
-            frame_accel_at(bd, p.faccel, p.ring_slots, n, a);
-            for (int c = 0; c < 3; c++) th.bd.accel[c] = a[c];
+        // row `lane`: source range clamped to the box's arrays
+        unsigned char* stage = smem + kStagedHeaderBytes + st * G::kStageBytes;
+        const int64_t Ei = bd.E, n3 = bd.n3;
+        const int64_t start = s0 - (cy * Ei + cz * Ei * Ei) - H;
+        const int64_t lo = start > 0 ? start : 0;
+        const int64_t hi = start + W < n3 ? start + W : n3;
+        const bool mine = lane < kQ && hi > lo;
+        uint32_t bytes = mine ? (uint32_t)((hi - lo) * sizeof(E)) : 0u;
+        if (lane < kQ) {
+            const int a = mine ? (int)(lo - start) : W;  // first copied element
+            const int e = mine ? (int)(hi - start) : W;  // end of the copied elements
+            if (a > 0 || e < W) {
+                uint4* row = reinterpret_cast<uint4*>(stage + lane * G::kRowStride);
+                constexpr int per16 = 16 / (int)sizeof(E);
+                for (int x = 0; x < a; x += per16) row[x / per16] = make_uint4(0, 0, 0, 0);
+                for (int x = e; x < W; x += per16) row[x / per16] = make_uint4(0, 0, 0, 0);
+            }
         }
-        th.box = b;
-        th.s0 = s0;
-        th.mlp_s = mlp_s;
-        th.frozen = p.status[b] != 0;
-        for (int a = 0; a < 4; a++) {
-            th.slot[a] = tw.slot[a];
-            th.c[a] = tw.c[a];
-        }
-        th.om = A(1) / (A)bd.tau;
-        th.om1 = A(1) - th.om;
-        th.srcfac = A(1) - A(0.5) * th.om;
-        th.drho_b = (A)bd.rho_b - A(1);
+        uint32_t total = bytes;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+        next = __shfl_sync(0xffffffffu, next, 0);
+        __syncwarp();  // header and zeroed parts written before the stage is armed
         if (t == p.withhold_tile) {
             // test only: this stage is never armed and no copy is issued, so
             // its full barrier never completes and the consumers' bounded wait
@@ -502,12 +911,21 @@ __device__ __forceinline__ void staged_produce(const SCParams& p, unsigned char*
             __threadfence_block();
             continue;
         }
-        fence_proxy_async_smem();
-        issue_tile<ST, SPT>(p, bd, s0, smem + kStagedHeaderBytes + st * G::kStageBytes, &hd->full[st]);
+        if (lane == 0) mbar_arrive_expect_tx(&hd->full[st], total);
+        __syncwarp();
+        if (mine) {
+            fence_proxy_async_smem();
+            const E* Ab = reinterpret_cast<const E*>(p.A) + bd.f_off;
+            bulk_load(stage + lane * G::kRowStride + (lo - start) * sizeof(E), Ab + (int64_t)lane * n3 + lo, bytes,
+                      &hd->full[st]);
+        }
     }
 }
 
-template <int ST, int SPT, bool GENERAL>
+// KIND 0: every box of the launch is plain (velocity faces, no body force);
+// 1: some box is periodic or carries a body force; 2: some box also takes the
+// fluctuating collision.  Each kind compiles only the tile bodies it can meet.
+template <int ST, int SPT, int KIND>
 __global__ void __launch_bounds__(kStagedThreads, 1) k_stream_collide_staged(SCParams p)
 {
     using G = Staged<ST, SPT>;
@@ -523,10 +941,10 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_stream_collide_staged(SCP
     }
     __syncthreads();
     if (threadIdx.x >= kStagedConsumers) {
-        if (threadIdx.x == kStagedConsumers) staged_produce<ST, SPT, GENERAL>(p, smem, hd, n);
+        staged_produce<ST, SPT, KIND>(p, smem, hd, n);  // the whole last warp
         return;
     }
-    staged_consume<ST, SPT, GENERAL>(p, smem, hd);
+    staged_consume<ST, SPT, KIND>(p, smem, hd, n);
 }
 
 }  // namespace lbt

@@ -32,7 +32,7 @@ EXPORTS = ["lb_plan", "lb_create", "lb_destroy", "lb_init", "lb_set_boundary", "
            "lb_graph_capture", "lb_graph_launch", "lb_read_fields", "lb_conservation", "lb_checkpoint_bytes", "lb_save",
            "lb_load", "lb_vorticity", "lb_set_frame_accel", "lb_sync",
            "lb_status",
-           "lb_current_step", "lb_set_launch", "lb_set_bead_launch", "lb_test_inject", "lb_profile", "lb_profile_read", "lb_last_error", "lb_synth_workspace_bytes", "lb_synth_faces",
+           "lb_current_step", "lb_set_launch", "lb_set_bead_launch", "lb_set_fluctuation", "lb_test_inject", "lb_profile", "lb_profile_read", "lb_last_error", "lb_synth_workspace_bytes", "lb_synth_faces",
            "lb_synth_volume", "lb_population_sums_noalloc", "lb_mlp_param_bytes", "lb_mlp_bind", "lb_mlp_train_bytes",
            "lb_mlp_train_init", "lb_mlp_features", "lb_mlp_targets", "lb_mlp_forward", "lb_mlp_grad",
            "lb_mlp_train_step", "lb_mlp_export"]
@@ -98,6 +98,7 @@ def load(path: str | None = None, build_if_missing: bool = True):
         "lb_set_launch": (_i32, [_vp, _i32, _i32, _i32, _i32]),
         "lb_set_bead_launch": (_i32, [_vp, _i32, _i32]),
         "lb_test_inject": (_i32, [_vp, _i32, _i32]),
+        "lb_set_fluctuation": (_i32, [_vp, _i32, _f64, ctypes.c_uint64, _vp]),
         "lb_profile": (_i32, [_vp, _i32, _i32]),
         "lb_profile_read": (_i32, [_vp, ctypes.POINTER(_f64), ctypes.POINTER(_i64)]),
         "lb_last_error": (ctypes.c_char_p, [_vp]),
@@ -202,6 +203,9 @@ class Tracers:
         _check(lib.lb_plan(arr, len(self.descs), storage, int(ring_slots), ctypes.byref(nbytes)))
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.arena = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.stream.device)
+        # the arena may reuse memory that work still pending on torch's current
+        # stream reads; the context's own stream must come after that work
+        self._after_current()
         ctx = _vp()
         _check(lib.lb_create(arr, len(self.descs), storage, int(ring_slots), self.arena.data_ptr(), nbytes.value,
                              self.stream.cuda_stream, ctypes.byref(ctx)))
@@ -209,14 +213,28 @@ class Tracers:
         self.real = torch.float64 if storage == LB_STORE_F64 else torch.float32
         self.np_real = np.float64 if storage == LB_STORE_F64 else np.float32
 
+    def _after_current(self, *tensors):
+        """Order the context stream after the work queued so far on torch's
+        current stream when device memory that stream produced (or last used)
+        is handed to the library: torch enqueues on its current stream, the
+        library on the context's stream."""
+        if tensors and not any(getattr(t, "is_cuda", False) for t in tensors):
+            return
+        cur = self.torch.cuda.current_stream(self.stream.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+
     # ---- thin wrappers (same names as the C ABI) ----
     def lb_init(self, box, u0):
+        self._after_current(u0)
         _check(self.lib.lb_init(self.ctx, box, _ptr(u0)), self.ctx)
 
     def lb_set_boundary(self, box, j, face_u):
+        self._after_current(face_u)
         _check(self.lib.lb_set_boundary(self.ctx, box, int(j), _ptr(face_u)), self.ctx)
 
     def chain_couple(self, box, desc: lb_chain_desc, pos0, vel0=None):
+        self._after_current(pos0, vel0)
         _check(self.lib.chain_couple(self.ctx, box, ctypes.byref(desc), _ptr(pos0), _ptr(vel0)), self.ctx)
 
     def lb_step(self, nsteps=1):
@@ -229,6 +247,7 @@ class Tracers:
         _check(self.lib.lb_graph_launch(self.ctx), self.ctx)
 
     def lb_read_fields(self, box, what, dst):
+        self._after_current(dst)
         _check(self.lib.lb_read_fields(self.ctx, box, what, _ptr(dst)), self.ctx)
 
     def lb_conservation(self, box):
@@ -241,9 +260,11 @@ class Tracers:
 
     def lb_save(self, dst):
         """Checkpoint of the context into dst (host numpy uint8 or device tensor of lb_checkpoint_bytes)."""
+        self._after_current(dst)
         _check(self.lib.lb_save(self.ctx, _ptr(dst)), self.ctx)
 
     def lb_load(self, src):
+        self._after_current(src)
         _check(self.lib.lb_load(self.ctx, _ptr(src)), self.ctx)
 
     def lb_set_frame_accel(self, box, j, a):
@@ -275,6 +296,12 @@ class Tracers:
         _check(self.lib.lb_set_launch(self.ctx, int(kernel), int(threads), int(ctas), int(sites_per_thread)),
                self.ctx)
 
+    def lb_set_fluctuation(self, box, kT, seed, gamma):
+        """Fluctuating collision of a box: gamma 19 relaxation factors (0..3 ignored), or None for BGK."""
+        g = None if gamma is None else np.ascontiguousarray(gamma, dtype=np.float64).reshape(19)
+        _check(self.lib.lb_set_fluctuation(self.ctx, int(box), float(kT), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                           None if g is None else g.ctypes.data), self.ctx)
+
     def lb_test_inject(self, what, wait_limit_us=0):
         _check(self.lib.lb_test_inject(self.ctx, int(what), int(wait_limit_us)), self.ctx)
 
@@ -287,6 +314,7 @@ class Tracers:
         return float(ms.value), int(n.value)
 
     def lb_mlp_bind(self, params, u_max):
+        self._after_current(params)
         _check(self.lib.lb_mlp_bind(self.ctx, _ptr(params), float(u_max)), self.ctx)
 
     def lb_destroy(self):

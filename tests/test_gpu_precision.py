@@ -84,7 +84,12 @@ def cfg3_oracle():
     emul = {}
     for st, ost in ((F16, oracle.STORE_F16), (BF16, oracle.STORE_BF16)):
         emul[st] = (c.run_oracle(nsteps=1, storage=ost).f - w[:, None, None, None]).astype(np.float32)
-    return c, u_plain, emul
+    # magnitude scale of the populations a site pulls: the largest initial
+    # deviation over the site's 3x3x3 neighbourhood
+    from scipy.ndimage import maximum_filter
+    d0 = np.abs(oracle.init(c.oracle_box(), u0) - w[:, None, None, None]).max(axis=0)
+    scale = maximum_filter(d0, size=3, mode="nearest").astype(np.float32)
+    return c, u_plain, emul, scale
 
 
 @pytest.mark.parametrize("storage", [F16, BF16])
@@ -94,18 +99,23 @@ def test_16bit_one_step_sitewise_at_256(lbt, cfg3_oracle, storage):
     # FP32 results and the oracle FP64 results, so a value near a rounding
     # boundary can land one ulp apart (already in the initial state); such a
     # flip moves its neighbours' next values by about one more ulp.
-    c, _, emul = cfg3_oracle
+    # The bound: one ulp of the value itself plus a few ulps of the largest
+    # population the site pulls -- a flipped pulled population moves rho and
+    # j, hence every equilibrium of the site, by about its own ulp, which can
+    # be many ulps of the site's smaller populations.
+    c, _, emul, scale = cfg3_oracle
     r = GpuRunner(lbt, torch, [c], storage)
     r.step(1)
     B = r.tr.deviations(0).astype(np.float64)
     dref = emul[storage].astype(np.float64)
     diff = np.abs(B - dref)
     rel_ulp = 2.0 ** -10 if storage == F16 else 2.0 ** -7
-    tol = 2 * rel_ulp * np.maximum(np.abs(dref), 2.0 ** -14) * 1.01 + 1e-17
+    own = rel_ulp * np.maximum(np.abs(dref), 2.0 ** -14)
+    site = rel_ulp * np.maximum(scale.astype(np.float64), 2.0 ** -14)[None]
     flips = np.count_nonzero(diff > 1e-17)
-    print("storage %d: %d of %d values differ (at most %.2f ulp)"
-          % (storage, flips, diff.size, float((diff / (rel_ulp * np.maximum(np.abs(dref), 2.0 ** -14))).max())))
-    assert np.all(diff <= tol)
+    print("storage %d: %d of %d values differ; at most %.2f own ulp, %.3f ulp of the site's largest pulled value"
+          % (storage, flips, diff.size, float((diff / own).max()), float((diff / site).max())))
+    assert np.all(diff <= 1.01 * own + 4 * site)
     assert flips < 0.01 * diff.size
 
 
@@ -113,7 +123,7 @@ def test_16bit_one_step_sitewise_at_256(lbt, cfg3_oracle, storage):
 def test_256_four_steps_against_fp64_oracle(lbt, cfg3_oracle, storage, bound):
     # the FP32 path that the long runs below compare with is itself checked
     # against the plain FP64 oracle at this size (spec FP32 bound)
-    c, u_plain, _ = cfg3_oracle
+    c, u_plain, _, _ = cfg3_oracle
     r = GpuRunner(lbt, torch, [c], storage)
     r.step(4)
     e = rel_l2(interior(r.tr.fields(0)[1]), u_plain)
@@ -159,7 +169,8 @@ def cfg3_long(lbt):
         tr.lb_read_fields(0, lbt.LB_FIELD_DEV, d)
         sl = (slice(None), slice(1, -1), slice(1, -1), slice(1, -1))
         out[storage] = (u[sl].double(), stress_neq(d)[:, :, 1:-1, 1:-1, 1:-1])
-        del d
+        torch.cuda.synchronize()  # the analysis above is done before its inputs are freed
+        del d, u
         tr.close()
     del faces
     torch.cuda.synchronize()

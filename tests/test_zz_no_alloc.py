@@ -60,12 +60,16 @@ def test_noalloc_sums_equal_conservation_on_two_calls(lbt, storage):
 
 
 def test_noalloc_rejects_boxes_beyond_its_scratch(lbt):
-    buf = torch.zeros(8, dtype=torch.float32, device="cuda")
+    # a buffer of the right size for E = 401 passes the binding's checks; the
+    # library refuses the edge because its fixed scratch covers E <= 400
+    E = 401
+    buf = torch.zeros(19 * E ** 3, dtype=torch.float16, device="cuda")
     out = torch.zeros(4, dtype=torch.float64, device="cuda")
     with pytest.raises(lbt.LBError) as ei:
-        lbt.lb_population_sums_noalloc(buf, lbt.LB_STORE_F32, 512, out)
+        lbt.lb_population_sums_noalloc(buf, lbt.LB_STORE_F16DEV, E, out)
     assert ei.value.code == lbt.LB_ERR_SIZE
     assert "E <= 400" in str(ei.value)
+    del buf
 
 
 def test_noalloc_accepts_the_largest_documented_box(lbt):
