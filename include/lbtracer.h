@@ -432,8 +432,8 @@ int32_t lb_synth_volume(const double* kvec, const double* amp, const double* ome
  * samples j-1 (clamped to 0), j, j+1, j+2 and the in-face differences of
  * samples j and j+1 (24 features divided by u_max, zero-padded to 32).
  * Network 32 -> 128 -> 128 -> 3K with ReLU; bf16 weights and activations on
- * the tensor cores (tcgen05 with TMEM accumulators for inference, the
- * warp-level path when training saves activations), f32 accumulation;
+ * the tcgen05 tensor cores with TMEM accumulators (inference, and the forward
+ * and backward of training; loss and Adam in FP32), f32 accumulation;
  * output row r = (f E + q) E + p holds
  * the residual of component c at substep s in units of u_max / 64 at
  * [3 (s-1) + c] (the residual is a few thousandths of u_max; a finer output

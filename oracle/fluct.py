@@ -1,5 +1,5 @@
 """FP64 oracle of the fluctuating lattice Boltzmann collision (test
-infrastructure only; the GPU path does not implement it yet).
+infrastructure only: the GPU's lb_set_fluctuation is checked against it).
 
 The hybrid method the paper builds on (Sec. 1, the Ahlrichs-Duenweg coupling)
 pairs thermal noise on the beads with a fluctuating fluid, so that kT > 0 is

@@ -1409,7 +1409,7 @@ int32_t lb_mlp_forward(const void* params, int32_t K, const void* X, int64_t row
 {
     if (int st = mlp_check(K, 1, "lb_mlp_forward")) return st;
     if (!params || !X || !Y || rows < 0) return LB_ERR_ARG;
-    return cuda_status(mlp_forward(X, rows, params, K, Y, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream)),
+    return cuda_status(mlp_forward(X, rows, params, K, Y, reinterpret_cast<cudaStream_t>(stream)),
                        "lb_mlp_forward");
 }
 

@@ -4,8 +4,9 @@
 // boundary linearly between samples, Sec. 3; the residual network is an
 // added form).  Network: 24 features (padded to 32) -> 128 -> 128 -> 3K,
 // ReLU, BF16 weights and activations on the tensor cores with FP32
-// accumulation.  Training runs on the GPU with the kernels below: the same
-// BF16 forward, an FP32 backward and Adam on FP32 master weights.
+// accumulation.  Training runs on the GPU: the forward and the backward on the
+// tcgen05 tensor cores (lbt_mlp_tc.cu), the loss and Adam on FP32 master
+// weights below.
 //
 // Layouts
 //   feature matrix X: bf16 [rows][32], row = (f E + q) E + p per box
@@ -50,152 +51,6 @@ MlpLayout mlp_layout(int K)
     L.m_b3 = L.m_w3 + kMlpHidden * L.nout;
     L.nmaster = L.m_b3 + L.nout;
     return L;
-}
-
-// ---------------------------------------------------------------------------
-// tensor-core helpers (mma.sync m16n8k16, bf16 inputs, f32 accumulators)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void mma_16816(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
-{
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-
-__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-
-// shared-memory row strides (bf16 elements), padded so that the eight
-// groups of a warp hit distinct banks when loading B fragments
-constexpr int kLd1 = kMlpIn + 8;
-constexpr int kLd2 = kMlpHidden + 8;
-
-template <int NOUT>
-struct MlpSmem {
-    __nv_bfloat16 w1[kMlpHidden * kLd1];
-    __nv_bfloat16 w2[kMlpHidden * kLd2];
-    __nv_bfloat16 w3[NOUT * kLd2];
-    float b1[kMlpHidden], b2[kMlpHidden], b3[NOUT];
-};
-
-// Hidden layer from the accumulators: bias, ReLU, bf16, packed as the A
-// fragments of the next layer (the C fragment of n-tiles 2k and 2k+1 is the A
-// fragment of k-step k).  Optionally stores the activations (as floats).
-__device__ __forceinline__ void hidden_to_a(const float acc[16][4], const float* bias, uint32_t a[8][4], float* save,
-                                            int64_t r0, int64_t rows, int g, int t)
-{
-#pragma unroll
-    for (int ks = 0; ks < 8; ks++) {
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int nt = 2 * ks + h;
-            const int col = 8 * nt + 2 * t;
-            const float v0 = bf16_round(fmaxf(acc[nt][0] + bias[col], 0.f));
-            const float v1 = bf16_round(fmaxf(acc[nt][1] + bias[col + 1], 0.f));
-            const float v2 = bf16_round(fmaxf(acc[nt][2] + bias[col], 0.f));
-            const float v3 = bf16_round(fmaxf(acc[nt][3] + bias[col + 1], 0.f));
-            a[ks][2 * h + 0] = pack_bf16(v0, v1);
-            a[ks][2 * h + 1] = pack_bf16(v2, v3);
-            if (save) {
-                if (r0 + g < rows) *reinterpret_cast<float2*>(save + (r0 + g) * kMlpHidden + col) = make_float2(v0, v1);
-                if (r0 + g + 8 < rows)
-                    *reinterpret_cast<float2*>(save + (r0 + g + 8) * kMlpHidden + col) = make_float2(v2, v3);
-            }
-        }
-    }
-}
-
-// Fused forward of the three layers: one warp per 16 rows, weights staged
-// once per block in shared memory, blocks stride over the row tiles.
-template <int NOUT, bool SAVE>
-__global__ void __launch_bounds__(256) k_mlp_forward(const __nv_bfloat16* __restrict__ X, int64_t rows,
-                                                     const unsigned char* __restrict__ params, MlpLayout L,
-                                                     float* __restrict__ Y, float* H1, float* H2)
-{
-    extern __shared__ __align__(16) unsigned char mlp_smem_raw[];
-    MlpSmem<NOUT>& sm = *reinterpret_cast<MlpSmem<NOUT>*>(mlp_smem_raw);
-    const __nv_bfloat16* w1 = reinterpret_cast<const __nv_bfloat16*>(params + L.w1);
-    const __nv_bfloat16* w2 = reinterpret_cast<const __nv_bfloat16*>(params + L.w2);
-    const __nv_bfloat16* w3 = reinterpret_cast<const __nv_bfloat16*>(params + L.w3);
-    for (int i = threadIdx.x; i < kMlpHidden * kMlpIn; i += blockDim.x)
-        sm.w1[(i / kMlpIn) * kLd1 + i % kMlpIn] = w1[i];
-    for (int i = threadIdx.x; i < kMlpHidden * kMlpHidden; i += blockDim.x)
-        sm.w2[(i / kMlpHidden) * kLd2 + i % kMlpHidden] = w2[i];
-    for (int i = threadIdx.x; i < NOUT * kMlpHidden; i += blockDim.x)
-        sm.w3[(i / kMlpHidden) * kLd2 + i % kMlpHidden] = w3[i];
-    for (int i = threadIdx.x; i < kMlpHidden; i += blockDim.x) {
-        sm.b1[i] = reinterpret_cast<const float*>(params + L.b1)[i];
-        sm.b2[i] = reinterpret_cast<const float*>(params + L.b2)[i];
-    }
-    for (int i = threadIdx.x; i < NOUT; i += blockDim.x) sm.b3[i] = reinterpret_cast<const float*>(params + L.b3)[i];
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int64_t ntiles = (rows + 15) / 16;
-    for (int64_t tile = (int64_t)blockIdx.x * 8 + warp; tile < ntiles; tile += (int64_t)gridDim.x * 8) {
-        const int64_t r0 = tile * 16;
-        // layer 1: A fragments straight from the feature matrix
-        uint32_t a1[2][4];
-#pragma unroll
-        for (int ks = 0; ks < 2; ks++) {
-            const int c = 16 * ks + 2 * t;
-            const uint32_t* x0 = reinterpret_cast<const uint32_t*>(X + (r0 + g) * kMlpIn + c);
-            const uint32_t* x8 = reinterpret_cast<const uint32_t*>(X + (r0 + g + 8) * kMlpIn + c);
-            const bool v0 = r0 + g < rows, v8 = r0 + g + 8 < rows;
-            a1[ks][0] = v0 ? x0[0] : 0u;
-            a1[ks][1] = v8 ? x8[0] : 0u;
-            a1[ks][2] = v0 ? x0[4] : 0u;  // columns c + 8
-            a1[ks][3] = v8 ? x8[4] : 0u;
-        }
-        float acc[16][4];
-#pragma unroll
-        for (int nt = 0; nt < 16; nt++) {
-            acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll
-            for (int ks = 0; ks < 2; ks++) {
-                const uint32_t* wb = reinterpret_cast<const uint32_t*>(sm.w1 + (8 * nt + g) * kLd1 + 16 * ks + 2 * t);
-                mma_16816(acc[nt], a1[ks], wb[0], wb[4]);
-            }
-        }
-        uint32_t a2[8][4];
-        hidden_to_a(acc, sm.b1, a2, SAVE ? H1 : nullptr, r0, rows, g, t);
-        // layer 2
-#pragma unroll
-        for (int nt = 0; nt < 16; nt++) {
-            acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll
-            for (int ks = 0; ks < 8; ks++) {
-                const uint32_t* wb = reinterpret_cast<const uint32_t*>(sm.w2 + (8 * nt + g) * kLd2 + 16 * ks + 2 * t);
-                mma_16816(acc[nt], a2[ks], wb[0], wb[4]);
-            }
-        }
-        uint32_t a3[8][4];
-        hidden_to_a(acc, sm.b2, a3, SAVE ? H2 : nullptr, r0, rows, g, t);
-        // layer 3 and the output
-#pragma unroll
-        for (int nt = 0; nt < NOUT / 8; nt++) {
-            float o[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int ks = 0; ks < 8; ks++) {
-                const uint32_t* wb = reinterpret_cast<const uint32_t*>(sm.w3 + (8 * nt + g) * kLd2 + 16 * ks + 2 * t);
-                mma_16816(o, a3[ks], wb[0], wb[4]);
-            }
-            const int col = 8 * nt + 2 * t;
-            if (r0 + g < rows)
-                *reinterpret_cast<float2*>(Y + (r0 + g) * NOUT + col) = make_float2(o[0] + sm.b3[col], o[1] + sm.b3[col + 1]);
-            if (r0 + g + 8 < rows)
-                *reinterpret_cast<float2*>(Y + (r0 + g + 8) * NOUT + col) =
-                    make_float2(o[2] + sm.b3[col], o[3] + sm.b3[col + 1]);
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -311,60 +166,6 @@ __global__ void k_mse(const float* Y, const float* T, int64_t n, float scale, fl
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc * scale);
 }
 
-// dW[i][o] += sum_r Hin[r][i] dZ[r][o] and db[o] += sum_r dZ[r][o] over a
-// chunk of rows; 32 x 32 output tile per block, 256 threads x 4 outputs.
-template <class TIN>
-__global__ void __launch_bounds__(256) k_grad_w(const TIN* Hin, int nin, const float* dZ, int nout, int64_t rows,
-                                                int64_t rows_per_block, float* dW, float* db)
-{
-    __shared__ float sH[64][33];
-    __shared__ float sZ[64][33];
-    const int i0 = blockIdx.x * 32, o0 = blockIdx.y * 32;
-    const int64_t rbeg = blockIdx.z * rows_per_block;
-    const int64_t rend = min(rows, rbeg + rows_per_block);
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // ty 0..7: outputs i = i0 + ty + 8 k
-    float acc[4] = {0, 0, 0, 0};
-    float bacc = 0.f;
-    for (int64_t r = rbeg; r < rend; r += 64) {
-        for (int e = threadIdx.x; e < 64 * 32; e += 256) {
-            const int rr = e >> 5, cc = e & 31;
-            const int64_t row = r + rr;
-            sH[rr][cc] = (row < rend && i0 + cc < nin) ? (float)Hin[row * nin + i0 + cc] : 0.f;
-            sZ[rr][cc] = (row < rend && o0 + cc < nout) ? dZ[row * nout + o0 + cc] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int rr = 0; rr < 64; rr++) {
-            const float z = sZ[rr][tx];
-#pragma unroll
-            for (int k = 0; k < 4; k++) acc[k] += sH[rr][ty + 8 * k] * z;
-            if (ty == 0 && blockIdx.x == 0) bacc += z;
-        }
-        __syncthreads();
-    }
-    if (o0 + tx < nout) {
-        for (int k = 0; k < 4; k++)
-            if (i0 + ty + 8 * k < nin) atomicAdd(&dW[(i0 + ty + 8 * k) * nout + o0 + tx], acc[k]);
-        if (ty == 0 && blockIdx.x == 0 && db) atomicAdd(&db[o0 + tx], bacc);
-    }
-}
-
-// dHin[r][i] = (sum_o dZ[r][o] W[i][o]) * (Hin[r][i] > 0), W taken from the
-// bf16 out-major inference weights (the ones the forward used).
-__global__ void k_grad_h(const float* dZ, int nout, const __nv_bfloat16* Wt, int nin, const float* Hin, int64_t rows,
-                         float* dH)
-{
-    const int64_t n = rows * nin;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = e / nin;
-        const int i = (int)(e - r * nin);
-        float s = 0.f;
-        if (Hin[e] > 0.f)
-            for (int o = 0; o < nout; o++) s += dZ[r * nout + o] * __bfloat162float(Wt[o * nin + i]);
-        dH[e] = s;
-    }
-}
-
 // Adam on the master weights, then the bf16 / f32 inference copy.
 __global__ void k_adam(float* master, float* m, float* v, const float* grad, int64_t n, float lr, float b1, float b2,
                        float eps, float c1, float c2)
@@ -416,33 +217,9 @@ static int grid_cap(int64_t n, int threads)
     return (int)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
 }
 
-template <int NOUT, bool SAVE>
-static cudaError_t forward_t(const void* X, int64_t rows, const void* params, const MlpLayout& L, float* Y, float* H1,
-                             float* H2, cudaStream_t s)
+cudaError_t mlp_forward(const void* X, int64_t rows, const void* params, int K, float* Y, cudaStream_t s)
 {
-    static int attr_done[kMaxDevices] = {};  // per instantiation and device
-    const int smem = (int)sizeof(MlpSmem<NOUT>);
-    cudaError_t e = smem_attr_per_device(k_mlp_forward<NOUT, SAVE>, smem, attr_done);
-    if (e != cudaSuccess) return e;
-    const int64_t tiles = (rows + 15) / 16;
-    int64_t blocks = (tiles + 7) / 8;
-    if (blocks > 152 * 2) blocks = 152 * 2;
-    if (blocks < 1) blocks = 1;
-    k_mlp_forward<NOUT, SAVE><<<(unsigned)blocks, 256, smem, s>>>(reinterpret_cast<const __nv_bfloat16*>(X), rows,
-                                                                  reinterpret_cast<const unsigned char*>(params), L, Y,
-                                                                  H1, H2);
-    return cudaGetLastError();
-}
-
-cudaError_t mlp_forward(const void* X, int64_t rows, const void* params, int K, float* Y, float* H1, float* H2,
-                        cudaStream_t s)
-{
-    const MlpLayout L = mlp_layout(K);
-    const bool save = H1 != nullptr;
-    if (!save) return mlp_forward_tc(X, rows, params, K, Y, nullptr, s);  // inference: tcgen05
-    if (K == 16) return save ? forward_t<48, true>(X, rows, params, L, Y, H1, H2, s) : forward_t<48, false>(X, rows, params, L, Y, H1, H2, s);
-    if (K == 8) return save ? forward_t<24, true>(X, rows, params, L, Y, H1, H2, s) : forward_t<24, false>(X, rows, params, L, Y, H1, H2, s);
-    return cudaErrorInvalidValue;
+    return mlp_forward_tc(X, rows, params, K, Y, nullptr, s);  // row-major output
 }
 
 cudaError_t mlp_features(const MlpFeatureSet* sets_dev, int nsets, int64_t total_rows, double u_max, int real_f64,
@@ -520,31 +297,18 @@ cudaError_t mlp_grad(unsigned char* ws, const MlpTrain& W, const void* X, const 
     float* f = reinterpret_cast<float*>(ws);
     const MlpLayout& L = W.L;
     const unsigned char* params = ws + W.params_byte;
-    cudaError_t e = mlp_forward(X, rows, params, W.K, f + W.y, f + W.h1, f + W.h2, s);
+    // forward on tcgen05, saving the bf16 activations (h1, h2 hold bf16 rows)
+    cudaError_t e = mlp_forward_save_tc(X, rows, params, W.K, f + W.y, f + W.h1, f + W.h2, s);
     if (e != cudaSuccess) return e;
     cudaMemsetAsync(f + W.grad, 0, sizeof(float) * L.nmaster, s);
     cudaMemsetAsync(f + W.loss, 0, sizeof(double), s);
     const int64_t ny = rows * L.nout;
     k_mse<<<grid_cap(ny, 256), 256, 0, s>>>(f + W.y, T, ny, 1.0f / (float)ny, f + W.dy,
                                             reinterpret_cast<double*>(f + W.loss));
-    const int64_t rpb = 1024;
-    const unsigned zsplit = (unsigned)((rows + rpb - 1) / rpb);
-    // layer 3
-    k_grad_w<float><<<dim3(kMlpHidden / 32, (L.nout + 31) / 32, zsplit), 256, 0, s>>>(
-        f + W.h2, kMlpHidden, f + W.dy, L.nout, rows, rpb, f + W.grad + L.m_w3, f + W.grad + L.m_b3);
-    k_grad_h<<<grid_cap(rows * kMlpHidden, 256), 256, 0, s>>>(
-        f + W.dy, L.nout, reinterpret_cast<const __nv_bfloat16*>(params + L.w3), kMlpHidden, f + W.h2, rows, f + W.dh2);
-    // layer 2
-    k_grad_w<float><<<dim3(kMlpHidden / 32, kMlpHidden / 32, zsplit), 256, 0, s>>>(
-        f + W.h1, kMlpHidden, f + W.dh2, kMlpHidden, rows, rpb, f + W.grad + L.m_w2, f + W.grad + L.m_b2);
-    k_grad_h<<<grid_cap(rows * kMlpHidden, 256), 256, 0, s>>>(
-        f + W.dh2, kMlpHidden, reinterpret_cast<const __nv_bfloat16*>(params + L.w2), kMlpHidden, f + W.h1, rows,
-        f + W.dh1);
-    // layer 1 (input: the bf16 features)
-    k_grad_w<__nv_bfloat16><<<dim3(kMlpIn / 32, kMlpHidden / 32, zsplit), 256, 0, s>>>(
-        reinterpret_cast<const __nv_bfloat16*>(X), kMlpIn, f + W.dh1, kMlpHidden, rows, rpb, f + W.grad + L.m_w1,
-        f + W.grad + L.m_b1);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // backward on tcgen05 (dh2, dh1 hold bf16 rows)
+    return mlp_backward_tc(X, rows, params, W.K, f + W.h1, f + W.h2, f + W.dy, f + W.dh2, f + W.dh1, f + W.grad, s);
 }
 
 cudaError_t mlp_adam(unsigned char* ws, const MlpTrain& W, float lr, int64_t t, cudaStream_t s)

@@ -41,8 +41,8 @@ struct MlpFeatureSet {
 MlpLayout mlp_layout(int K);
 MlpTrain mlp_train_layout(int K, int64_t batch_rows);
 
-cudaError_t mlp_forward(const void* X, int64_t rows, const void* params, int K, float* Y, float* H1, float* H2,
-                        cudaStream_t s);
+// Inference forward, Y row-major [rows][3K] (tcgen05).
+cudaError_t mlp_forward(const void* X, int64_t rows, const void* params, int K, float* Y, cudaStream_t s);
 // Inference forward on the tcgen05 tensor cores (lbt_mlp_tc.cu); err (device,
 // may be null) receives LB_ERR_TIMEOUT if an MMA does not complete.  Y is
 // row-major [rows][3K] when col_stride is 0, else column-major: output c of
@@ -50,6 +50,14 @@ cudaError_t mlp_forward(const void* X, int64_t rows, const void* params, int K, 
 // residual at one substep is then read from consecutive rows).
 cudaError_t mlp_forward_tc(const void* X, int64_t rows, const void* params, int K, float* Y, int32_t* err,
                            cudaStream_t s, int64_t col_stride = 0);
+// Training forward on tcgen05: Y row-major [rows][3K] FP32 and the bf16
+// hidden activations after ReLU, H1 and H2 row-major [rows][128].
+cudaError_t mlp_forward_save_tc(const void* X, int64_t rows, const void* params, int K, float* Y, void* H1, void* H2,
+                                cudaStream_t s);
+// Backward on tcgen05 from dY (FP32 [rows][3K]): the FP32 gradient (master
+// layout, added to `grad`), with dH2 and dH1 (bf16 [rows][128]) as scratch.
+cudaError_t mlp_backward_tc(const void* X, int64_t rows, const void* params, int K, const void* H1, const void* H2,
+                            const float* dY, void* dH2, void* dH1, float* grad, cudaStream_t s);
 cudaError_t mlp_features(const MlpFeatureSet* sets_dev, int nsets, int64_t total_rows, double u_max, int real_f64,
                          void* X, cudaStream_t s);
 // Features of one face set passed by value (6 E^2 rows from row 0).
