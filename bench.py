@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--threads", type=int, default=0, help="stream-collide block size (0 = library default)")
     p.add_argument("--ctas", type=int, default=0, help="persistent grid size (0 = one block per tile)")
     p.add_argument("--vw", type=int, default=0, help="sites per thread in stream-collide (0 = default)")
+    p.add_argument("--bead-layout", default=None, help="MD thread layout 'lanes,beads_per_thread' of the bead "
+                   "kernel (as lb_set_bead_launch; default: autotuned, or the library default with --no-tune)")
     p.add_argument("--kernel", default="staged", choices=["staged", "register"],
                    help="stream-collide kernel: TMA-staged pipeline or register tiles")
     p.add_argument("--dry-run", action="store_true",
@@ -350,13 +352,13 @@ def main():
     from paper_0809_4958_gb300 import autotune
     modes = inputs.mode_table(seed, w["M"], w["k_min"], w["k_max"], E)
     ncand = 0 if args.no_tune else len(autotune.candidates(storage, torch.cuda.get_device_properties(dev).multi_processor_count))
-    tune_steps = 7 * ncand + 7 * 5  # launch shapes, then the bead kernel's thread layouts
+    tune_steps = 7 * ncand + 7 * 6  # launch shapes, then the bead kernel's six thread layouts
     # graph replays of G steps, then any remainder stepped plainly: exactly
     # args.steps timed steps.  G is the largest even length of at most 16
     # steps that divides the step count (an odd count leaves one plain step)
     even = args.steps // 2 * 2
     G = max([g for g in range(2, min(w["graph"], even) + 1, 2) if even % g == 0] or [0])
-    nsamp = args.warmup + tune_steps + args.steps + w["graph"] + 2
+    nsamp = args.warmup + tune_steps + args.steps + 2 * w["graph"] + 2  # + one untimed replay
     faces = lbt.synth_faces(modes, E, w["K"], 0, nsamp, real)
     u0 = lbt.synth_volume(modes, E, 0.0, real)
     pos0 = inputs.chain_start(seed + 5, w["nbeads"], E)
@@ -386,6 +388,9 @@ def main():
     choice = (kernel, args.threads, args.ctas, args.vw)
     if not args.no_tune:  # the autotuner steps the simulation; its steps are untimed warm-up
         choice, table = autotune.tune(tr, step, steps_per_candidate=6, use_cache=False)
+    if args.bead_layout:
+        tr.bead_lanes = tuple(int(v) for v in args.bead_layout.split(","))
+        tr.lb_set_bead_launch(*tr.bead_lanes)
     step(args.warmup)
     tr.lb_sync()
 
@@ -402,12 +407,25 @@ def main():
     tr.lb_profile(1, G if nrep else rest)
     if nrep:
         tr.lb_graph_capture(G)
+        push_until(tr.lb_current_step() + G, dev_src)  # one untimed replay: the graph's first run
+        tr.lb_graph_launch()
+        tr.lb_sync()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)  # let the sampler take its first reading
+    # The samples of a replay are pushed while the replay before it runs (the
+    # host enqueues them behind that graph): the first replay's before the
+    # timed region, one replay's worth after the last one inside it, so the
+    # timed region still pushes exactly one sample per timed step.
+    if nrep:
+        push_until(tr.lb_current_step() + G, dev_src)
+        torch.cuda.synchronize()
     ev0.record(stream)
     for _ in range(nrep):
-        push_until(tr.lb_current_step() + G, dev_src)
         tr.lb_graph_launch()
+        push_until(tr.lb_current_step() + G, dev_src)
     step(rest)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -424,10 +442,12 @@ def main():
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     if not args.no_e2e:
-        e2e_steps = min(args.steps, 2000, nsamp - 2)
-        host_faces = torch.empty((e2e_steps + 2, 6, 3, E, E), dtype=real, pin_memory=True)
-        host_faces.copy_(faces[:e2e_steps + 2].cpu())
-        host_chain = torch.empty((e2e_steps, 2, w["nbeads"], 3), dtype=torch.float64, pin_memory=True)
+        W2 = args.warmup  # untimed steps through the same path first
+        e2e_steps = min(args.steps, 2000, nsamp - 2 - W2)
+        nstep2 = W2 + e2e_steps
+        host_faces = torch.empty((nstep2 + 2, 6, 3, E, E), dtype=real, pin_memory=True)
+        host_faces.copy_(faces[:nstep2 + 2].cpu())
+        host_chain = torch.empty((nstep2, 2, w["nbeads"], 3), dtype=torch.float64, pin_memory=True)
         # fresh context so the pushed samples line up with the host record
         tr2 = lbt.Tracers([lbt.box_desc(E, w["tau"], nbeads=w["nbeads"], K=w["K"])], storage, stream=stream)
         tr2.lb_set_launch(*choice)
@@ -437,22 +457,53 @@ def main():
         tr2.chain_couple(0, lbt.chain_desc(w["nbeads"], kT=w["kT"], n_md=w["n_md"], seed=seed), pos0)
         tr2.lb_set_boundary(0, 0, host_faces[0])
         tr2.lb_sync()
+        # Each step's sample goes host -> device on a copy stream into a small
+        # ring of device staging buffers, AHEAD samples before the step that
+        # needs it, so the copy overlaps the steps before; the context stream
+        # waits for the copy, then pushes the sample into the boundary ring
+        # (device to device) and steps.  Events order the reuse of a buffer.
+        AHEAD, D = 2, 4
+        copy_stream = torch.cuda.Stream()
+        stage = torch.empty((D, 6, 3, E, E), dtype=real, device=dev)
+        ev_copied = [torch.cuda.Event() for _ in range(D)]
+        ev_used = [torch.cuda.Event() for _ in range(D)]
+
+        def start_copy(j, last):
+            if j <= last:
+                copy_stream.wait_event(ev_used[j % D])  # the buffer's previous sample is in the ring
+                with torch.cuda.stream(copy_stream):
+                    stage[j % D].copy_(host_faces[j], non_blocking=True)
+                ev_copied[j % D].record(copy_stream)
+
+        def run_steps(n0, count):  # steps n0 .. n0 + count - 1 (samples n0 + 1 ..)
+            for j in range(n0 + 1, n0 + AHEAD + 1):
+                start_copy(j, n0 + count)
+            for n in range(n0, n0 + count):
+                start_copy(n + 1 + AHEAD, n0 + count)
+                stream.wait_event(ev_copied[(n + 1) % D])
+                tr2.lb_set_boundary(0, n + 1, stage[(n + 1) % D])
+                ev_used[(n + 1) % D].record(stream)
+                tr2.lb_step(1)
+                tr2.lb_read_fields(0, lbt.LB_FIELD_CHAIN | lbt.LB_FIELD_ASYNC, host_chain[n])
+
+        run_steps(0, W2)
+        tr2.lb_sync()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ev0.record(stream)
-        for n in range(e2e_steps):
-            tr2.lb_set_boundary(0, n + 1, host_faces[n + 1])
-            tr2.lb_step(1)
-            tr2.lb_read_fields(0, lbt.LB_FIELD_CHAIN | lbt.LB_FIELD_ASYNC, host_chain[n])
+        run_steps(W2, e2e_steps)
         ev1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         units2, ms2 = whole_job(E ** 3 * e2e_steps, max(ev0.elapsed_time(ev1), wall * 1e3), dev)
         e2e = {"value": units2 / (ms2 * 1e-3) / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": 6 * 3 * E * E * s_real, "d2h_bytes_per_step": 2 * w["nbeads"] * 3 * 8,
-               "steps": e2e_steps}
+               "steps": e2e_steps,
+               "how": "pinned host samples copied on a second stream %d steps ahead into device staging, pushed "
+                      "with lb_set_boundary, lb_step per step, the chain read back asynchronously every step"
+                      % AHEAD}
         tr2.close()
 
     if rank != 0:
@@ -473,6 +524,7 @@ def main():
         "config": single_config(args.storage),
         "launch": {"kernel": ["staged", "register"][choice[0]], "threads": choice[1], "ctas": choice[2],
                    "sites_per_thread": choice[3], "bead_layout": list(getattr(tr, "bead_lanes", (0, 1))),
+                   "bead_autotune": [[list(c), t] for c, t in getattr(tr, "bead_table", [])],
                    "graph_steps": G, "graph_replays": nrep, "plain_steps": rest,
                    "autotune": [[list(c), t] for c, t in table]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -529,8 +581,8 @@ def run_batch(args, standalone=True):
     steps = (args.steps + G - 1) // G * G
     warm = (args.warmup + G - 1) // G * G
     ncand = len(autotune.candidates(lbt.LB_STORE_F32, torch.cuda.get_device_properties(dev).multi_processor_count))
-    tune_steps = 7 * ncand + 7 * 5  # launch shapes, then the bead kernel's thread layouts
-    nsamp = warm + tune_steps + steps + G + 2
+    tune_steps = 7 * ncand + 7 * 6  # launch shapes, then the bead kernel's six thread layouts
+    nsamp = warm + tune_steps + steps + 3 * G + 2  # + the untimed first replay and one replay pushed ahead
     descs = [lbt.box_desc(int(E), w["tau"], nbeads=int(N), K=w["K"]) for E, N in zip(edges, nbs)]
     stream = torch.cuda.Stream()
     tr = lbt.Tracers(descs, lbt.LB_STORE_F32, stream=stream, ring_slots=G + 4)
@@ -567,6 +619,10 @@ def run_batch(args, standalone=True):
     tr.lb_profile(1, G)
     tr.lb_graph_capture(G)
     tr.lb_profile(0)
+    push_until(tr.lb_current_step() + G)  # one untimed replay: the graph's first run
+    tr.lb_graph_launch()
+    push_until(tr.lb_current_step() + G)  # the first timed replay's samples
+    tr.lb_sync()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     if world > 1:
@@ -575,9 +631,9 @@ def run_batch(args, standalone=True):
     clocks.start()
     time.sleep(0.3)
     ev0.record(stream)
-    for _ in range(steps // G):
-        push_until(tr.lb_current_step() + G)
+    for _ in range(steps // G):  # a replay's samples are pushed behind the replay before it
         tr.lb_graph_launch()
+        push_until(tr.lb_current_step() + G)
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -642,7 +698,7 @@ def run_paper(args):
     warm = (args.warmup + G - 1) // G * G
     u_eta = um.eta_lb / um.tau_eta_lb
     modes = inputs.mode_table(21, 256, 1.0, 10.0, E, u_max=3 * u_eta)
-    J = (warm + steps + G) // K + 3
+    J = (warm + steps + 3 * G) // K + 3
     faces = lbt.synth_faces(modes, E, K, 0, J, torch.float32, zoom=z)
     v = inputs.tracer_velocity(modes, np.arange(J) * K)
     faces -= torch.from_numpy(v).to(faces)[:, None, :, None, None]  # co-moving frame
@@ -667,15 +723,19 @@ def run_paper(args):
         tr.lb_step(1)
     tr.lb_sync()
     tr.lb_graph_capture(G)
+    push_until(tr.lb_current_step() + G)  # one untimed replay: the graph's first run
+    tr.lb_graph_launch()
+    push_until(tr.lb_current_step() + G)  # the first timed replay's samples
+    tr.lb_sync()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
     ev0.record(stream)
-    for _ in range(steps // G):
-        push_until(tr.lb_current_step() + G)
+    for _ in range(steps // G):  # a replay's samples are pushed behind the replay before it
         tr.lb_graph_launch()
+        push_until(tr.lb_current_step() + G)
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -858,7 +918,7 @@ def run_mlp(args, standalone=True):
         tr = lbt.Tracers(descs, lbt.LB_STORE_F32, stream=stream, ring_slots=G // Kb + 4 if Kb else 4)
         fs = 18 * E * E
         warm = args.warmup // G * G if timed else 0
-        nsamp = (warm + nsteps) // Kb + 4
+        nsamp = (warm + nsteps + (3 * G if timed else 0)) // Kb + 4
         faces = torch.empty((nsamp, len(seeds) * fs), dtype=torch.float32, device="cuda")
         for b, sd in enumerate(seeds):
             modes = inputs.mode_table(sd, w["M"], w["k_min"], w["k_max"], E)
@@ -883,12 +943,16 @@ def run_mlp(args, standalone=True):
                 push_until(need(n))
                 tr.lb_step(1)
             tr.lb_graph_capture(G)
+            push_until(need(tr.lb_current_step() + G - 1))  # one untimed replay: the graph's first run
+            tr.lb_graph_launch()
+            push_until(need(tr.lb_current_step() + G - 1))  # the first timed replay's samples
+            tr.lb_sync()
             torch.cuda.synchronize()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            for _ in range(nsteps // G):
-                push_until(need(tr.lb_current_step() + G - 1))
+            for _ in range(nsteps // G):  # a replay's samples are pushed behind the replay before it
                 tr.lb_graph_launch()
+                push_until(need(tr.lb_current_step() + G - 1))
             ev1.record(stream)
             torch.cuda.synchronize()
             ms = ev0.elapsed_time(ev1)

@@ -336,9 +336,13 @@ int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas
  *   lanes: threads per bead, 0 = default (8, halved until the MD threads
  *   fit 512), or 1, 2, 4, 8; the lanes of a bead share its bond and pair
  *   forces and sum them by shuffles.  beads_per_thread: 1, or 2 with
- *   lanes = 1 (one warp holds up to 64 beads).
- *   lanes x ceil(largest chain / beads_per_thread) <= 512.  Used by the
- *   autotuner; drops a captured graph.  LB_ERR_ARG otherwise. */
+ *   lanes = 1 (two beads per thread), or 0 with lanes = 2: the chain-order
+ *   layout -- thread t holds bead t / 2; one lane of a bead takes its bonds,
+ *   the other the beads two apart, the two split the Verlet list, every pair
+ *   slot masked rather than branched.  One barrier over the MD threads per
+ *   substep in every layout.  lanes x ceil(largest chain / beads_per_thread)
+ *   <= 512.  Used by the autotuner; drops a captured graph.  LB_ERR_ARG
+ *   otherwise. */
 int32_t lb_set_bead_launch(lb_ctx* ctx, int32_t lanes, int32_t beads_per_thread);
 
 /*

@@ -54,9 +54,9 @@ def tune_bead_lanes(tr, step, nsteps: int = 6):
     maxb = max(d.nbeads for d in tr.descs)
     if maxb == 0:
         return (0, 1)
-    best = None
-    for lanes, bpt in ((1, 2), (1, 1), (2, 1), (4, 1), (8, 1)):
-        if lanes * ((maxb + bpt - 1) // bpt) > 512:
+    best, table = None, []
+    for lanes, bpt in ((2, 0), (1, 2), (1, 1), (2, 1), (4, 1), (8, 1)):
+        if bpt > 0 and lanes * ((maxb + bpt - 1) // bpt) > 512:
             continue
         tr.lb_set_bead_launch(lanes, bpt)
         step(1)
@@ -66,10 +66,12 @@ def tune_bead_lanes(tr, step, nsteps: int = 6):
         e1.record(tr.stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / nsteps
+        table.append(((lanes, bpt), ms))
         if best is None or ms < best[1]:
             best = ((lanes, bpt), ms)
     tr.lb_set_bead_launch(*best[0])
     tr.bead_lanes = best[0]
+    tr.bead_table = table
     return best[0]
 
 

@@ -377,6 +377,8 @@ int enqueue_step(lb_ctx* ctx, int64_t n)
     sp.status = ctx->at<int32_t>(ctx->L.status);
     sp.wait_ns = ctx->wait_ns;
     sp.withhold_tile = ctx->inject == LB_INJECT_WITHHOLD_LAST_TILE ? sp.total_tiles - 1 : -1;
+    sp.hint_loads = nch > 0;
+    sp.pad_hint = 0;
     const bool timed = ctx->profiling && ctx->prof_used + 2 <= ctx->prof_ev.size();
     // inside a stream capture the timing events must become event-record nodes of the graph
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -815,6 +817,10 @@ int32_t lb_graph_capture(lb_ctx* ctx, int32_t nsteps)
     e = cudaGraphInstantiate(&ctx->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaGraphInstantiate");
+    // move the executable graph to the device now, so that the first launch
+    // costs what every later one does
+    e = cudaGraphUpload(ctx->graph, ctx->stream);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaGraphUpload");
     ctx->graph_steps = nsteps;
     ctx->graph_parity = parity;
     ctx->graph_step0 = ctx->step;
@@ -987,11 +993,13 @@ int32_t lb_set_bead_launch(lb_ctx* ctx, int32_t lanes, int32_t beads_per_thread)
     if (!ctx) return LB_ERR_ARG;
     if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
         return ctx->fail(LB_ERR_ARG, "lb_set_bead_launch: lanes must be 0, 1, 2, 4 or 8");
-    if (beads_per_thread != 1 && beads_per_thread != 2)
-        return ctx->fail(LB_ERR_ARG, "lb_set_bead_launch: beads_per_thread must be 1 or 2");
-    if (beads_per_thread == 2 && lanes > 1)
+    if (beads_per_thread != 0 && beads_per_thread != 1 && beads_per_thread != 2)
+        return ctx->fail(LB_ERR_ARG, "lb_set_bead_launch: beads_per_thread must be 0, 1 or 2");
+    if (beads_per_thread == 2 && lanes != 1)
         return ctx->fail(LB_ERR_ARG, "lb_set_bead_launch: two beads per thread take one lane per bead");
-    if (lanes * ((ctx->max_beads + beads_per_thread - 1) / beads_per_thread) > 512)
+    if (beads_per_thread == 0 && lanes != 2)
+        return ctx->fail(LB_ERR_ARG, "lb_set_bead_launch: the chain-order layout (beads_per_thread 0) takes two lanes");
+    if (beads_per_thread > 0 && lanes * ((ctx->max_beads + beads_per_thread - 1) / beads_per_thread) > 512)
         return ctx->fail(LB_ERR_ARG, "lb_set_bead_launch: lanes x beads per thread layout exceeds 512 threads");
     ctx->bead_lanes = lanes;
     ctx->bead_bpt = beads_per_thread;

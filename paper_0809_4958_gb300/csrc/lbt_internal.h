@@ -156,6 +156,8 @@ struct SCParams {
     const FluctDev* fluct;        // [nboxes] fluctuating-collision parameters
     int64_t wait_ns;              // limit of the staged kernel's bounded barrier waits
     int64_t withhold_tile;        // test only: the staged producer never arms this tile (-1: none)
+    int32_t hint_loads;           // 1: the staged bulk copies take the L2 evict-first policy (chains in the launch)
+    int32_t pad_hint;
 };
 
 constexpr int64_t kWaitLimitNs = 1000000000;  // bounded device waits give up after one second
@@ -192,7 +194,7 @@ struct BeadParams {
     int32_t max_beads;    // largest chain of the launch (shared-memory strides)
     int32_t noise_chunk;  // substeps whose noise is drawn at once
     int32_t lanes;        // threads per bead in the MD substeps (1, 2, 4 or 8)
-    int32_t beads_per_thread;  // beads an MD thread holds (1 or 2)
+    int32_t beads_per_thread;  // beads an MD thread holds (1 or 2; 0: one warp holds the chain)
 };
 
 struct ForcedParams {

@@ -728,6 +728,265 @@ __device__ __forceinline__ int md_substeps_split(const BeadParams& p, const Chai
     return 0;
 }
 
+// Force on a bead at X from a partner at q, added to F where `on` (exactly
+// zero otherwise, so that lanes taking different pairs run one instruction
+// stream): WCA within the cut-off (the Kremer-Grest chain: WCA acts between
+// every pair, bonded or not) plus, for a bond (`fene`), FENE -- the
+// expressions of pair_force, the two laws sharing r^2.  Both beads of a pair
+// evaluate the same fac from exactly negated differences.  Returns true for a
+// bond stretched to R0 or beyond.
+template <class MT>
+__device__ __forceinline__ bool chain_pair(const MT X[3], const typename Vec4<MT>::T& q, bool fene, bool on,
+                                           const PairConsts<MT>& c, bool wca, MT F[3])
+{
+    const MT rx = X[0] - q.x, ry = X[1] - q.y, rz = X[2] - q.z;
+    const MT r2 = rx * rx + ry * ry + rz * rz;
+    MT fac = fene ? -c.kf * recip(MT(1) - r2 * c.inv_R02) : MT(0);
+    if (wca) {
+        const MT inv = recip(r2);
+        const MT s2 = c.sig2 * inv, s6 = s2 * s2 * s2;
+        fac += r2 < c.rc2 ? c.e24 * (MT(2) * s6 * s6 - s6) * inv : MT(0);
+    }
+    fac = on ? fac : MT(0);
+    F[0] += fac * rx;
+    F[1] += fac * ry;
+    F[2] += fac * rz;
+    return on && fene && r2 >= c.R02;
+}
+
+// The MD substeps with two lanes per bead in chain order: thread t holds
+// bead t / 2 in role t & 1.  Each lane reads two partners from the positions
+// published in shared memory -- role 0 the bonded neighbours (FENE + WCA),
+// role 1 the beads two apart (WCA) -- and the pairs at least three apart come
+// from Verlet lists split between the two lanes (role r takes entries r,
+// r + 2, ...; the first four of a lane as bytes of one register).  The lanes
+// of a bead sum their forces with one shuffle and apply the same update, so
+// both hold the bead's state; role 0 publishes the position.  Every branch of
+// the force phase is uniform over the warp (pair slots are masked, not
+// skipped), so a lane's pair computations interleave.  One barrier over the
+// MD threads per substep publishes the positions and ORs the flags "some bead
+// left half the Verlet skin" and "error" (a warp vote when the chain fits one
+// warp).  The lists are built by the whole block before the substeps from the
+// start positions and rebuilt by the MD threads after a flagged barrier.
+// Symplectic Euler as in md_substeps.  Called by every thread of the block;
+// returns an error code (0 = none), the same in all threads.
+template <class MT>
+__device__ __forceinline__ int md_chain_pairs(const BeadParams& p, const ChainDev& ch, int N, int64_t n, int b,
+                                              MT* sXbuf, MT (*sU)[3], MT (*sV)[3], double (*sR)[3], MT (*sP)[3],
+                                              unsigned char (*sNb)[kMaxTasks], int* sErrP)
+{
+    using V4 = typename Vec4<MT>::T;
+    __shared__ int sNbN[kMaxBeads];  // listed partners of each bead
+    __shared__ int sErrB;            // list overflow of the block's build
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int maxb = p.max_beads;
+    V4* sX4 = reinterpret_cast<V4*>(sXbuf);  // [2][maxb] positions, then [chunk][N] noise
+    const V4* sXi = sX4 + 2 * maxb;
+    const MT* mc;
+    if constexpr (sizeof(MT) == 8) mc = reinterpret_cast<const MT*>(ch.md_d);
+    else mc = reinterpret_cast<const MT*>(ch.md_f);
+    const MT dt = mc[kMdDt], dtm = mc[kMdDtm], namp = mc[kMdNamp], zeta = mc[kMdZeta];
+    const PairConsts<MT> pc{mc[kMdR02], mc[kMdInvR02], mc[kMdKf], mc[kMdSig2], mc[kMdRc2], mc[kMdE24]};
+    const bool wca = ch.eps > 0.0;
+    const MT rl2 = mc[kMdRl2], half_skin2 = mc[kMdHalfSkin2];
+    // errors of substep s go to sErrP[s & 1]: a thread that has passed the
+    // barrier of substep s can write next only to the other word, so every MD
+    // thread reads the same value after that barrier and all stop together
+    if (tid < 2) sErrP[tid] = 0;
+    if (tid == 0) sErrB = 0;
+    __syncthreads();
+    // Verlet lists of the pairs at least three apart, from the start positions
+    // (buffer 0): eight threads per bead scan every eighth partner and merge
+    // their finds in order by a prefix sum over the eight
+    if (wca) {
+        for (int base = 0; base < 8 * N; base += nthr) {
+            const int e = base + tid;
+            const bool act = e < 8 * N;
+            const int bb = act ? e >> 3 : 0, r = e & 7;
+            uint32_t m = 0;  // bit k: partner r + 8 k (N <= 256)
+            if (act) {
+                const V4 xb = sX4[bb];
+                for (int k = 0, p2 = r; p2 < N; k++, p2 += 8) {
+                    const int dd = p2 - bb;
+                    if (dd >= -2 && dd <= 2) continue;
+                    const V4 q = sX4[p2];
+                    const MT dx = xb.x - q.x, dy = xb.y - q.y, dz = xb.z - q.z;
+                    if (dx * dx + dy * dy + dz * dz < rl2) m |= 1u << k;
+                }
+            }
+            const int cnt = __popc(m);
+            int incl = cnt;
+            for (int o = 1; o < 8; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o, 8);
+                if (r >= o) incl += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 7, 8);
+            if (act) {
+                int k = incl - cnt;
+                for (uint32_t mm = m; mm; mm &= mm - 1, k++)
+                    if (k < kMaxTasks) sNb[bb][k] = (unsigned char)(r + 8 * (__ffs(mm) - 1));
+                if (r == 7) {
+                    sNbN[bb] = total;
+                    if (total > kMaxTasks) sErrB = LB_ERR_CHAIN;  // more neighbours than the list holds
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (sErrB) return sErrB;
+
+    const int nmd = (2 * N + 31) & ~31;  // MD threads: whole warps
+    const bool md = tid < nmd;
+    const int g = tid >> 1, role = tid & 1;
+    const bool own = md && g < N;
+    const int gg = own ? g : 0;
+    const V4 xs = sX4[gg];
+    const MT x0[3] = {own ? xs.x : MT(0), own ? xs.y : MT(0), own ? xs.z : MT(0)};
+    MT u[3], v[3], d[3] = {MT(0), MT(0), MT(0)}, pm[3] = {MT(0), MT(0), MT(0)}, dref[3] = {MT(0), MT(0), MT(0)};
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        u[a] = own ? sU[gg][a] : MT(0);
+        v[a] = own ? sV[gg][a] : MT(0);
+    }
+    // the two fixed partners of this lane: g -/+ 1 (role 0) or g -/+ 2 (role 1)
+    const int off = role ? 2 : 1;
+    const bool onl = own && g - off >= 0, onr = own && g + off < N;
+    const int il = onl ? g - off : gg, ir = onr ? g + off : gg;
+    const bool fene = role == 0;
+    MT fx[3];
+    for (int a = 0; a < 3; a++) fx[a] = role == 0 ? (MT)ch.f_ext[a] : MT(0);  // added once per bead
+    // this lane's share of the list: entries role, role + 2, ...; the first
+    // four as bytes of li (unused slots name the bead itself: a valid
+    // position, masked out), and the warp's largest share
+    int nl = own && wca ? sNbN[gg] : 0;
+    uint32_t li = 0;
+    int mine = 0, kmax = 0;
+    auto pack = [&]() {
+        mine = nl > role ? (nl - role + 1) >> 1 : 0;
+        li = 0;
+#pragma unroll
+        for (int s = 0; s < 4; s++) li |= (uint32_t)(s < mine ? sNb[gg][role + 2 * s] : gg) << (8 * s);  // < kMaxTasks
+        kmax = __reduce_max_sync(0xffffffffu, mine);
+    };
+    if (md) pack();
+    auto sync_or = [&](bool f) -> bool {
+        if (nmd == 32) {
+            __syncwarp();
+            return __any_sync(0xffffffffu, f);
+        }
+        return bar_or(1, nmd, f);
+    };
+    const int chunk = namp > MT(0) ? p.noise_chunk : ch.n_md;
+    for (int c0 = 0; c0 < ch.n_md; c0 += chunk) {
+        const int nc = min(chunk, ch.n_md - c0);
+        if (namp > MT(0)) {
+            __syncthreads();  // the previous chunk's noise is consumed
+            md_noise<MT>(sX4 + 2 * maxb, n, c0, nc, N, b, ch.seed);
+            __syncthreads();
+        }
+        if (md) {
+            for (int sb = 0; sb < nc; sb++) {
+                const int sub = c0 + sb;
+                const V4* Xc = sX4 + (sub & 1) * maxb;
+                V4* Xn = sX4 + ((sub + 1) & 1) * maxb;
+                const V4 xi = namp > MT(0) ? sXi[sb * N + gg] : V4{};
+                const V4 ql = Xc[il], qr = Xc[ir];
+                const MT X[3] = {x0[0] + d[0], x0[1] + d[1], x0[2] + d[2]};
+                MT F[3] = {fx[0], fx[1], fx[2]};
+                bool stretched = chain_pair<MT>(X, ql, fene, onl, pc, wca, F);
+                stretched |= chain_pair<MT>(X, qr, fene, onr, pc, wca, F);
+                if (kmax > 0) {
+#pragma unroll
+                    for (int s = 0; s < 2; s++) chain_pair<MT>(X, Xc[(li >> (8 * s)) & 255u], false, s < mine, pc, true, F);
+                }
+                if (kmax > 2) {
+#pragma unroll
+                    for (int s = 2; s < 4; s++) chain_pair<MT>(X, Xc[(li >> (8 * s)) & 255u], false, s < mine, pc, true, F);
+                }
+                if (kmax > 4) {
+                    const int nlc = min(nl, kMaxTasks);  // an overflowing list stops at the next barrier
+                    for (int k = role + 8; k < nlc; k += 2) chain_pair<MT>(X, Xc[sNb[gg][k]], false, true, pc, true, F);
+                }
+#pragma unroll
+                for (int a = 0; a < 3; a++) F[a] += __shfl_xor_sync(0xffffffffu, F[a], 1);
+                const MT xin[3] = {xi.x, xi.y, xi.z};
+                MT m2 = MT(0), xn[3];
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    const MT ffric = -zeta * (v[a] - u[a]);
+                    const MT fnoise = namp * xin[a];
+                    v[a] += dtm * (F[a] + ffric + fnoise);
+                    d[a] += dt * v[a];
+                    pm[a] -= (ffric + fnoise) * dt;
+                    xn[a] = x0[a] + d[a];
+                    const MT dm = d[a] - dref[a];
+                    m2 += dm * dm;
+                }
+                if (own && role == 0) {
+                    V4 w;
+                    w.x = xn[0];
+                    w.y = xn[1];
+                    w.z = xn[2];
+                    w.w = MT(0);
+                    Xn[g] = w;
+                }
+                if (stretched) sErrP[sub & 1] = LB_ERR_FENE;
+                const bool moved = own && wca && m2 > half_skin2;
+                // publish Xn; any flag: stop on an error, or rebuild the lists
+                if (sync_or(stretched || moved)) {
+                    if (sErrP[sub & 1]) break;
+                    // the two lanes of a bead scan alternate partners: a count
+                    // pass, then each writes its finds after the other's count
+                    const V4 xb = Xn[gg];
+                    int cnt = 0;
+                    if (own)
+                        for (int p2 = role; p2 < N; p2 += 2) {
+                            const int dd = p2 - g;
+                            if (dd >= -2 && dd <= 2) continue;
+                            const V4 q = Xn[p2];
+                            const MT dx = xb.x - q.x, dy = xb.y - q.y, dz = xb.z - q.z;
+                            cnt += dx * dx + dy * dy + dz * dz < rl2;
+                        }
+                    const int c_other = __shfl_xor_sync(0xffffffffu, cnt, 1);
+                    int k = role ? c_other : 0;
+                    if (own)
+                        for (int p2 = role; p2 < N; p2 += 2) {
+                            const int dd = p2 - g;
+                            if (dd >= -2 && dd <= 2) continue;
+                            const V4 q = Xn[p2];
+                            const MT dx = xb.x - q.x, dy = xb.y - q.y, dz = xb.z - q.z;
+                            if (dx * dx + dy * dy + dz * dz < rl2) {
+                                if (k < kMaxTasks) sNb[gg][k] = (unsigned char)p2;
+                                k++;
+                            }
+                        }
+                    nl = own ? cnt + c_other : 0;
+                    // more neighbours than the list holds: the error stops
+                    // the next barrier (or the chunk's)
+                    if (nl > kMaxTasks) sErrP[(sub + 1) & 1] = LB_ERR_CHAIN;
+#pragma unroll
+                    for (int a = 0; a < 3; a++) dref[a] = d[a];
+                    __syncwarp();  // both lanes' finds are in place
+                    pack();
+                }
+            }
+        }
+        __syncthreads();
+        if (sErrP[0] || sErrP[1]) break;
+    }
+    const int err = sErrP[0] ? sErrP[0] : sErrP[1];
+    if (err) return err;
+    if (own && role == 0)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            sR[g][a] += (double)d[a];
+            sV[g][a] = v[a];
+            sP[g][a] = pm[a];
+        }
+    __syncthreads();
+    return 0;
+}
+
 template <int ST>
 __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
 {
@@ -858,7 +1117,9 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
     {
         __shared__ int sErrP[2];
         int err;
-        if (p.beads_per_thread == 1 && p.lanes == 8)
+        if (p.beads_per_thread == 0)
+            err = md_chain_pairs<MT>(p, ch, N, n, b, sXbuf, sU, sV, sR, sP, sNb, sErrP);
+        else if (p.beads_per_thread == 1 && p.lanes == 8)
             err = md_substeps_split<MT, 8>(p, ch, N, n, b, sXbuf, sU, sV, sR, sP, sNb, sErrP);
         else if (p.beads_per_thread == 1 && p.lanes == 4)
             err = md_substeps_split<MT, 4>(p, ch, N, n, b, sXbuf, sU, sV, sR, sP, sNb, sErrP);
@@ -1268,11 +1529,14 @@ cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, int max_be
         bpt = 1;
         while (lanes > 1 && lanes * max_beads > kBeadThreadsMax) lanes >>= 1;
     }
-    if (bpt != 2) bpt = 1;
+    if (bpt != 2 && bpt != 0) bpt = 1;
     q.lanes = lanes;
     q.beads_per_thread = bpt;
-    // the MD threads, at least 256 for the gather, the noise and the spreading
-    int threads = (lanes * ((max_beads + bpt - 1) / bpt) + 31) / 32 * 32;
+    // the MD threads, at least 256 for the gather, the noise and the
+    // spreading; the chain-order layout: eight threads per bead for those
+    int threads = bpt == 0 ? 8 * max_beads : lanes * ((max_beads + bpt - 1) / bpt);
+    threads = (threads + 31) / 32 * 32;
+    if (threads > kBeadThreadsMax) threads = kBeadThreadsMax;
     if (threads < 256) threads = 256;
     k_bead_couple<ST><<<nchains, threads, dyn, s>>>(q);
     return cudaGetLastError();

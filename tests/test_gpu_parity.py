@@ -129,7 +129,7 @@ def test_bead_lanes_agree(lbt, storage):
     # same chain up to the order of the force sums
     c = Case(24, 0.8, 20, M=32, nbeads=40, kT=1e-4)
     runs = []
-    for lanes, bpt in ((1, 1), (1, 2), (2, 1), (4, 1), (8, 1)):
+    for lanes, bpt in ((1, 1), (1, 2), (2, 1), (4, 1), (8, 1), (2, 0)):
         r = GpuRunner(lbt, torch, [c], storage)
         r.tr.lb_set_bead_launch(lanes, bpt)
         r.step(20)
