@@ -353,10 +353,13 @@ def main():
     modes = inputs.mode_table(seed, w["M"], w["k_min"], w["k_max"], E)
     ncand = 0 if args.no_tune else len(autotune.candidates(storage, torch.cuda.get_device_properties(dev).multi_processor_count))
     tune_steps = 7 * ncand + 7 * 6  # launch shapes, then the bead kernel's six thread layouts
-    # graph replays of G steps, then any remainder stepped plainly: exactly
-    # args.steps timed steps.  G is the largest even length of at most 16
-    # steps that divides the step count (an odd count leaves one plain step)
-    even = args.steps // 2 * 2
+    # graph replays of G steps, then P steps stepped plainly with the
+    # stream-collide launches timed by CUDA events (event-record nodes inside
+    # a graph serialise its kernels: they cost about 10 us per step at
+    # 128^3), then any remainder: exactly args.steps timed steps.  G is the
+    # largest even length of at most 16 steps that divides the graph part.
+    P = min(8, args.steps)
+    even = (args.steps - P) // 2 * 2
     G = max([g for g in range(2, min(w["graph"], even) + 1, 2) if even % g == 0] or [0])
     nsamp = args.warmup + tune_steps + args.steps + 2 * w["graph"] + 2  # + one untimed replay
     faces = lbt.synth_faces(modes, E, w["K"], 0, nsamp, real)
@@ -402,9 +405,8 @@ def main():
     torch.cuda.synchronize()
     # G steps per CUDA graph replay; the samples of the next G steps are pushed
     # (device to device) before each replay
-    nrep = args.steps // G if G else 0
-    rest = args.steps - nrep * G
-    tr.lb_profile(1, G if nrep else rest)
+    nrep = (args.steps - P) // G if G else 0
+    rest = args.steps - nrep * G  # the plain steps, P of them and more, all with timed stream-collides
     if nrep:
         tr.lb_graph_capture(G)
         push_until(tr.lb_current_step() + G, dev_src)  # one untimed replay: the graph's first run
@@ -426,6 +428,7 @@ def main():
     for _ in range(nrep):
         tr.lb_graph_launch()
         push_until(tr.lb_current_step() + G, dev_src)
+    tr.lb_profile(1, rest)  # host side only: the plain steps below record the events
     step(rest)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -616,9 +619,7 @@ def run_batch(args, standalone=True):
     choice, table = autotune.tune(tr, step, steps_per_candidate=6, use_cache=False)
     step(warm)
     tr.lb_sync()
-    tr.lb_profile(1, G)
     tr.lb_graph_capture(G)
-    tr.lb_profile(0)
     push_until(tr.lb_current_step() + G)  # one untimed replay: the graph's first run
     tr.lb_graph_launch()
     push_until(tr.lb_current_step() + G)  # the first timed replay's samples
@@ -631,13 +632,18 @@ def run_batch(args, standalone=True):
     clocks.start()
     time.sleep(0.3)
     ev0.record(stream)
-    for _ in range(steps // G):  # a replay's samples are pushed behind the replay before it
+    for _ in range(steps // G - 1):  # a replay's samples are pushed behind the replay before it
         tr.lb_graph_launch()
         push_until(tr.lb_current_step() + G)
+    # the last G steps plainly, their stream-collide launches timed by CUDA
+    # events (event-record nodes inside a graph would serialise its kernels)
+    tr.lb_profile(1, G)
+    step(G)
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    sc_ms, sc_n = tr.lb_profile_read()  # the kernels of the last graph replay
+    tr.lb_profile(0)
+    sc_ms, sc_n = tr.lb_profile_read()
     tr.lb_sync()
     units, ms = whole_job(sites * steps, ev0.elapsed_time(ev1), dev)
     value = units / (ms * 1e-3) / 1e6

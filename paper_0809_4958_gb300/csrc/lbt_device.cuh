@@ -159,10 +159,18 @@ __device__ __forceinline__ float unit_uniform_t<float>(uint32_t v)
 }
 
 // Reciprocal of the bead pair forces: correctly rounded division in FP64,
-// the fast approximate division intrinsic in FP32 (a couple of ulp, far
-// below the FP32 dynamics' own rounding).
+// the hardware's approximate reciprocal in FP32 (PTX rcp.approx.ftz.f32, at
+// most one ulp off, far below the FP32 dynamics' own rounding; the pair
+// arguments are never subnormal).  One instruction: the MD substeps are a
+// latency-bound chain, and the approximate division intrinsic it replaces
+// cost half of a substep's force phase.
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
-__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float recip(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 __device__ __forceinline__ int wrapi(int v, int E) { return v < 0 ? v + E : (v >= E ? v - E : v); }
 

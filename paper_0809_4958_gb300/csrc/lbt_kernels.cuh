@@ -754,12 +754,49 @@ __device__ __forceinline__ bool chain_pair(const MT X[3], const typename Vec4<MT
     return on && fene && r2 >= c.R02;
 }
 
+// Verlet list of bead g (pairs at least three apart within sqrt(rl2)) from
+// the positions X, written to lst by the two lanes of the bead: each scans
+// alternate partners, a count pass, then each writes its finds after the
+// other's.  Kept out of line so that the substep loop stays small in the
+// instruction cache; called by every lane of the warp.  Returns the length
+// (entries past kMaxTasks are not written).
+template <class MT>
+__device__ __noinline__ int rebuild_chain_list(const typename Vec4<MT>::T* X, unsigned char* lst, int g, int role, int N,
+                                               bool own, MT rl2)
+{
+    using V4 = typename Vec4<MT>::T;
+    const V4 xb = X[own ? g : 0];
+    int cnt = 0;
+    if (own)
+        for (int p2 = role; p2 < N; p2 += 2) {
+            const int dd = p2 - g;
+            if (dd >= -2 && dd <= 2) continue;
+            const V4 q = X[p2];
+            const MT dx = xb.x - q.x, dy = xb.y - q.y, dz = xb.z - q.z;
+            cnt += dx * dx + dy * dy + dz * dz < rl2;
+        }
+    const int c_other = __shfl_xor_sync(0xffffffffu, cnt, 1);
+    int k = role ? c_other : 0;
+    if (own)
+        for (int p2 = role; p2 < N; p2 += 2) {
+            const int dd = p2 - g;
+            if (dd >= -2 && dd <= 2) continue;
+            const V4 q = X[p2];
+            const MT dx = xb.x - q.x, dy = xb.y - q.y, dz = xb.z - q.z;
+            if (dx * dx + dy * dy + dz * dz < rl2) {
+                if (k < kMaxTasks) lst[k] = (unsigned char)p2;
+                k++;
+            }
+        }
+    return own ? cnt + c_other : 0;
+}
+
 // The MD substeps with two lanes per bead in chain order: thread t holds
 // bead t / 2 in role t & 1.  Each lane reads two partners from the positions
 // published in shared memory -- role 0 the bonded neighbours (FENE + WCA),
 // role 1 the beads two apart (WCA) -- and the pairs at least three apart come
 // from Verlet lists split between the two lanes (role r takes entries r,
-// r + 2, ...; the first four of a lane as bytes of one register).  The lanes
+// r + 2, ...; the first two of a lane as bytes of one register).  The lanes
 // of a bead sum their forces with one shuffle and apply the same update, so
 // both hold the bead's state; role 0 publishes the position.  Every branch of
 // the force phase is uniform over the warp (pair slots are masked, not
@@ -856,7 +893,7 @@ __device__ __forceinline__ int md_chain_pairs(const BeadParams& p, const ChainDe
     MT fx[3];
     for (int a = 0; a < 3; a++) fx[a] = role == 0 ? (MT)ch.f_ext[a] : MT(0);  // added once per bead
     // this lane's share of the list: entries role, role + 2, ...; the first
-    // four as bytes of li (unused slots name the bead itself: a valid
+    // two as bytes of li (unused slots name the bead itself: a valid
     // position, masked out), and the warp's largest share
     int nl = own && wca ? sNbN[gg] : 0;
     uint32_t li = 0;
@@ -865,7 +902,7 @@ __device__ __forceinline__ int md_chain_pairs(const BeadParams& p, const ChainDe
         mine = nl > role ? (nl - role + 1) >> 1 : 0;
         li = 0;
 #pragma unroll
-        for (int s = 0; s < 4; s++) li |= (uint32_t)(s < mine ? sNb[gg][role + 2 * s] : gg) << (8 * s);  // < kMaxTasks
+        for (int s = 0; s < 2; s++) li |= (uint32_t)(s < mine ? sNb[gg][role + 2 * s] : gg) << (8 * s);  // < kMaxTasks
         kmax = __reduce_max_sync(0xffffffffu, mine);
     };
     if (md) pack();
@@ -889,23 +926,25 @@ __device__ __forceinline__ int md_chain_pairs(const BeadParams& p, const ChainDe
                 const int sub = c0 + sb;
                 const V4* Xc = sX4 + (sub & 1) * maxb;
                 V4* Xn = sX4 + ((sub + 1) & 1) * maxb;
+                // the lane's two fixed partners and its first two list slots
+                // in one branch-free block, so that the four pair
+                // computations interleave (empty slots are masked)
                 const V4 xi = namp > MT(0) ? sXi[sb * N + gg] : V4{};
-                const V4 ql = Xc[il], qr = Xc[ir];
+                const V4 ql = Xc[il], qr = Xc[ir], q0 = Xc[li & 255u], q1 = Xc[(li >> 8) & 255u];
                 const MT X[3] = {x0[0] + d[0], x0[1] + d[1], x0[2] + d[2]};
-                MT F[3] = {fx[0], fx[1], fx[2]};
+                MT F[3] = {fx[0], fx[1], fx[2]}, G[3] = {MT(0), MT(0), MT(0)};
                 bool stretched = chain_pair<MT>(X, ql, fene, onl, pc, wca, F);
-                stretched |= chain_pair<MT>(X, qr, fene, onr, pc, wca, F);
-                if (kmax > 0) {
+                stretched |= chain_pair<MT>(X, qr, fene, onr, pc, wca, G);
+                chain_pair<MT>(X, q0, false, wca && 0 < mine, pc, wca, F);
+                chain_pair<MT>(X, q1, false, wca && 1 < mine, pc, wca, G);
 #pragma unroll
-                    for (int s = 0; s < 2; s++) chain_pair<MT>(X, Xc[(li >> (8 * s)) & 255u], false, s < mine, pc, true, F);
-                }
-                if (kmax > 2) {
-#pragma unroll
-                    for (int s = 2; s < 4; s++) chain_pair<MT>(X, Xc[(li >> (8 * s)) & 255u], false, s < mine, pc, true, F);
-                }
-                if (kmax > 4) {
-                    const int nlc = min(nl, kMaxTasks);  // an overflowing list stops at the next barrier
-                    for (int k = role + 8; k < nlc; k += 2) chain_pair<MT>(X, Xc[sNb[gg][k]], false, true, pc, true, F);
+                for (int a = 0; a < 3; a++) F[a] += G[a];
+                // the rest of the list (rare: a bead with more than four
+                // listed partners), one slot per trip, read from shared memory
+                for (int s = 2; s < kmax; s++) {
+                    const int k = role + 2 * s;
+                    const bool on = s < mine && k < kMaxTasks;  // an overflowing list stops at the next barrier
+                    chain_pair<MT>(X, Xc[on ? sNb[gg][k] : gg], false, on, pc, true, F);
                 }
 #pragma unroll
                 for (int a = 0; a < 3; a++) F[a] += __shfl_xor_sync(0xffffffffu, F[a], 1);
@@ -935,32 +974,7 @@ __device__ __forceinline__ int md_chain_pairs(const BeadParams& p, const ChainDe
                 // publish Xn; any flag: stop on an error, or rebuild the lists
                 if (sync_or(stretched || moved)) {
                     if (sErrP[sub & 1]) break;
-                    // the two lanes of a bead scan alternate partners: a count
-                    // pass, then each writes its finds after the other's count
-                    const V4 xb = Xn[gg];
-                    int cnt = 0;
-                    if (own)
-                        for (int p2 = role; p2 < N; p2 += 2) {
-                            const int dd = p2 - g;
-                            if (dd >= -2 && dd <= 2) continue;
-                            const V4 q = Xn[p2];
-                            const MT dx = xb.x - q.x, dy = xb.y - q.y, dz = xb.z - q.z;
-                            cnt += dx * dx + dy * dy + dz * dz < rl2;
-                        }
-                    const int c_other = __shfl_xor_sync(0xffffffffu, cnt, 1);
-                    int k = role ? c_other : 0;
-                    if (own)
-                        for (int p2 = role; p2 < N; p2 += 2) {
-                            const int dd = p2 - g;
-                            if (dd >= -2 && dd <= 2) continue;
-                            const V4 q = Xn[p2];
-                            const MT dx = xb.x - q.x, dy = xb.y - q.y, dz = xb.z - q.z;
-                            if (dx * dx + dy * dy + dz * dz < rl2) {
-                                if (k < kMaxTasks) sNb[gg][k] = (unsigned char)p2;
-                                k++;
-                            }
-                        }
-                    nl = own ? cnt + c_other : 0;
+                    nl = rebuild_chain_list<MT>(Xn, sNb[gg], g, role, N, own, rl2);
                     // more neighbours than the list holds: the error stops
                     // the next barrier (or the chunk's)
                     if (nl > kMaxTasks) sErrP[(sub + 1) & 1] = LB_ERR_CHAIN;
