@@ -356,11 +356,16 @@ def main():
     # graph replays of G steps, then P steps stepped plainly with the
     # stream-collide launches timed by CUDA events (event-record nodes inside
     # a graph serialise its kernels: they cost about 10 us per step at
-    # 128^3), then any remainder: exactly args.steps timed steps.  G is the
-    # largest even length of at most 16 steps that divides the graph part.
-    P = min(8, args.steps)
-    even = (args.steps - P) // 2 * 2
-    G = max([g for g in range(2, min(w["graph"], even) + 1, 2) if even % g == 0] or [0])
+    # 128^3): exactly args.steps timed steps.  G = 16 for runs of 64 steps
+    # or more (P from 8 to 23), else the largest even length that divides
+    # the graph part.
+    if args.steps >= 64:  # full graphs of 16: P in 8 .. 23
+        P = 8 + (args.steps - 8) % w["graph"]
+        G = w["graph"]
+    else:
+        P = min(8, args.steps)
+        even = (args.steps - P) // 2 * 2
+        G = max([g for g in range(2, min(w["graph"], even) + 1, 2) if even % g == 0] or [0])
     nsamp = args.warmup + tune_steps + args.steps + 2 * w["graph"] + 2  # + one untimed replay
     faces = lbt.synth_faces(modes, E, w["K"], 0, nsamp, real)
     u0 = lbt.synth_volume(modes, E, 0.0, real)
@@ -441,76 +446,113 @@ def main():
         dist.barrier()
     ms_per_step = ms / args.steps
     value = units / (ms * 1e-3) / 1e6
+    bead_layout = list(getattr(tr, "bead_lanes", (0, 1)))
+    bead_table = [[list(c), t] for c, t in getattr(tr, "bead_table", [])]
+    tr.close()  # the end-to-end leg gets the device to itself (a run with the sample
+    # record of 10,000 steps still held measured 20 % slower end to end)
 
     # ---- end to end through the C ABI with host buffers ----
+    # The same step as above (graph replays of G2 steps), fed from pinned host
+    # memory and read back to it: every step's boundary sample goes host ->
+    # device on a copy stream (a replay's G2 samples in one copy, two replays
+    # ahead, into a pair of device staging blocks), is pushed into the
+    # boundary ring behind the replay before its own (device to device,
+    # lb_set_boundary), and every step's chain positions, left by the bead
+    # kernel in a trajectory ring (lb_set_chain_history), come back to pinned
+    # host memory after each replay.  The first replay's samples are pushed
+    # before the timed region and one replay's worth after the last one inside
+    # it, so the timed region moves exactly one sample in and one result out
+    # per timed step.
     e2e = None
     if not args.no_e2e:
-        W2 = args.warmup  # untimed steps through the same path first
-        e2e_steps = min(args.steps, 2000, nsamp - 2 - W2)
-        nstep2 = W2 + e2e_steps
-        host_faces = torch.empty((nstep2 + 2, 6, 3, E, E), dtype=real, pin_memory=True)
-        host_faces.copy_(faces[:nstep2 + 2].cpu())
-        host_chain = torch.empty((nstep2, 2, w["nbeads"], 3), dtype=torch.float64, pin_memory=True)
+        W2 = args.warmup  # plain untimed steps first
+        G2 = w["graph"]  # replays of 16 steps (shorter graphs cost more per step end to end)
+        nrep2 = max(1, min(args.steps, 2000) // G2)
+        e2e_steps = nrep2 * G2
+        nstep2 = W2 + (nrep2 + 3) * G2
+        if nstep2 + 2 > faces.shape[0]:
+            faces = torch.cat([faces, lbt.synth_faces(modes, E, w["K"], faces.shape[0], nstep2 + 2 - faces.shape[0], real)])
+        host_faces = faces[:nstep2 + 2].cpu()  # the host record of the boundary samples (pageable)
+        del faces, dev_src
+        torch.cuda.empty_cache()
+        nb = w["nbeads"]
+        host_hist = torch.empty((nrep2, G2, nb, 3), dtype=torch.float64, pin_memory=True)
         # fresh context so the pushed samples line up with the host record
-        tr2 = lbt.Tracers([lbt.box_desc(E, w["tau"], nbeads=w["nbeads"], K=w["K"])], storage, stream=stream)
+        tr2 = lbt.Tracers([lbt.box_desc(E, w["tau"], nbeads=nb, K=w["K"])], storage, stream=stream, ring_slots=G2 + 4)
         tr2.lb_set_launch(*choice)
-        tr2.lb_set_bead_launch(*getattr(tr, "bead_lanes", (0, 1)))
+        tr2.lb_set_bead_launch(*bead_layout)
         torch.cuda.synchronize()
         tr2.lb_init(0, u0)
-        tr2.chain_couple(0, lbt.chain_desc(w["nbeads"], kT=w["kT"], n_md=w["n_md"], seed=seed), pos0)
-        tr2.lb_set_boundary(0, 0, host_faces[0])
+        tr2.chain_couple(0, lbt.chain_desc(nb, kT=w["kT"], n_md=w["n_md"], seed=seed), pos0)
+        hist = torch.zeros((G2, nb, 3), dtype=torch.float64, device=dev)
+        tr2.lb_set_chain_history(hist, G2)
+        tr2.lb_set_boundary(0, 0, host_faces[0].contiguous())
+        for n in range(W2):
+            tr2.lb_set_boundary(0, n + 1, host_faces[n + 1])
+            tr2.lb_step(1)
         tr2.lb_sync()
-        # Each step's sample goes host -> device on a copy stream into a small
-        # ring of device staging buffers, AHEAD samples before the step that
-        # needs it, so the copy overlaps the steps before; the context stream
-        # waits for the copy, then pushes the sample into the boundary ring
-        # (device to device) and steps.  Events order the reuse of a buffer.
-        AHEAD, D = 2, 4
         copy_stream = torch.cuda.Stream()
-        stage = torch.empty((D, 6, 3, E, E), dtype=real, device=dev)
-        ev_copied = [torch.cuda.Event() for _ in range(D)]
-        ev_used = [torch.cuda.Event() for _ in range(D)]
+        NB = 3  # pinned staging blocks: a small ring stays fast for the copy engine (copies from a
+        # pinned buffer of the whole record slowed to about 5 GB/s once the device had been busy)
+        pinned = torch.empty((NB, G2, 6, 3, E, E), dtype=real, pin_memory=True)
+        stage = torch.empty((2, G2, 6, 3, E, E), dtype=real, device=dev)
+        ev_h2d = [torch.cuda.Event() for _ in range(NB)]
+        ev_copied = [torch.cuda.Event() for _ in range(2)]
+        ev_used = [torch.cuda.Event() for _ in range(2)]
+        lib, ctx = tr2.lib, tr2.ctx
 
-        def start_copy(j, last):
-            if j <= last:
-                copy_stream.wait_event(ev_used[j % D])  # the buffer's previous sample is in the ring
-                with torch.cuda.stream(copy_stream):
-                    stage[j % D].copy_(host_faces[j], non_blocking=True)
-                ev_copied[j % D].record(copy_stream)
+        def copy_block(k):  # host -> device: the samples of replay k (steps W2 + k G2 ..)
+            j0 = W2 + k * G2 + 1
+            b = k % NB
+            ev_h2d[b].synchronize()  # the pinned block's previous copy has left
+            pinned[b].copy_(host_faces[j0:j0 + G2])  # host record -> pinned staging (CPU)
+            copy_stream.wait_event(ev_used[k % 2])  # the device block's previous samples are in the ring
+            with torch.cuda.stream(copy_stream):
+                stage[k % 2].copy_(pinned[b], non_blocking=True)
+            ev_h2d[b].record(copy_stream)
+            ev_copied[k % 2].record(copy_stream)
 
-        def run_steps(n0, count):  # steps n0 .. n0 + count - 1 (samples n0 + 1 ..)
-            for j in range(n0 + 1, n0 + AHEAD + 1):
-                start_copy(j, n0 + count)
-            for n in range(n0, n0 + count):
-                start_copy(n + 1 + AHEAD, n0 + count)
-                stream.wait_event(ev_copied[(n + 1) % D])
-                tr2.lb_set_boundary(0, n + 1, stage[(n + 1) % D])
-                ev_used[(n + 1) % D].record(stream)
-                tr2.lb_step(1)
-                tr2.lb_read_fields(0, lbt.LB_FIELD_CHAIN | lbt.LB_FIELD_ASYNC, host_chain[n])
+        def push_block(k):  # staging -> boundary ring, on the context stream
+            j0 = W2 + k * G2 + 1
+            stream.wait_event(ev_copied[k % 2])
+            for i in range(G2):
+                lbt._check(lib.lb_set_boundary(ctx, 0, j0 + i, stage[k % 2, i].data_ptr()), ctx)
+            ev_used[k % 2].record(stream)
 
-        run_steps(0, W2)
+        tr2.lb_graph_capture(G2)
+        copy_block(0)
+        push_block(0)
+        copy_block(1)
+        tr2.lb_graph_launch()  # replay 0, untimed: the graph's first run
+        push_block(1)
+        copy_block(2)
         tr2.lb_sync()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ev0.record(stream)
-        run_steps(W2, e2e_steps)
+        for r in range(1, nrep2 + 1):
+            tr2.lb_graph_launch()
+            with torch.cuda.stream(stream):
+                host_hist[r - 1].copy_(hist, non_blocking=True)  # every step's chain positions of this replay
+            push_block(r + 1)
+            copy_block(r + 2)
         ev1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        units2, ms2 = whole_job(E ** 3 * e2e_steps, max(ev0.elapsed_time(ev1), wall * 1e3), dev)
+        ev_ms = ev0.elapsed_time(ev1)
+        units2, ms2 = whole_job(E ** 3 * e2e_steps, max(ev_ms, wall * 1e3), dev)
         e2e = {"value": units2 / (ms2 * 1e-3) / 1e6, "unit": UNIT,
-               "h2d_bytes_per_step": 6 * 3 * E * E * s_real, "d2h_bytes_per_step": 2 * w["nbeads"] * 3 * 8,
-               "steps": e2e_steps,
-               "how": "pinned host samples copied on a second stream %d steps ahead into device staging, pushed "
-                      "with lb_set_boundary, lb_step per step, the chain read back asynchronously every step"
-                      % AHEAD}
+               "h2d_bytes_per_step": 6 * 3 * E * E * s_real, "d2h_bytes_per_step": nb * 3 * 8,
+               "steps": e2e_steps, "event_ms": ev_ms, "wall_ms": wall * 1e3,
+               "how": "graph replays of %d steps through the C ABI; per step one boundary sample from the host "
+                      "record (pageable) into a ring of pinned staging blocks, host to device %d samples at a "
+                      "time two replays ahead, pushed with lb_set_boundary; the chain's positions back to "
+                      "pinned host memory (trajectory ring, read after each replay)" % (G2, G2)}
         tr2.close()
 
     if rank != 0:
-        tr.close()
         if world > 1:
             dist.destroy_process_group()
         return
@@ -526,8 +568,7 @@ def main():
         "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
         "config": single_config(args.storage),
         "launch": {"kernel": ["staged", "register"][choice[0]], "threads": choice[1], "ctas": choice[2],
-                   "sites_per_thread": choice[3], "bead_layout": list(getattr(tr, "bead_lanes", (0, 1))),
-                   "bead_autotune": [[list(c), t] for c, t in getattr(tr, "bead_table", [])],
+                   "sites_per_thread": choice[3], "bead_layout": bead_layout, "bead_autotune": bead_table,
                    "graph_steps": G, "graph_replays": nrep, "plain_steps": rest,
                    "autotune": [[list(c), t] for c, t in table]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -539,8 +580,6 @@ def main():
         "e2e": e2e,
         "gpu_launches": args.steps * 3,
     }
-    tr.close()
-    del faces
     torch.cuda.synchronize()
     if not args.no_forms:
         line["forms"] = measure_forms(args, value) if world == 1 else {"skipped": "forms run at one GPU only"}

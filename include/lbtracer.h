@@ -346,6 +346,23 @@ int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas
 int32_t lb_set_bead_launch(lb_ctx* ctx, int32_t lanes, int32_t beads_per_thread);
 
 /*
+ * lb_set_chain_history -- the chain trajectory on the device (Sec. 4: the
+ * chain's conformation is followed along the tracer path).  After every
+ * step n -> n + 1 the bead kernel writes the end-of-step positions of every
+ * chain into slot (n + 1) mod slots of dev, so that a graph replay of several
+ * steps leaves each step's positions to be read back at once.
+ *   dev: device memory owned by the caller, 8-byte aligned, slots x 3 x
+ *   (total bead capacity) doubles: chains in box order, each taking its
+ *   box's bead capacity (nbeads of its description), bead b of a chain at
+ *   its offset + b, x y z.  Valid until replaced or slots = 0.
+ *   slots: ring length; 0 stops recording (dev ignored).
+ *   A step whose box is flagged with an error writes nothing for that chain.
+ *   Drops a captured graph.  LB_ERR_ARG for a negative slot count, a null
+ *   or host buffer; LB_ERR_STATE when the context has no chain.
+ */
+int32_t lb_set_chain_history(lb_ctx* ctx, void* dev, int32_t slots);
+
+/*
  * lb_set_fluctuation -- fluctuating collision for one box: the thermal fluid
  * of the hybrid method the paper builds on (Sec. 1, the Ahlrichs-Duenweg
  * coupling of a bead chain to a fluctuating lattice Boltzmann fluid).  The

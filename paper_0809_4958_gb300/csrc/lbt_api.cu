@@ -200,6 +200,8 @@ struct lb_ctx {
     int sms = 0;        // multiprocessors of the context's device
     int bead_lanes = 0; // lanes per bead in the MD substeps (0 = default)
     int bead_bpt = 1;   // beads per MD thread
+    double* hist = nullptr;  // chain trajectory ring (caller's device memory), lb_set_chain_history
+    int hist_slots = 0;
     int threads = 256, ctas = 0, vw = 0;  // vw: sites per thread in stream-collide
     std::vector<int64_t> tile_prefix;  // for the current block size
     cudaGraphExec_t graph = nullptr;
@@ -349,6 +351,10 @@ int enqueue_step(lb_ctx* ctx, int64_t n)
         bp.ring_slots = ctx->L.ring_slots;
         bp.step = ctx->at<int64_t>(ctx->L.step);
         bp.status = ctx->at<int32_t>(ctx->L.status);
+        bp.hist = ctx->hist;
+        bp.hist_stride = 3 * (int64_t)ctx->L.total_beads;
+        bp.hist_slots = ctx->hist_slots;
+        bp.hist_pad = 0;
         CK(DISPATCH(ctx->storage, bead_couple(bp, nch, ctx->max_beads, ctx->bead_lanes, ctx->bead_bpt, ctx->side)));
         CK(cudaEventRecord(ctx->ev_join, ctx->side));
     }
@@ -986,6 +992,28 @@ int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas
         ctx->graph = nullptr;
     }
     return rebuild_tiles(ctx);
+}
+
+int32_t lb_set_chain_history(lb_ctx* ctx, void* dev, int32_t slots)
+{
+    if (!ctx) return LB_ERR_ARG;
+    if (slots < 0 || (slots > 0 && !dev)) return ctx->fail(LB_ERR_ARG, "lb_set_chain_history: bad slots or buffer");
+    if (slots > 0) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, dev) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+            (reinterpret_cast<uintptr_t>(dev) & 7) != 0) {
+            cudaGetLastError();
+            return ctx->fail(LB_ERR_ARG, "lb_set_chain_history: the buffer must be 8-byte aligned device memory");
+        }
+        if (ctx->chains.empty()) return ctx->fail(LB_ERR_STATE, "lb_set_chain_history: the context has no chain");
+    }
+    ctx->hist = slots > 0 ? static_cast<double*>(dev) : nullptr;
+    ctx->hist_slots = slots;
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    return LB_OK;
 }
 
 int32_t lb_set_bead_launch(lb_ctx* ctx, int32_t lanes, int32_t beads_per_thread)

@@ -194,7 +194,11 @@ struct BeadParams {
     int32_t max_beads;    // largest chain of the launch (shared-memory strides)
     int32_t noise_chunk;  // substeps whose noise is drawn at once
     int32_t lanes;        // threads per bead in the MD substeps (1, 2, 4 or 8)
-    int32_t beads_per_thread;  // beads an MD thread holds (1 or 2; 0: one warp holds the chain)
+    int32_t beads_per_thread;  // beads an MD thread holds (1 or 2; 0: chain order, two lanes per bead)
+    double* hist;              // chain trajectory ring (null: off): [slot][3 x total beads]
+    int64_t hist_stride;       // doubles per slot
+    int32_t hist_slots;
+    int32_t hist_pad;
 };
 
 struct ForcedParams {

@@ -1192,6 +1192,10 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
             pos[3 * tid + a] = R[a];
             vel[3 * tid + a] = (double)V[a];
         }
+    if (p.hist_slots > 0 && tid < N) {  // the trajectory ring: positions after step n + 1
+        double* h = p.hist + ((n + 1) % p.hist_slots) * p.hist_stride + 3 * (int64_t)ch.bead_off;
+        for (int a = 0; a < 3; a++) h[3 * tid + a] = R[a];
+    }
 
     // 5. force density at the stencil sites: every entry sums, in bead order,
     //    the contributions of all beads whose stencil holds its site; entries
@@ -1279,6 +1283,9 @@ __global__ void __launch_bounds__(kBeadThreadsMax) k_bead_couple(BeadParams p)
 template <int ST>
 __global__ void __launch_bounds__(kForcedThreads) k_forced(ForcedParams p)
 {
+    // the next step's stream-collide (a programmatic dependent) may be
+    // scheduled now; it waits on the device for this kernel to complete
+    asm volatile("griddepcontrol.launch_dependents;");
     using S = Stor<ST>;
     using A = typename S::A;
     const int chain = (int)blockIdx.x / p.splits, part = (int)blockIdx.x - chain * p.splits;
@@ -1496,8 +1503,19 @@ cudaError_t launch_staged(const SCParams& p, int ctas, cudaStream_t s)
     int64_t grid = ctas > 0 ? ctas : sms;
     if (grid > p.total_tiles) grid = p.total_tiles;
     if (grid < 1) return cudaSuccess;
-    k_stream_collide_staged<ST, SPT, KIND><<<(unsigned)grid, kStagedThreads, G::kSmemBytes, s>>>(p);
-    return cudaGetLastError();
+    // programmatic dependent launch: the blocks may be scheduled before the
+    // previous kernel on the stream completes (they wait for it on the device)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kStagedThreads);
+    cfg.dynamicSmemBytes = G::kSmemBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_stream_collide_staged<ST, SPT, KIND>, p);
 }
 
 template <int ST>

@@ -974,7 +974,6 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_stream_collide_staged(SCP
     using G = Staged<ST, SPT>;
     extern __shared__ __align__(128) unsigned char smem[];
     StagedHeader<ST>* hd = reinterpret_cast<StagedHeader<ST>*>(smem);
-    const int64_t n = *p.step;
     if (threadIdx.x == 0) {
         for (int st = 0; st < G::kStages; st++) {
             mbar_init(&hd->full[st], 1);
@@ -983,6 +982,12 @@ __global__ void __launch_bounds__(kStagedThreads, 1) k_stream_collide_staged(SCP
         fence_mbar_init();
     }
     __syncthreads();
+    // Launched as a programmatic dependent of the kernel before it on the
+    // stream (the previous step's forced re-collision): the block may start
+    // while that kernel runs, and everything above touched only shared
+    // memory.  Wait here for it to complete and its writes to be visible.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int64_t n = *p.step;
     if (threadIdx.x >= kStagedConsumers) {
         staged_produce<ST, SPT, KIND>(p, smem, hd, n);  // the whole last warp
         return;

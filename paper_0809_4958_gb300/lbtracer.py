@@ -32,7 +32,7 @@ EXPORTS = ["lb_plan", "lb_create", "lb_destroy", "lb_init", "lb_set_boundary", "
            "lb_graph_capture", "lb_graph_launch", "lb_read_fields", "lb_conservation", "lb_checkpoint_bytes", "lb_save",
            "lb_load", "lb_vorticity", "lb_set_frame_accel", "lb_sync",
            "lb_status",
-           "lb_current_step", "lb_set_launch", "lb_set_bead_launch", "lb_set_fluctuation", "lb_test_inject", "lb_profile", "lb_profile_read", "lb_last_error", "lb_synth_workspace_bytes", "lb_synth_faces",
+           "lb_current_step", "lb_set_launch", "lb_set_bead_launch", "lb_set_chain_history", "lb_set_fluctuation", "lb_test_inject", "lb_profile", "lb_profile_read", "lb_last_error", "lb_synth_workspace_bytes", "lb_synth_faces",
            "lb_synth_volume", "lb_population_sums_noalloc", "lb_mlp_param_bytes", "lb_mlp_bind", "lb_mlp_train_bytes",
            "lb_mlp_train_init", "lb_mlp_features", "lb_mlp_targets", "lb_mlp_forward", "lb_mlp_grad",
            "lb_mlp_train_step", "lb_mlp_export"]
@@ -97,6 +97,7 @@ def load(path: str | None = None, build_if_missing: bool = True):
         "lb_current_step": (_i64, [_vp]),
         "lb_set_launch": (_i32, [_vp, _i32, _i32, _i32, _i32]),
         "lb_set_bead_launch": (_i32, [_vp, _i32, _i32]),
+        "lb_set_chain_history": (_i32, [_vp, _vp, _i32]),
         "lb_test_inject": (_i32, [_vp, _i32, _i32]),
         "lb_set_fluctuation": (_i32, [_vp, _i32, _f64, ctypes.c_uint64, _vp]),
         "lb_profile": (_i32, [_vp, _i32, _i32]),
@@ -291,6 +292,13 @@ class Tracers:
 
     def lb_set_bead_launch(self, lanes=0, beads_per_thread=1):
         _check(self.lib.lb_set_bead_launch(self.ctx, int(lanes), int(beads_per_thread)), self.ctx)
+
+    def lb_set_chain_history(self, dev, slots):
+        """Trajectory ring of the chains: dev a device float64 tensor of slots x 3 x total bead capacity
+        (None with slots = 0 to stop)."""
+        if dev is not None:
+            self._after_current(dev)
+        _check(self.lib.lb_set_chain_history(self.ctx, _ptr(dev), int(slots)), self.ctx)
 
     def lb_set_launch(self, kernel=LB_KERNEL_STAGED, threads=0, ctas=0, sites_per_thread=0):
         _check(self.lib.lb_set_launch(self.ctx, int(kernel), int(threads), int(ctas), int(sites_per_thread)),

@@ -67,9 +67,12 @@ class GpuRunner:
     """Drives boxes of a Tracers context step by step, pushing each box's
     boundary samples (uploaded once to the device) as they are needed."""
 
-    def __init__(self, lbt, torch, cases, storage):
+    def __init__(self, lbt, torch, cases, storage, ring_slots=None):
         self.lbt, self.torch, self.cases = lbt, torch, cases
-        self.tr = lbt.Tracers([c.gpu_desc(lbt) for c in cases], storage)
+        if ring_slots is None:
+            self.tr = lbt.Tracers([c.gpu_desc(lbt) for c in cases], storage)
+        else:
+            self.tr = lbt.Tracers([c.gpu_desc(lbt) for c in cases], storage, ring_slots=ring_slots)
         real = self.tr.real
         self.dev_samples = [torch.from_numpy(c.samples).to("cuda", real) for c in cases]
         u0s = [torch.from_numpy(c.u0).to("cuda", real).contiguous() for c in cases]
