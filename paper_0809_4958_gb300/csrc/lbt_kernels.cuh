@@ -1286,6 +1286,9 @@ __global__ void __launch_bounds__(kForcedThreads) k_forced(ForcedParams p)
     // the next step's stream-collide (a programmatic dependent) may be
     // scheduled now; it waits on the device for this kernel to complete
     asm volatile("griddepcontrol.launch_dependents;");
+    // this kernel is itself a programmatic dependent of the stream-collide
+    // before it: wait for that grid to complete and its stores to be visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     using S = Stor<ST>;
     using A = typename S::A;
     const int chain = (int)blockIdx.x / p.splits, part = (int)blockIdx.x - chain * p.splits;
@@ -1577,8 +1580,20 @@ cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, int max_be
 template <int ST>
 cudaError_t Launch<ST>::forced(const ForcedParams& p, cudaStream_t s)
 {
-    k_forced<ST><<<p.nchains > 0 ? p.nchains * p.splits : 1, kForcedThreads, 0, s>>>(p);
-    return cudaGetLastError();
+    // a programmatic dependent of the stream-collide before it on the stream:
+    // its blocks may start on the SMs that grid has left (they wait on the
+    // device for it to complete)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(p.nchains > 0 ? p.nchains * p.splits : 1));
+    cfg.blockDim = dim3(kForcedThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_forced<ST>, p);
 }
 
 template <int ST>

@@ -884,6 +884,11 @@ __device__ __forceinline__ void staged_produce(const SCParams& p, unsigned char*
                 th.box = -1;
                 mbar_arrive(&hd->full[st]);  // completes the phase with no bytes: end of work
             }
+            // no tile left for this block: the kernel after this one (the
+            // forced re-collision, a programmatic dependent) may be scheduled
+            // once every block has got here; it waits on the device for this
+            // grid to complete
+            asm volatile("griddepcontrol.launch_dependents;");
             return;
         }
         if (lane == 0) next = (long long)atomicAdd(ctr, 1ull);  // the next claim overlaps this tile's copies
