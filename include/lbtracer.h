@@ -191,7 +191,9 @@ int32_t lb_init(lb_ctx* ctx, int32_t box, const void* u0);
  *   Samples must be pushed in order 0, 1, 2, ...; sample j may be pushed
  *   once no step still to be enqueued needs sample j - ring_slots.
  *   The copy is enqueued on the context stream (pinned host memory keeps it
- *   asynchronous).
+ *   asynchronous).  A zoomed box's sample is interpolated bilinearly onto
+ *   its face sites as it is pushed (Sec. 3: bilinear in space, interpolated
+ *   in time; both are linear, so a step then interpolates in time only).
  */
 int32_t lb_set_boundary(lb_ctx* ctx, int32_t box, int64_t sample_index, const void* face_u);
 

@@ -106,13 +106,16 @@ Layout plan_layout(const lb_box_desc* boxes, int nboxes, int storage, int ring_s
     off = align_up(off + sizeof(int64_t) * (nboxes + 1));
     L.chains = off;
     off = align_up(off + sizeof(ChainDev) * nboxes);
-    size_t pop = 0, ring = 0;
+    size_t pop = 0, ring = 0, zst = 0;
     int64_t beads = 0, chunks = 1;
     for (int b = 0; b < nboxes; b++) {
         const int64_t E = boxes[b].E, n3 = E * E * E;
         pop = align_up(pop + 19 * n3 * elem_bytes(storage));
-        const int64_t Ec = coarse_points(boxes[b].E, boxes[b].zoom);
-        ring += align_up(6 * 3 * Ec * Ec * real_bytes(storage)) / real_bytes(storage);
+        ring += align_up(6 * 3 * E * E * real_bytes(storage)) / real_bytes(storage);  // face sites
+        if (boxes[b].zoom > 1) {
+            const int64_t Ec = coarse_points(boxes[b].E, boxes[b].zoom);
+            zst = align_up(zst + 6 * 3 * Ec * Ec * real_bytes(storage));
+        }
         beads += boxes[b].nbeads;
         const int64_t c = (n3 + 4095) / 4096;
         if (c > chunks) chunks = c;
@@ -127,6 +130,9 @@ Layout plan_layout(const lb_box_desc* boxes, int nboxes, int storage, int ring_s
     off = align_up(off + pop);
     L.ring = off;
     off = align_up(off + (size_t)ring_slots * ring * real_bytes(storage));
+    L.zstage = off;
+    L.zstage_bytes = zst;
+    off = align_up(off + (zst > 0 ? zst : 16));
     L.pos = off;
     off = align_up(off + sizeof(double) * 3 * (beads + 1));
     L.vel = off;
@@ -202,6 +208,7 @@ struct lb_ctx {
     int bead_bpt = 1;   // beads per MD thread
     double* hist = nullptr;  // chain trajectory ring (caller's device memory), lb_set_chain_history
     int hist_slots = 0;
+    std::vector<size_t> zst_off;  // per zoomed box: byte offset of its coarse-sample staging (L.zstage)
     int threads = 256, ctas = 0, vw = 0;  // vw: sites per thread in stream-collide
     std::vector<int64_t> tile_prefix;  // for the current block size
     cudaGraphExec_t graph = nullptr;
@@ -532,7 +539,8 @@ int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int
         return LB_ERR_CUDA;
     }
     // box and chain tables
-    size_t pop = 0, ring = 0;
+    size_t pop = 0, ring = 0, zst = 0;
+    ctx->zst_off.assign(nboxes, 0);
     int64_t beads = 0, mlp_rows = 0;
     std::vector<MlpFeatureSet> mlp_sets;
     for (int b = 0; b < nboxes; b++) {
@@ -583,8 +591,11 @@ int32_t lb_create(const lb_box_desc* boxes, int32_t nboxes, int32_t storage, int
         }
         ctx->boxes.push_back(bd);
         pop = align_up(pop + 19 * n3 * elem_bytes(storage));
-        const int64_t Ec = coarse_points(boxes[b].E, boxes[b].zoom);
-        ring += align_up(6 * 3 * Ec * Ec * real_bytes(storage)) / real_bytes(storage);
+        ring += align_up(6 * 3 * n3 / E * real_bytes(storage)) / real_bytes(storage);  // 6 x 3 x E^2
+        if (bd.zoom > 1) {
+            ctx->zst_off[b] = zst;
+            zst = align_up(zst + 6 * 3 * (size_t)bd.Ec * bd.Ec * real_bytes(storage));
+        }
     }
     // zero the whole arena once (ring, status, step counter, force lists ...)
     e = cudaMemsetAsync(arena, 0, L.total, ctx->stream);
@@ -682,12 +693,14 @@ int32_t lb_set_boundary(lb_ctx* ctx, int32_t box, int64_t j, const void* face_u)
     }
     char* slot = ctx->arena + ctx->L.ring + (size_t)(j % ctx->L.ring_slots) * ctx->L.ring_slot_elems * rb;
     const char* src = reinterpret_cast<const char*>(face_u);
-    // boxes whose ring regions are packed back to back take one copy
+    // boxes whose ring regions are packed back to back (and hold the samples
+    // as given: no zoom) take one copy
     size_t packed = 0;
     bool contiguous = true;
     for (int b = b0; b < b1 && contiguous; b++) {
-        contiguous = (size_t)ctx->boxes[b].ring_off * rb == (size_t)ctx->boxes[b0].ring_off * rb + packed;
-        packed += 6 * 3 * (size_t)ctx->boxes[b].Ec * ctx->boxes[b].Ec * rb;
+        contiguous = ctx->boxes[b].zoom == 1 &&
+                     (size_t)ctx->boxes[b].ring_off * rb == (size_t)ctx->boxes[b0].ring_off * rb + packed;
+        packed += 6 * 3 * (size_t)ctx->boxes[b].E * ctx->boxes[b].E * rb;
     }
     if (contiguous && b1 - b0 > 1) {
         CK(cudaMemcpyAsync(slot + ctx->boxes[b0].ring_off * rb, src, packed, cudaMemcpyDefault, ctx->stream));
@@ -695,9 +708,20 @@ int32_t lb_set_boundary(lb_ctx* ctx, int32_t box, int64_t j, const void* face_u)
         return LB_OK;
     }
     for (int b = b0; b < b1; b++) {
-        const int64_t Ec = ctx->boxes[b].Ec;
+        const BoxDev& bd = ctx->boxes[b];
+        const int64_t Ec = bd.Ec;
         const size_t bytes = 6 * 3 * Ec * Ec * rb;
-        CK(cudaMemcpyAsync(slot + ctx->boxes[b].ring_off * rb, src, bytes, cudaMemcpyDefault, ctx->stream));
+        if (bd.zoom == 1) {
+            CK(cudaMemcpyAsync(slot + bd.ring_off * rb, src, bytes, cudaMemcpyDefault, ctx->stream));
+        } else {
+            // a zoomed box: the coarse sample into its staging, then bilinear in
+            // space onto the face sites of the ring slot, once per sample, so
+            // that a step interpolates only in time (Sec. 3: bilinear in space,
+            // interpolated in time -- both linear, so the order is free)
+            char* stage = ctx->arena + ctx->L.zstage + ctx->zst_off[b];
+            CK(cudaMemcpyAsync(stage, src, bytes, cudaMemcpyDefault, ctx->stream));
+            CK(DISPATCH(ctx->storage, upsample_faces(stage, slot + bd.ring_off * rb, bd.E, bd.Ec, bd.zoom, ctx->stream)));
+        }
         src += bytes;
         ctx->pushed[b] = j;
     }

@@ -275,29 +275,30 @@ __device__ __forceinline__ void coarse_velocity(const R* ring, int64_t slot_elem
     }
 }
 
-// Boundary velocity of face site (p, q): the ring holds the coarse face grid
-// (point P at site P z, Ec per side); with z > 1 the bilinear interpolation,
-// within the face, of the time-interpolated velocities at the four coarse
-// points around the site (Sec. 3: bilinear in space, interpolated in time).
+// Boundary velocity of face site (p, q): the ring holds every sample on the
+// face sites (a zoomed box's coarse samples are interpolated bilinearly onto
+// them when pushed, see bilinear_face_site), so a step interpolates in time
+// only (Sec. 3: bilinear in space, interpolated in time).
 template <class R>
 __device__ __forceinline__ void boundary_velocity(const R* ring, int64_t slot_elems, const BoxDev& bd, int f, int p,
                                                   int q, const TimeWeights<R>& tw, R u[3])
 {
-    const int z = bd.zoom, Ec = bd.Ec;
-    if (z == 1) {
-        coarse_velocity<R>(ring, slot_elems, bd.ring_off, Ec, f, p, q, tw, u);
-        return;
-    }
+    coarse_velocity<R>(ring, slot_elems, bd.ring_off, bd.E, f, p, q, tw, u);
+}
+
+// Component c of face f of a coarse sample [6][3][Ec][Ec] (point P at site
+// P z) at face site (p, q): bilinear interpolation between the four coarse
+// points around it, the last point standing in past the grid's end.
+template <class R>
+__host__ __device__ inline R bilinear_face_site(const R* coarse, int Ec, int z, int f, int c, int p, int q)
+{
     const int P0 = p / z, Q0 = q / z;
     const int P1 = P0 + 1 < Ec ? P0 + 1 : P0, Q1 = Q0 + 1 < Ec ? Q0 + 1 : Q0;
     const R fp = (R)(p - P0 * z) / (R)z, fq = (R)(q - Q0 * z) / (R)z;
-    R u00[3], u10[3], u01[3], u11[3];
-    coarse_velocity<R>(ring, slot_elems, bd.ring_off, Ec, f, P0, Q0, tw, u00);
-    coarse_velocity<R>(ring, slot_elems, bd.ring_off, Ec, f, P1, Q0, tw, u10);
-    coarse_velocity<R>(ring, slot_elems, bd.ring_off, Ec, f, P0, Q1, tw, u01);
-    coarse_velocity<R>(ring, slot_elems, bd.ring_off, Ec, f, P1, Q1, tw, u11);
-    for (int c = 0; c < 3; c++)
-        u[c] = (R(1) - fq) * ((R(1) - fp) * u00[c] + fp * u10[c]) + fq * ((R(1) - fp) * u01[c] + fp * u11[c]);
+    const R* g = coarse + ((int64_t)f * 3 + c) * Ec * Ec;
+    const R u00 = g[(int64_t)Q0 * Ec + P0], u10 = g[(int64_t)Q0 * Ec + P1];
+    const R u01 = g[(int64_t)Q1 * Ec + P0], u11 = g[(int64_t)Q1 * Ec + P1];
+    return (R(1) - fq) * ((R(1) - fp) * u00 + fp * u10) + fq * ((R(1) - fp) * u01 + fp * u11);
 }
 
 }  // namespace lbt

@@ -120,11 +120,12 @@ struct ForceEntry {
 
 // Arena layout (byte offsets), computed by plan().
 struct Layout {
-    size_t boxes, tile_prefix, chains, pop_a, pop_b, ring, pos, vel, forces, cons_partial, cons_out,
+    size_t boxes, tile_prefix, chains, pop_a, pop_b, ring, zstage, pos, vel, forces, cons_partial, cons_out,
         status, step, tile_counter, faccel, chain_accel, fluct, mlp_sets, mlp_x, mlp_y, total;
     size_t pop_bytes;        // bytes of one population buffer
-    size_t ring_slot_elems;  // real elements per ring slot
-    int32_t ring_slots;      // slots in the ring of coarse samples
+    size_t ring_slot_elems;  // real elements per ring slot (6 x 3 x E^2 per box: face sites, zoomed or not)
+    int32_t ring_slots;      // slots in the ring of boundary samples
+    size_t zstage_bytes;     // staging of the coarse samples of zoomed boxes (6 x 3 x Ec^2 each, back to back)
     int64_t cons_chunks;     // max conservation chunks per box
     int64_t total_beads;
     int64_t mlp_rows;        // face rows of all boxes that use the upsampler
@@ -226,6 +227,8 @@ template <int ST>
 struct Launch {
     static cudaError_t stream_collide(const SCParams& p, int kernel, int threads, int ctas, int vw, cudaStream_t s);
     static cudaError_t bead_couple(const BeadParams& p, int nchains, int max_beads, int lanes, int bpt, cudaStream_t s);
+    // coarse face sample [6][3][Ec][Ec] -> face sites [6][3][E][E] (bilinear, point P at site P z)
+    static cudaError_t upsample_faces(const void* coarse, void* fine, int E, int Ec, int z, cudaStream_t s);
     static cudaError_t forced(const ForcedParams& p, cudaStream_t s);
     static cudaError_t init(void* A, const BoxDev* boxes, int box, int64_t n3, const void* u0, cudaStream_t s);
     static cudaError_t fields(const void* A, const BoxDev* boxes, int box, int64_t n3, int what, void* dst,

@@ -1577,6 +1577,30 @@ cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, int max_be
     return cudaGetLastError();
 }
 
+// A zoomed box's coarse boundary sample onto its face sites (one thread per
+// face site and component).
+template <class R>
+__global__ void k_upsample_faces(const R* coarse, R* fine, int E, int Ec, int z)
+{
+    const int64_t fe = (int64_t)E * E, total = 18 * fe;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int fc = (int)(i / fe);  // face * 3 + component
+        const int64_t r = i - fc * fe;
+        const int q = (int)(r / E), p = (int)(r - (int64_t)q * E);
+        fine[i] = bilinear_face_site<R>(coarse, Ec, z, fc / 3, fc % 3, p, q);
+    }
+}
+
+template <int ST>
+cudaError_t Launch<ST>::upsample_faces(const void* coarse, void* fine, int E, int Ec, int z, cudaStream_t s)
+{
+    using R = typename Stor<ST>::R;
+    const int64_t total = 18LL * E * E;
+    const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    k_upsample_faces<R><<<blocks, 256, 0, s>>>(reinterpret_cast<const R*>(coarse), reinterpret_cast<R*>(fine), E, Ec, z);
+    return cudaGetLastError();
+}
+
 template <int ST>
 cudaError_t Launch<ST>::forced(const ForcedParams& p, cudaStream_t s)
 {
