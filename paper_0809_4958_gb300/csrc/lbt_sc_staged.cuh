@@ -836,6 +836,40 @@ __device__ __forceinline__ void staged_consume(const SCParams& p, unsigned char*
     }
 }
 
+// Prefetch into L2 (evict-last) of the upsampler residuals of substep ms for
+// the boundary sites of the box rows that tile [s0, s0 + T) covers: the
+// x-face sites at both ends of every row (faces 0 and 1, in-face (y, z)) and
+// whole rows on a y or z face, three components each.  One row per lane;
+// every address lies inside the box's residual columns.
+__device__ __forceinline__ void prefetch_l2(const float* a)
+{
+    asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(a));
+}
+__device__ __forceinline__ void prefetch_mlp_residuals(const SCParams& p, const BoxDev& bd, int ms, int64_t s0, int T,
+                                                       int lane)
+{
+    const int Eb = bd.E;
+    const int64_t fe = (int64_t)Eb * Eb, str = p.mlp_ystride;
+    const float* y0 = p.mlp_y + (int64_t)(3 * (ms - 1)) * str + bd.mlp_row;
+    const int64_t r_first = s0 / Eb, r_end = (s0 + T - 1) / Eb + 1;
+    for (int64_t r = r_first + lane; r < r_end && r < fe; r += 32) {
+        const int yy = (int)(r % Eb), zz = (int)(r / Eb);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            prefetch_l2(y0 + c * str + (int64_t)zz * Eb + yy);       // x- face
+            prefetch_l2(y0 + c * str + fe + (int64_t)zz * Eb + yy);  // x+ face
+        }
+        const int fo = yy == 0 ? 2 : (yy == Eb - 1 ? 3 : (zz == 0 ? 4 : (zz == Eb - 1 ? 5 : -1)));
+        if (fo >= 0) {
+            const int q = fo < 4 ? zz : yy;  // in-face (x, z) on a y face, (x, y) on a z face
+            const float* row = y0 + fo * fe + (int64_t)q * Eb;
+            for (int x0 = 0; x0 < Eb; x0 += 32)
+#pragma unroll
+                for (int c = 0; c < 3; c++) prefetch_l2(row + c * str + x0);
+        }
+    }
+}
+
 // Producer warp (the last warp): claims tiles from the global counter (reset
 // to zero by the forced re-collision at the end of every step, so a block that
 // starts late -- its SM still busy with the bead kernel -- simply takes fewer
@@ -967,6 +1001,11 @@ __device__ __forceinline__ void staged_produce(const SCParams& p, unsigned char*
                 bulk_load(stage + lane * G::kRowStride + (lo - start) * sizeof(E), Ab + (int64_t)lane * n3 + lo, bytes,
                           &hd->full[st]);
         }
+        // upsampler boxes: the residuals the tile's boundary sites will add
+        // come from an output far larger than L2; prefetch them into L2 while
+        // the copies are in flight, so that the consumers' loads hit there
+        const int ms = __shfl_sync(0xffffffffu, mlp_s, 0);
+        if (bd.mlp_row >= 0 && ms > 0) prefetch_mlp_residuals(p, bd, ms, s0, T, lane);
     }
 }
 
