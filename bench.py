@@ -146,6 +146,25 @@ KERNEL_SOURCES = {
 }
 
 
+def plan_timed_steps(steps, graph=16):
+    """Split `steps` timed steps into graph replays and plain steps:
+    (G, nrep, rest) with nrep * G + rest == steps.  The last `rest` steps run
+    plainly, their stream-collide launches timed by CUDA events (event-record
+    nodes inside a graph serialise its kernels: about 10 us per step at
+    128^3).  Runs of 64 steps or more use graphs of `graph` steps and 8 to
+    graph + 7 plain steps; shorter runs keep up to 8 plain steps and the
+    largest even graph length that divides the rest (G = 0: no graph)."""
+    if steps >= 64:
+        P = 8 + (steps - 8) % graph
+        G = graph
+    else:
+        P = min(8, steps)
+        even = (steps - P) // 2 * 2
+        G = max([g for g in range(2, min(graph, even) + 1, 2) if even % g == 0] or [0])
+    nrep = (steps - P) // G if G else 0
+    return G, nrep, steps - nrep * G
+
+
 def kernel_source_hash(kernel):
     """Hash of the sources a stream-collide kernel is compiled from."""
     h = hashlib.sha256()
@@ -353,19 +372,7 @@ def main():
     modes = inputs.mode_table(seed, w["M"], w["k_min"], w["k_max"], E)
     ncand = 0 if args.no_tune else len(autotune.candidates(storage, torch.cuda.get_device_properties(dev).multi_processor_count))
     tune_steps = 7 * ncand + 7 * 6  # launch shapes, then the bead kernel's six thread layouts
-    # graph replays of G steps, then P steps stepped plainly with the
-    # stream-collide launches timed by CUDA events (event-record nodes inside
-    # a graph serialise its kernels: they cost about 10 us per step at
-    # 128^3): exactly args.steps timed steps.  G = 16 for runs of 64 steps
-    # or more (P from 8 to 23), else the largest even length that divides
-    # the graph part.
-    if args.steps >= 64:  # full graphs of 16: P in 8 .. 23
-        P = 8 + (args.steps - 8) % w["graph"]
-        G = w["graph"]
-    else:
-        P = min(8, args.steps)
-        even = (args.steps - P) // 2 * 2
-        G = max([g for g in range(2, min(w["graph"], even) + 1, 2) if even % g == 0] or [0])
+    G, _, _ = plan_timed_steps(args.steps, w["graph"])
     nsamp = args.warmup + tune_steps + args.steps + 2 * w["graph"] + 2  # + one untimed replay
     faces = lbt.synth_faces(modes, E, w["K"], 0, nsamp, real)
     u0 = lbt.synth_volume(modes, E, 0.0, real)
@@ -409,9 +416,9 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     # G steps per CUDA graph replay; the samples of the next G steps are pushed
-    # (device to device) before each replay
-    nrep = (args.steps - P) // G if G else 0
-    rest = args.steps - nrep * G  # the plain steps, P of them and more, all with timed stream-collides
+    # (device to device) before each replay; `rest` plain steps after them
+    # (at least 8 when the run is that long), all with timed stream-collides
+    _, nrep, rest = plan_timed_steps(args.steps, w["graph"])
     if nrep:
         tr.lb_graph_capture(G)
         push_until(tr.lb_current_step() + G, dev_src)  # one untimed replay: the graph's first run
