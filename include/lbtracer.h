@@ -140,7 +140,7 @@ typedef struct lb_ctx lb_ctx;
 /*
  * lb_plan -- size of the device arena for a context of tracer boxes (Sec. 2:
  * one fine lattice Boltzmann box per Lagrangian tracer, each fed by the
- * coarse flow around it; Sec. 4: the paper follows 100 tracers).
+ * coarse flow around it; Sec. 3: the paper follows 100 tracers).
  *   boxes[nboxes]: box descriptions (host).  storage: LB_STORE_*.
  *   ring_slots: coarse samples the boundary ring holds (0 = 4, at most 4096).
  *   Four slots cover one step at a time; a captured graph of G steps needs
@@ -240,7 +240,7 @@ int32_t lb_graph_capture(lb_ctx* ctx, int32_t nsteps);
 int32_t lb_graph_launch(lb_ctx* ctx);
 
 /*
- * lb_read_fields -- observables of one box at the current step (Sec. 4: the
+ * lb_read_fields -- observables of one box at the current step (Sec. 3: the
  * LB velocity field is what the paper compares with the DNS, Figs. 1-2).
  *   LB_FIELD_RHO / LB_FIELD_U: on boundary sites the moments of the stored
  *   equilibrium; elsewhere the moments of the pulled populations
@@ -262,7 +262,7 @@ int32_t lb_conservation(lb_ctx* ctx, int32_t box, double* out);
 
 /*
  * lb_vorticity -- mean magnitude of the vorticity over a cube of one box
- * (Sec. 4, Figs. 1 and 2: |omega| averaged over the whole sub-volume around
+ * (Sec. 3, Figs. 1 and 2: |omega| averaged over the whole sub-volume around
  * the tracer and over a small region at its centre, LB against DNS).
  *   u is the velocity lb_read_fields(LB_FIELD_U) reports; omega = curl u by
  *   second-order central differences, omega_x = (u_z(y+1) - u_z(y-1))/2 -
@@ -348,8 +348,8 @@ int32_t lb_set_launch(lb_ctx* ctx, int32_t kernel, int32_t threads, int32_t ctas
 int32_t lb_set_bead_launch(lb_ctx* ctx, int32_t lanes, int32_t beads_per_thread);
 
 /*
- * lb_set_chain_history -- the chain trajectory on the device (Sec. 4: the
- * chain's conformation is followed along the tracer path).  After every
+ * lb_set_chain_history -- the chain trajectory on the device (Sec. 1 and 4: the
+ * method exists to follow a polymer chain's conformation in the flow).  After every
  * step n -> n + 1 the bead kernel writes the end-of-step positions of every
  * chain into slot (n + 1) mod slots of dev, so that a graph replay of several
  * steps leaves each step's positions to be read back at once.

@@ -406,7 +406,7 @@ def num_threads() -> int:
 def vorticity_mean(u, lo, hi):
     """Mean magnitude of the vorticity over the cube lo <= x, y, z <= hi of a
     velocity field u [3][E][E][E] (layout [c][z][y][x]), omega = curl u by
-    second-order central differences (Sec. 4, Figs. 1 and 2: |omega| averaged
+    second-order central differences (Sec. 3, Figs. 1 and 2: |omega| averaged
     over the sub-volume around the tracer and over a region at its centre).
     The cube must lie inside sites 1 .. E-2.  FP64, numpy."""
     u = np.asarray(u, dtype=np.float64)

@@ -7,7 +7,7 @@ tau~_eta = eta~^2 / nu~.  Eq. (1) matches velocities in Kolmogorov units,
 w~ tau~_eta / eta~ = w tau_eta / eta, and the times t~ / tau~_eta =
 t / tau_eta; lengths scale with eta~ / eta.  Accelerations (the co-moving
 frame force -dv/dt) follow as length / time^2.  The Mach number of the LB run
-is Ma = eta~ / (tau~_eta c_s) (Sec. 4).  Host-side arithmetic only.
+is Ma = eta~ / (tau~_eta c_s) (Sec. 3).  Host-side arithmetic only.
 """
 from __future__ import annotations
 

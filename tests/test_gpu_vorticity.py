@@ -1,5 +1,5 @@
 """Vorticity diagnostic through the C ABI: the GPU result against the
-oracle's definition on the same velocity field, and the validation of Sec. 4
+oracle's definition on the same velocity field, and the validation of Sec. 3
 (Fig. 2: LB vorticity against the DNS over the whole sub-volume and over a
 region of 1.25/6 of its edge at the centre) restated with an exact
 Navier-Stokes solution, the decaying ABC flow, in place of the DNS record."""

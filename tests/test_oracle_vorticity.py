@@ -1,5 +1,5 @@
 """Pins of the oracle's vorticity diagnostic (mean |curl u| over a cube by
-central differences, Sec. 4, Figs. 1 and 2) against closed forms."""
+central differences, Sec. 3, Figs. 1 and 2) against closed forms."""
 import numpy as np
 import pytest
 

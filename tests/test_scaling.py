@@ -1,5 +1,5 @@
 """Eq. (1) unit matching (Sec. 3) against the numbers the paper prints for its
-case study (Sec. 4), and the synthetic tracer's frame acceleration."""
+case study (Sec. 3), and the synthetic tracer's frame acceleration."""
 import math
 
 import numpy as np
